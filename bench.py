@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark: new configurations per second of the breadth-first exploration.
+
+Workload (default "random64"): the seeded 64-neuron random SNP system
+(seed 1; 2-3 rules per neuron, regexes a^i(a^j)*, out-degree 4, initial spikes
+U[0,6]) explored to depth 8 with the frontier capped at 2^20 configurations
+and at most 2^24 candidates examined per depth, sparse int32 transition.
+
+One step = one complete snp_explore call (all 8 depths, steps (a)-(d) on the
+GPU) with the system already resident.  value = new configurations found over
+all timed steps (and all ranks) / the max over ranks of the device time of the
+timed region (CUDA events on the exploration's stream).  The working set of a
+step (2.1 GB of configurations, 128 MB table) exceeds L2, so no flush is added.
+
+e2e: the same metric through the C ABI with host buffers: every step loads the
+system from host arrays, explores, and copies every configuration back to
+pinned host memory; wall clock around all of it.
+
+With --gpus N > 1 (torchrun), every rank explores its own copy of the system
+(replicas: one system's BFS is not sharded); the value aggregates all ranks.
+--impl reference times the CPU oracle on bounded samples instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "new configurations/sec per BFS depth (bit-exact), int8-TC batched vs plain int32"
+UNIT = "new configurations/s"
+
+WORKLOADS = {
+    "random64": dict(seed=1, depth=8, cap=1 << 20, budget=1 << 24,
+                     desc="random SNP system seed 1: m=64, 2-3 rules/neuron, a^i(a^j)* with i U[1,4], j U{0,1,2}, "
+                          "c U[1,i], p U{1,2} (15% forgetting), out-degree 4, C0 U[0,6]; BFS depth 8, "
+                          "frontier cap 2^20, candidate budget 2^24, sparse int32 transition"),
+}
+# The CPU baseline runs the oracle on the workload's first two depths, exactly.
+CPU_SAMPLE = dict(depth=2, cap=1 << 20, budget=1 << 24)
+# Each step of the reference arm: the first two depths with a smaller cap and budget.
+REF_SAMPLE = dict(depth=2, cap=1 << 16, budget=1 << 20)
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_system(name):
+    import snp_synth
+    w = WORKLOADS[name]
+    return snp_synth.random_64(w["seed"])
+
+
+class ClockSampler:
+    """nvidia-smi samples of clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1104_1824_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the expand kernel from the committed ncu summary,
+    or None when the summary is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"expand_kernel_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line:
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return {"bytes_per_candidate": float(vals["dram_bytes_per_candidate"])}
+    except (KeyError, ValueError):
+        return None
+
+
+def run_cpu_baseline(system, sample):
+    import oracle
+    oracle.build()
+    o = oracle.Oracle(system)
+    t0 = time.perf_counter()
+    e = o.explore(sample["depth"], cap=sample["cap"], budget=sample["budget"])
+    dt = time.perf_counter() - t0
+    new = sum(d.new for d in e.depths[1:])
+    return new, dt
+
+
+def bench_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = rank_info()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1104_1824_gb300 as snp
+
+    w = WORKLOADS[args.workload]
+    system = make_system(args.workload)
+    s = snp.System(system)
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(cap=w["cap"], budget=w["budget"], stream=stream)
+    for _ in range(args.warmup):
+        s.explore(w["depth"], **kw)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    total_new = 0
+    expand_bytes = 0
+    expand_ms = 0.0
+    launches = 0
+    candidates = 0
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            s.explore(w["depth"], kernel_timing=True, **kw)
+            st = s.depth_stats()
+            total_new += sum(d.new for d in st[1:])
+            expand_bytes += sum(d.expand_bytes for d in st)
+            expand_ms += sum(d.expand_ms for d in st)
+            launches += sum(d.launches for d in st)
+            candidates += sum(d.examined for d in st[1:])
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    per_depth = [{"depth": d, "new": x.new, "examined": x.examined, "ms": round(x.ms, 4),
+                  "new_per_s": round(x.new / (x.ms * 1e-3)) if x.ms > 0 else None} for d, x in enumerate(st) if d > 0]
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+        t = torch.tensor([float(total_new), float(launches)], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        total_all, launches_all = int(t[0].item()), int(t[1].item())
+    else:
+        ms_max, total_all, launches_all = ms, total_new, launches
+    value = total_all / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (the expand kernel: steps (b)-(d) per candidate)
+    peak, peak_kind = measured_peaks()
+    achieved = expand_bytes / (expand_ms * 1e-3) / 1e9 if expand_ms > 0 else None
+    traffic = profiled_traffic(args.workload)
+    nlaunch_expand = sum(x.chunks for x in st) * args.steps
+    roofline = {
+        "kernel": "k_claim (expand: decode, C' = C + S.M, fingerprint, probe/claim)",
+        "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+        "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+        "frac": round(achieved / peak, 4) if achieved else None,
+        "algorithmic_bytes_per_launch": int(expand_bytes / max(1, nlaunch_expand)),
+        "avg_launch_ms": round(expand_ms / max(1, nlaunch_expand), 4),
+        "traffic": (int(traffic["bytes_per_candidate"] * candidates / max(1, nlaunch_expand)) if traffic else None),
+        "expand_share_of_step": round(expand_ms / ms, 4) if ms > 0 else None,
+    }
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(args, system, w, snp, torch, dev)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        new, dt = run_cpu_baseline(system, CPU_SAMPLE)
+        cpu = {"value": round(new / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the workload's first {CPU_SAMPLE['depth']} depths exactly (cap 2^20, budget 2^24): "
+                         f"{new} new configurations in {dt:.2f} s, single-threaded C++ oracle",
+               "seconds": round(dt, 2)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {w['desc']}", "depth": w["depth"], "frontier_cap": w["cap"],
+                       "candidate_budget": w["budget"], "transition": "sparse_i32",
+                       "new_per_step": total_new // args.steps,
+                       "l2": "inputs larger than L2 (2.1 GB of configurations written per step)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "per_depth": per_depth,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_all,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def bench_e2e(args, system, w, snp, torch, dev):
+    """Host arrays in, every configuration back in pinned host memory, per step."""
+    import numpy as np
+    arrays = [np.ascontiguousarray(x, dtype=np.int32) for x in (system.rule_neuron, system.rule_i, system.rule_j,
+                                                                   system.M, system.c0)]
+    h2d = sum(a.nbytes for a in arrays)
+    host_out = None
+    steps = max(1, min(args.steps, 3))
+    total_new, d2h = 0, 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        h = snp.snp_load_system(system.m, *arrays)
+        o = snp.snp_explore_opts_init()
+        o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
+        snp.snp_explore(h, o)
+        n = snp.snp_reachable_count(h)
+        if host_out is None or host_out.shape[0] < n:
+            host_out = torch.empty((n, system.m), dtype=torch.int32, pin_memory=True)
+        snp.snp_reachable(h, host_out, n)
+        snp.snp_free(h)
+        total_new += n - 1
+        d2h = n * system.m * 4
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(total_new / dt, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps, "ms_per_step": round(dt / steps * 1e3, 3)}
+
+
+def bench_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    system = make_system(args.workload)
+    for _ in range(args.warmup):
+        run_cpu_baseline(system, REF_SAMPLE)
+    total_new, total_s = 0, 0.0
+    for _ in range(args.steps):
+        new, dt = run_cpu_baseline(system, REF_SAMPLE)
+        total_new += new
+        total_s += dt
+    value = total_new / total_s
+    sample = (f"per step the workload's first {REF_SAMPLE['depth']} depths with cap 2^16 and budget 2^20 "
+              f"({total_new // args.steps} new configurations), single-threaded C++ oracle")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload]['desc']}", "transition": "oracle"},
+            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/* snp.h — C ABI of the GB300 simulator for spiking neural P systems without
+ * delays (Cabarle, Adorna, Martinez-del-Amor, "Simulating Spiking Neural P
+ * systems without delays using GPUs").
+ *
+ * The library explores, breadth first, every configuration reachable from the
+ * initial configuration C0 (Algorithm 1).  Each depth runs four steps on one
+ * GPU: (a) the rule-applicability scan of every frontier configuration
+ * (Algorithm 2, II-1), (b) the enumeration of every valid spiking vector as a
+ * mixed-radix index over the per-neuron choice counts (Eq. psi; Algorithm 2,
+ * II-2/II-3), (c) the transition C' = C + S . M_Pi (Eq. next-config), and (d)
+ * deduplication through a device hash table into the next frontier
+ * (Algorithm 1, step IV).
+ *
+ * Conventions
+ *  - Every function returns an int status (SNP_OK = 0 or an SNP_E_* code) and
+ *    never throws.  snp_last_error() gives a message for the calling thread.
+ *  - Arrays described as "host or device" may be either; the library infers
+ *    the direction of each copy from the pointer.  Arrays described as
+ *    "host" must be host memory.  The caller keeps ownership of every array
+ *    it passes; the library copies what it needs before returning.
+ *  - A handle owns all device memory it allocates and is bound to the CUDA
+ *    device that was current when it was created.  Handles are not
+ *    thread-safe: one thread at a time per handle.
+ *  - Configurations are int32 rows of length m (spikes per neuron, neuron 0
+ *    first); lists of configurations are row-major [n x m].
+ */
+#ifndef SNP_H_
+#define SNP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SNP_ABI_VERSION 1
+
+/* Status codes. */
+#define SNP_OK 0
+#define SNP_E_INVALID 1  /* malformed system or options (shapes, signs, order, limits) */
+#define SNP_E_RANGE 2    /* an entry of M_Pi is out of range for the requested transition */
+#define SNP_E_NOMEM 3    /* a device or host allocation failed */
+#define SNP_E_CUDA 4     /* a CUDA call or kernel failed */
+#define SNP_E_TIMEOUT 5  /* a bounded device-side wait ran out */
+#define SNP_E_BUFFER 6   /* caller's buffer too small: the count is set, nothing is written */
+#define SNP_E_OVERFLOW 7 /* a spike count could leave the int32 range */
+#define SNP_E_STATE 8    /* call out of order (e.g. results before an exploration) */
+#define SNP_E_INTERNAL 9 /* a device-side consistency check failed */
+
+/* Transition forms for step (c). */
+#define SNP_T_SPARSE_I32 0 /* gather over M_Pi's nonzeros, int32 on the CUDA cores */
+#define SNP_T_TC_I8 1      /* dense 0/1 x int8 tensor-core product, int32 accumulation */
+
+/* Saturation value of Psi and of sums of Psi: "at least 2^64 - 1". */
+#define SNP_PSI_SAT UINT64_MAX
+
+typedef struct snp_system* snp_handle;
+
+/* An SNP system without delays in matrix form (Definition 1, Definition 2).
+ * All arrays are host memory and are copied by snp_load_system.
+ *  m            neurons, 1 <= m <= 1024.
+ *  R            rules, 1 <= R; the rules of one neuron are consecutive and in
+ *               the system's total rule order (rule_neuron non-decreasing), at
+ *               most 32 rules per neuron.
+ *  rule_neuron  [R] owning neuron of each rule, in [0, m).
+ *  rule_i,      [R] the rule's regular expression E = a^i (a^j)*; j = 0 means
+ *  rule_j           E = a^i exactly.  i >= 0, j >= 0.  The paper's rules
+ *                   a^k -> a (form (b-3)) are i = k, j = 1.
+ *  M            [R * m] spiking transition matrix M_Pi, row-major, rows =
+ *               rules, columns = neurons (Definition 2, Eq. snp_mat).  The
+ *               entry on a rule's own neuron is -c (c >= 1 spikes consumed);
+ *               every other entry is >= 0 (spikes received).
+ *  c0           [m] initial configuration C0, entries >= 0.
+ * A rule is applicable to a neuron holding x spikes iff a^x is in L(E) and
+ * x >= c (Section 2.1, rule (b-1)). */
+typedef struct {
+  int32_t m;
+  int32_t R;
+  const int32_t* rule_neuron;
+  const int32_t* rule_i;
+  const int32_t* rule_j;
+  const int32_t* M;
+  const int32_t* c0;
+} snp_system_desc;
+
+/* Options of snp_explore.  Fill with snp_explore_opts_init first.
+ *  depth             number of BFS expansions (depth >= 0).  Exploration ends
+ *                    earlier when a depth finds no new configuration
+ *                    (Algorithm 1, stopping criteria).
+ *  transition        SNP_T_SPARSE_I32 or SNP_T_TC_I8.
+ *  frontier_cap      most new configurations accepted per depth; <= 0: no cap.
+ *                    The accepted ones are the first ones in candidate order.
+ *  candidate_budget  most candidates (parent, spiking vector) examined per
+ *                    depth; <= 0: no budget.
+ *  max_expand_value  >= 0: a configuration holding more than this many spikes
+ *                    in some neuron is recorded but not expanded; < 0: off.
+ *  record_parents    1: remember, per configuration, its parent's discovery
+ *                    index and the spiking vector's index (snp_parents).
+ *  chunk             candidates per device pass; <= 0 chooses automatically.
+ *  stream            cudaStream_t to run on, or NULL for the default stream.
+ *  kernel_timing     1: time the expand kernel of every pass with CUDA events
+ *                    on `stream` (snp_depth_info.expand_ms).
+ * Candidate order ("canonical order"): parents in discovery order; for each,
+ * its valid spiking vectors in mixed-radix order with neuron 0's choice most
+ * significant and the last neuron's least; a neuron's choices are its
+ * applicable rules in rule order, or "no rule" if none applies. */
+typedef struct {
+  int32_t depth;
+  int32_t transition;
+  int64_t frontier_cap;
+  int64_t candidate_budget;
+  int32_t max_expand_value;
+  int32_t record_parents;
+  int64_t chunk;
+  void* stream;
+  int32_t kernel_timing;
+  int32_t reserved0;
+  int64_t reserved[3];
+} snp_explore_opts;
+
+/* Statistics of one BFS depth (index 0 is the root level). */
+typedef struct {
+  int64_t new_configs;   /* configurations first found at this depth */
+  int64_t parents;       /* frontier size expanded at this depth */
+  uint64_t candidates;   /* sum of Psi over the frontier (saturating) */
+  int64_t examined;      /* candidates examined before the depth stopped */
+  int32_t truncated;     /* 1 iff examined < candidates */
+  int32_t chunks;        /* device passes used */
+  float ms;              /* device time of the depth (CUDA events) */
+  float expand_ms;       /* device time of the expand kernel (kernel_timing) */
+  int64_t expand_bytes;  /* algorithmic DRAM bytes of the expand kernel: per
+                            candidate an 8-byte slot probe, per duplicate a
+                            4m-byte key compare, per new key a 4m-byte staged
+                            row and an 8-byte slot write, per parent a 4m-byte
+                            row read */
+  int64_t launches;      /* kernels launched for this depth */
+} snp_depth_info;
+
+/* Fills *opts with defaults: depth 1, sparse int32, no cap, no budget,
+ * max_expand_value -1, no parent records, automatic chunk, default stream,
+ * no kernel timing. */
+void snp_explore_opts_init(snp_explore_opts* opts);
+
+/* Validates and copies a system (Definition 1, Definition 2) and uploads its
+ * rule table and M_Pi to the current device.  On success *out is a new handle.
+ * Errors: SNP_E_INVALID (see snp_system_desc), SNP_E_NOMEM, SNP_E_CUDA. */
+int snp_load_system(const snp_system_desc* desc, snp_handle* out);
+
+/* Releases a handle and all its device memory.  NULL is accepted. */
+int snp_free(snp_handle h);
+
+/* One transition step from configuration C (Eq. next-config for every valid
+ * spiking vector, Algorithm 2): writes the children C + S . M_Pi of C, in
+ * canonical order and without deduplication, to out[k * m + j] for
+ * k < min(Psi(C), capacity).  *psi receives Psi(C) (Eq. psi with neurons that
+ * cannot fire counted once; saturating).
+ *  C    [m] host or device.   out  [capacity * m] host or device.
+ * Errors: SNP_E_INVALID (negative entries in C, capacity < 0),
+ * SNP_E_OVERFLOW (a child would leave int32), SNP_E_CUDA. */
+int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uint64_t* psi);
+
+/* Breadth-first exploration from C0 (Algorithm 1): runs steps (a)-(d) for
+ * depths 1..opts->depth on the device and keeps every configuration found.
+ * *depth_reached = the last depth that found a new configuration.
+ * truncated_flags (host, [opts->depth + 1], may be NULL) receives 1 for each
+ * depth stopped by the cap or the budget.  A new call discards the previous
+ * exploration.  Errors: SNP_E_INVALID, SNP_E_RANGE (SNP_T_TC_I8 with an entry
+ * of M_Pi outside [-127, 127]), SNP_E_NOMEM, SNP_E_OVERFLOW, SNP_E_TIMEOUT,
+ * SNP_E_INTERNAL, SNP_E_CUDA. */
+int snp_explore(snp_handle h, const snp_explore_opts* opts, int32_t* depth_reached, int32_t* truncated_flags);
+
+/* Every configuration found by the last snp_explore, C0 first, in discovery
+ * order (depth by depth, each depth in canonical candidate order), into
+ * out[capacity * m] (host or device).  *n receives the count.  With
+ * capacity < *n nothing is written and SNP_E_BUFFER is returned (out may then
+ * be NULL).  per_depth_new (host, may be NULL) receives depth_reached + 1
+ * counts, index 0 being C0's level.  Errors: SNP_E_STATE, SNP_E_BUFFER, SNP_E_CUDA. */
+int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int64_t* per_depth_new);
+
+/* With record_parents set in the last snp_explore: for each configuration k in
+ * discovery order, parent[k] = discovery index of the parent it was first
+ * produced from and index[k] = that spiking vector's position among the
+ * parent's valid vectors (C0: -1 and 0).  Host or device arrays of capacity
+ * entries.  Errors: SNP_E_STATE, SNP_E_BUFFER, SNP_E_CUDA. */
+int snp_parents(snp_handle h, int64_t* parent, uint64_t* index, int64_t capacity, int64_t* n);
+
+/* Statistics of depth d (0 <= d <= depth_reached + 1) of the last
+ * exploration.  Errors: SNP_E_STATE, SNP_E_INVALID. */
+int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char* snp_last_error(void);
+
+/* SNP_ABI_VERSION of the loaded library. */
+int snp_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNP_H_ */

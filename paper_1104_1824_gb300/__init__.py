@@ -1,0 +1,293 @@
+"""GB300 simulator for spiking neural P systems without delays.
+
+A thin ctypes binding over the C ABI in include/snp.h (libsnp_gb300.so, built
+by paper_1104_1824_gb300.build).  Every function with an ``snp_`` name marshals
+its arguments and calls the C function of the same name; every step of the
+exploration runs in the library's CUDA kernels.  There is no fallback: if the
+library is missing, the first call raises ImportError.
+
+Arrays may be numpy arrays (host memory) or objects exposing ``data_ptr()``
+such as torch tensors (device memory); the library infers the copy direction.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsnp_gb300.so")
+
+SNP_OK = 0
+SNP_E_INVALID = 1
+SNP_E_RANGE = 2
+SNP_E_NOMEM = 3
+SNP_E_CUDA = 4
+SNP_E_TIMEOUT = 5
+SNP_E_BUFFER = 6
+SNP_E_OVERFLOW = 7
+SNP_E_STATE = 8
+SNP_E_INTERNAL = 9
+SNP_T_SPARSE_I32 = 0
+SNP_T_TC_I8 = 1
+SNP_PSI_SAT = (1 << 64) - 1
+
+ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOMEM", 4: "SNP_E_CUDA",
+               5: "SNP_E_TIMEOUT", 6: "SNP_E_BUFFER", 7: "SNP_E_OVERFLOW", 8: "SNP_E_STATE",
+               9: "SNP_E_INTERNAL"}
+
+# Every symbol include/snp.h declares.
+EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
+           "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version"]
+
+
+class SnpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class snp_system_desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("R", ctypes.c_int32),
+                ("rule_neuron", ctypes.c_void_p), ("rule_i", ctypes.c_void_p), ("rule_j", ctypes.c_void_p),
+                ("M", ctypes.c_void_p), ("c0", ctypes.c_void_p)]
+
+
+class snp_explore_opts(ctypes.Structure):
+    _fields_ = [("depth", ctypes.c_int32), ("transition", ctypes.c_int32),
+                ("frontier_cap", ctypes.c_int64), ("candidate_budget", ctypes.c_int64),
+                ("max_expand_value", ctypes.c_int32), ("record_parents", ctypes.c_int32),
+                ("chunk", ctypes.c_int64), ("stream", ctypes.c_void_p), ("kernel_timing", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 3)]
+
+
+class snp_depth_info(ctypes.Structure):
+    _fields_ = [("new_configs", ctypes.c_int64), ("parents", ctypes.c_int64), ("candidates", ctypes.c_uint64),
+                ("examined", ctypes.c_int64), ("truncated", ctypes.c_int32), ("chunks", ctypes.c_int32),
+                ("ms", ctypes.c_float), ("expand_ms", ctypes.c_float), ("expand_bytes", ctypes.c_int64),
+                ("launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libsnp_gb300.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1104_1824_gb300.build.build() "
+                          "(the simulator has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    lib.snp_explore_opts_init.argtypes = [ctypes.POINTER(snp_explore_opts)]
+    lib.snp_explore_opts_init.restype = None
+    lib.snp_load_system.argtypes = [ctypes.POINTER(snp_system_desc), ctypes.POINTER(vp)]
+    lib.snp_free.argtypes = [vp]
+    lib.snp_step.argtypes = [vp, vp, i64, vp, ctypes.POINTER(u64)]
+    lib.snp_explore.argtypes = [vp, ctypes.POINTER(snp_explore_opts), ctypes.POINTER(i32), vp]
+    lib.snp_reachable.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
+    lib.snp_parents.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
+    lib.snp_depth_stats.argtypes = [vp, i32, ctypes.POINTER(snp_depth_info)]
+    lib.snp_last_error.restype = ctypes.c_char_p
+    lib.snp_last_error.argtypes = []
+    lib.snp_abi_version.restype = ctypes.c_int
+    for name in EXPORTS:
+        if name not in ("snp_explore_opts_init", "snp_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != SNP_OK:
+        raise SnpError(code, _lib.snp_last_error().decode())
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return 0
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr())
+    if isinstance(a, np.ndarray):
+        return int(a.ctypes.data)
+    return int(a)
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return 0
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+# --- functions named as in the C ABI ------------------------------------------------------
+
+def snp_abi_version() -> int:
+    return load_library().snp_abi_version()
+
+
+def snp_last_error() -> str:
+    return load_library().snp_last_error().decode()
+
+
+def snp_explore_opts_init() -> snp_explore_opts:
+    o = snp_explore_opts()
+    load_library().snp_explore_opts_init(ctypes.byref(o))
+    return o
+
+
+def snp_load_system(m, rule_neuron, rule_i, rule_j, M, c0) -> ctypes.c_void_p:
+    lib = load_library()
+    arrs = [np.ascontiguousarray(x, dtype=np.int32).reshape(-1) for x in (rule_neuron, rule_i, rule_j, M, c0)]
+    d = snp_system_desc(int(m), int(arrs[0].shape[0]), *[a.ctypes.data for a in arrs])
+    h = ctypes.c_void_p()
+    _check(lib.snp_load_system(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def snp_free(h) -> None:
+    load_library().snp_free(h)
+
+
+def snp_step(h, C, capacity: int, out) -> int:
+    psi = ctypes.c_uint64()
+    _check(load_library().snp_step(h, _ptr(C), int(capacity), _ptr(out), ctypes.byref(psi)))
+    return psi.value
+
+
+def snp_explore(h, opts: snp_explore_opts, truncated_flags: Optional[np.ndarray] = None) -> int:
+    dr = ctypes.c_int32()
+    _check(load_library().snp_explore(h, ctypes.byref(opts), ctypes.byref(dr), _ptr(truncated_flags)))
+    return dr.value
+
+
+def snp_reachable(h, out, capacity: int, per_depth_new: Optional[np.ndarray] = None) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().snp_reachable(h, _ptr(out), int(capacity), ctypes.byref(n), _ptr(per_depth_new)))
+    return n.value
+
+
+def snp_reachable_count(h) -> int:
+    n = ctypes.c_int64()
+    rc = load_library().snp_reachable(h, None, 0, ctypes.byref(n), None)
+    if rc not in (SNP_OK, SNP_E_BUFFER):
+        _check(rc)
+    return n.value
+
+
+def snp_parents(h, parent, index, capacity: int) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().snp_parents(h, _ptr(parent), _ptr(index), int(capacity), ctypes.byref(n)))
+    return n.value
+
+
+def snp_depth_stats(h, d: int) -> snp_depth_info:
+    info = snp_depth_info()
+    _check(load_library().snp_depth_stats(h, int(d), ctypes.byref(info)))
+    return info
+
+
+# --- convenience wrapper ------------------------------------------------------------------
+
+@dataclass
+class DepthStats:
+    new: int
+    parents: int
+    candidates: int
+    examined: int
+    truncated: int
+    chunks: int
+    ms: float
+    expand_ms: float
+    expand_bytes: int
+    launches: int
+
+
+class System:
+    """One loaded system (owns a library handle)."""
+
+    def __init__(self, system):
+        self.m = int(system.m)
+        self.R = int(system.R)
+        self.h = snp_load_system(self.m, system.rule_neuron, system.rule_i, system.rule_j, system.M, system.c0)
+        self.depth_reached = None
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            snp_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, C, capacity: Optional[int] = None) -> Tuple[np.ndarray, int]:
+        C = np.ascontiguousarray(C, dtype=np.int32)
+        if capacity is None:
+            psi = snp_step(self.h, C, 0, None)
+            capacity = min(psi, 1 << 22)
+        out = np.zeros((max(int(capacity), 1), self.m), dtype=np.int32)
+        psi = snp_step(self.h, C, int(capacity), out)
+        return out[: min(psi, int(capacity))], psi
+
+    def explore(self, depth: int, cap: int = 0, budget: int = 0, transition: int = SNP_T_SPARSE_I32,
+                max_expand: int = -1, record_parents: bool = False, chunk: int = 0, stream=None,
+                kernel_timing: bool = False) -> int:
+        o = snp_explore_opts_init()
+        o.depth = int(depth)
+        o.transition = int(transition)
+        o.frontier_cap = int(cap)
+        o.candidate_budget = int(budget)
+        o.max_expand_value = int(max_expand)
+        o.record_parents = 1 if record_parents else 0
+        o.chunk = int(chunk)
+        o.stream = _stream_handle(stream)
+        o.kernel_timing = 1 if kernel_timing else 0
+        self.truncated = np.zeros(int(depth) + 1, dtype=np.int32)
+        self.depth_reached = snp_explore(self.h, o, self.truncated)
+        return self.depth_reached
+
+    def count(self) -> int:
+        return snp_reachable_count(self.h)
+
+    def reachable(self) -> np.ndarray:
+        n = self.count()
+        out = np.zeros((n, self.m), dtype=np.int32)
+        snp_reachable(self.h, out, n)
+        return out
+
+    def per_depth_new(self) -> List[int]:
+        pdn = np.zeros(self.depth_reached + 1, dtype=np.int64)
+        n = ctypes.c_int64()
+        rc = load_library().snp_reachable(self.h, None, 0, ctypes.byref(n), _ptr(pdn))
+        if rc not in (SNP_OK, SNP_E_BUFFER):
+            _check(rc)
+        return [int(x) for x in pdn]
+
+    def depth_stats(self) -> List[DepthStats]:
+        out = []
+        d = 0
+        while True:
+            info = snp_depth_info()
+            if load_library().snp_depth_stats(self.h, d, ctypes.byref(info)) != SNP_OK:
+                break
+            out.append(DepthStats(info.new_configs, info.parents, info.candidates, info.examined, info.truncated,
+                                  info.chunks, info.ms, info.expand_ms, info.expand_bytes, info.launches))
+            d += 1
+        return out
+
+    def parents(self) -> Tuple[np.ndarray, np.ndarray]:
+        n = self.count()
+        par = np.zeros(n, dtype=np.int64)
+        idx = np.zeros(n, dtype=np.uint64)
+        snp_parents(self.h, par, idx, n)
+        return par, idx
+

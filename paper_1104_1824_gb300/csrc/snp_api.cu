@@ -1,0 +1,654 @@
+// C ABI of the simulator (include/snp.h): handles, validation, device memory
+// and the depth / chunk loop of the breadth-first exploration (Algorithm 1).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "snp.h"
+#include "snp_kernels.cuh"
+
+using namespace snp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(x)                                                                                    \
+  do {                                                                                           \
+    cudaError_t e_ = (x);                                                                        \
+    if (e_ != cudaSuccess) {                                                                     \
+      if (e_ == cudaErrorMemoryAllocation) {                                                     \
+        cudaGetLastError();                                                                      \
+        return fail(SNP_E_NOMEM, "%s: %s", #x, cudaGetErrorString(e_));                          \
+      }                                                                                          \
+      return fail(SNP_E_CUDA, "%s (%s:%d): %s", #x, __FILE__, __LINE__, cudaGetErrorString(e_)); \
+    }                                                                                            \
+  } while (0)
+
+#define TRY(x)              \
+  do {                      \
+    int r_ = (x);           \
+    if (r_ != SNP_OK) return r_; \
+  } while (0)
+
+// A device allocation that grows on demand (contents are not preserved unless asked).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  int reserve(size_t want, cudaStream_t st = nullptr, bool keep = false) {
+    if (want <= bytes) return SNP_OK;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, want);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SNP_E_NOMEM, "cudaMalloc(%zu bytes): %s", want, cudaGetErrorString(e));
+    }
+    if (keep && p && bytes) {
+      e = cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        cudaFree(q);
+        return fail(SNP_E_CUDA, "grow copy: %s", cudaGetErrorString(e));
+      }
+    }
+    release();
+    p = q;
+    bytes = want;
+    return SNP_OK;
+  }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+// Pinned host words the depth loop reads back: chunk counters and one u64.
+struct PinnedState {
+  ChunkState* h = nullptr;
+  uint64_t* u64 = nullptr;
+  PinnedState() {
+    void* p = nullptr;
+    if (cudaMallocHost(&p, 256) == cudaSuccess) {
+      h = static_cast<ChunkState*>(p);
+      u64 = reinterpret_cast<uint64_t*>(static_cast<char*>(p) + 128);
+    }
+  }
+  ~PinnedState() {
+    if (h) cudaFreeHost(h);
+  }
+};
+
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+constexpr int kWarpsPerBlock = 4;
+constexpr int kThreads = kWarpsPerBlock * 32;
+
+}  // namespace
+
+struct snp_system {
+  int device = 0;
+  int32_t m = 0, R = 0, K = 1;
+  int32_t max_abs_m = 0;
+  std::vector<int32_t> c0, M, rule_neuron, rule_i, rule_j, first_rule, gain;
+  std::vector<int4> rule;
+  std::vector<int2> csr;
+  // device copies of the system
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_M8;
+  // exploration state
+  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_psi, d_off, d_scan_tmp, d_st,
+      d_rec_parent, d_rec_index, d_tmp;
+  int64_t pool_rows = 0;  // capacity in rows
+  uint64_t nbuckets = 0;
+  uint64_t q_cap = 0;     // staging capacity in rows
+  int64_t psi_cap = 0;    // parents
+  int64_t rec_rows = 0;
+  PinnedState pin;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t evk[2] = {nullptr, nullptr};  // around the expand kernel
+  // results
+  bool explored = false;
+  bool have_parents = false;
+  int64_t n_rows = 0;
+  int32_t depth_reached = 0;
+  std::vector<snp_depth_info> stats;
+
+  DevSys dev() const {
+    DevSys s;
+    s.m = m;
+    s.R = R;
+    s.K = K;
+    s.first_rule = d_first_rule.as<int32_t>();
+    s.rule = d_rule.as<int4>();
+    s.csr = d_csr.as<int2>();
+    s.gain = d_gain.as<int32_t>();
+    return s;
+  }
+  DevTable table() const { return DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }
+};
+
+namespace {
+
+int grid_for(int64_t work_items, int per_block, int max_blocks) {
+  int64_t b = (work_items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+int sm_count(int device) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+  return n > 0 ? n : 1;
+}
+
+size_t claim_smem(int m) { return (size_t)kWarpsPerBlock * 3 * m * sizeof(int32_t); }
+
+int check_device_errors(snp_system* h, cudaStream_t st, const char* where) {
+  CK(cudaMemcpyAsync(h->pin.h, h->d_st.p, sizeof(ChunkState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const uint32_t e = h->pin.h->error;
+  if (!e) return SNP_OK;
+  if (e & kErrOverflow) return fail(SNP_E_OVERFLOW, "%s: a spike count could leave the int32 range", where);
+  if (e & kErrTimeout) return fail(SNP_E_TIMEOUT, "%s: bounded wait for a hash slot ran out", where);
+  return fail(SNP_E_INTERNAL, "%s: device consistency check failed (bits 0x%x)", where, e);
+}
+
+// Staging and first-occurrence buffers for chunks of up to q candidates
+// (grow only; a fresh first-occurrence bitmap starts cleared).
+int ensure_chunk_buffers(snp_system* h, uint64_t q, cudaStream_t st) {
+  if (h->q_cap >= q) return SNP_OK;
+  q = std::max<uint64_t>(q, std::min<uint64_t>(h->q_cap * 2, 1ull << 30));
+  const uint64_t words = q / 32 + 1;
+  TRY(h->d_staging.reserve(sizeof(int32_t) * (size_t)h->m * q));
+  TRY(h->d_gmin.reserve(sizeof(uint32_t) * q));
+  TRY(h->d_slot_of.reserve(sizeof(uint32_t) * q));
+  TRY(h->d_srow.reserve(sizeof(uint32_t) * q));
+  TRY(h->d_bits.reserve(sizeof(uint32_t) * words));
+  TRY(h->d_wbase.reserve(sizeof(uint32_t) * words));
+  TRY(h->d_scan_tmp.reserve(scan_temp_bytes((int64_t)words, 4)));
+  CK(cudaMemsetAsync(h->d_bits.p, 0, sizeof(uint32_t) * words, st));
+  h->q_cap = q;
+  return SNP_OK;
+}
+
+// Clears the table and inserts rows [0, n) of the pool.
+int rebuild_table(snp_system* h, uint64_t nbuckets, cudaStream_t st) {
+  TRY(h->d_slots.reserve(nbuckets * kBucket * sizeof(unsigned long long)));
+  h->nbuckets = nbuckets;
+  const uint64_t nslots = nbuckets * kBucket;
+  k_fill_u64<<<grid_for((int64_t)nslots, 256, 152 * 32), 256, 0, st>>>(h->d_slots.as<unsigned long long>(), nslots,
+                                                                       kEmpty);
+  CK(cudaGetLastError());
+  if (h->n_rows > 0) {
+    k_insert_rows<<<grid_for(h->n_rows, kWarpsPerBlock, 152 * 64), kThreads, 0, st>>>(
+        h->dev(), h->d_pool.as<int32_t>(), 0, h->n_rows, h->table(), h->d_st.as<ChunkState>());
+    CK(cudaGetLastError());
+  }
+  return SNP_OK;
+}
+
+int validate_desc(const snp_system_desc* d) {
+  if (!d) return fail(SNP_E_INVALID, "desc is NULL");
+  if (d->m < 1 || d->m > 1024) return fail(SNP_E_INVALID, "m = %d outside [1, 1024]", d->m);
+  if (d->R < 1) return fail(SNP_E_INVALID, "R = %d < 1", d->R);
+  if (!d->rule_neuron || !d->rule_i || !d->rule_j || !d->M || !d->c0)
+    return fail(SNP_E_INVALID, "NULL array in desc");
+  int per = 0;
+  for (int r = 0; r < d->R; ++r) {
+    const int n = d->rule_neuron[r];
+    if (n < 0 || n >= d->m) return fail(SNP_E_INVALID, "rule %d: neuron %d outside [0, m)", r, n);
+    if (r > 0 && n < d->rule_neuron[r - 1])
+      return fail(SNP_E_INVALID, "rule %d: rules must be grouped by neuron in increasing order", r);
+    per = (r > 0 && n == d->rule_neuron[r - 1]) ? per + 1 : 1;
+    if (per > 32) return fail(SNP_E_INVALID, "neuron %d has more than 32 rules", n);
+    if (d->rule_i[r] < 0 || d->rule_j[r] < 0)
+      return fail(SNP_E_INVALID, "rule %d: regex a^%d(a^%d)* needs i, j >= 0", r, d->rule_i[r], d->rule_j[r]);
+    for (int j = 0; j < d->m; ++j) {
+      const int32_t v = d->M[(size_t)r * d->m + j];
+      if (j == n && v > -1) return fail(SNP_E_INVALID, "rule %d: M[%d][%d] = %d must be -c with c >= 1", r, r, j, v);
+      if (j != n && v < 0) return fail(SNP_E_INVALID, "rule %d: M[%d][%d] = %d must be >= 0", r, r, j, v);
+    }
+  }
+  for (int j = 0; j < d->m; ++j)
+    if (d->c0[j] < 0) return fail(SNP_E_INVALID, "c0[%d] = %d < 0", j, d->c0[j]);
+  return SNP_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" {
+
+void snp_explore_opts_init(snp_explore_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->depth = 1;
+  o->transition = SNP_T_SPARSE_I32;
+  o->frontier_cap = 0;
+  o->candidate_budget = 0;
+  o->max_expand_value = -1;
+  o->record_parents = 0;
+  o->chunk = 0;
+  o->stream = nullptr;
+}
+
+const char* snp_last_error(void) { return g_err.c_str(); }
+
+int snp_abi_version(void) { return SNP_ABI_VERSION; }
+
+int snp_load_system(const snp_system_desc* d, snp_handle* out) {
+  g_err.clear();
+  if (!out) return fail(SNP_E_INVALID, "out is NULL");
+  *out = nullptr;
+  TRY(validate_desc(d));
+  snp_system* h = new (std::nothrow) snp_system;
+  if (!h) return fail(SNP_E_NOMEM, "host allocation failed");
+  CK(cudaGetDevice(&h->device));
+  const int m = d->m, R = d->R;
+  h->m = m;
+  h->R = R;
+  h->K = (m + 31) / 32;
+  h->c0.assign(d->c0, d->c0 + m);
+  h->M.assign(d->M, d->M + (size_t)R * m);
+  h->rule_neuron.assign(d->rule_neuron, d->rule_neuron + R);
+  h->rule_i.assign(d->rule_i, d->rule_i + R);
+  h->rule_j.assign(d->rule_j, d->rule_j + R);
+  h->first_rule.assign(m + 1, 0);
+  for (int r = 0; r < R; ++r) h->first_rule[d->rule_neuron[r] + 1]++;
+  for (int n = 0; n < m; ++n) h->first_rule[n + 1] += h->first_rule[n];
+  // M_Pi's nonzeros, rule by rule (Definition 2: -c on the own neuron, +p on synapse targets).
+  h->rule.resize(R + 1);
+  for (int r = 0; r < R; ++r) {
+    const int32_t* row = &h->M[(size_t)r * m];
+    h->rule[r] = make_int4(d->rule_i[r], d->rule_j[r], -row[d->rule_neuron[r]], (int)h->csr.size());
+    for (int j = 0; j < m; ++j) {
+      if (row[j] != 0) h->csr.push_back(make_int2(j, row[j]));
+      h->max_abs_m = std::max(h->max_abs_m, std::abs(row[j]));
+    }
+  }
+  h->rule[R] = make_int4(0, 0, 0, (int)h->csr.size());
+  // gain[j]: at most one rule per neuron fires, so column j grows by at most
+  // the sum over neurons of their largest positive entry in column j.
+  std::vector<int64_t> g(m, 0);
+  for (int n = 0; n < m; ++n)
+    for (int j = 0; j < m; ++j) {
+      int32_t best = 0;
+      for (int r = h->first_rule[n]; r < h->first_rule[n + 1]; ++r) best = std::max(best, h->M[(size_t)r * m + j]);
+      g[j] += best;
+    }
+  h->gain.resize(m);
+  for (int j = 0; j < m; ++j) h->gain[j] = (int32_t)std::min<int64_t>(g[j], INT32_MAX);
+  int rc = SNP_OK;
+  auto up = [&](DevBuf& b, const void* src, size_t bytes) -> int {
+    if ((rc = b.reserve(std::max<size_t>(bytes, 16))) != SNP_OK) return rc;
+    CK(cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice));
+    return SNP_OK;
+  };
+  if ((rc = up(h->d_first_rule, h->first_rule.data(), sizeof(int32_t) * (m + 1))) ||
+      (rc = up(h->d_rule, h->rule.data(), sizeof(int4) * (R + 1))) ||
+      (rc = up(h->d_csr, h->csr.data(), sizeof(int2) * std::max<size_t>(h->csr.size(), 1))) ||
+      (rc = up(h->d_gain, h->gain.data(), sizeof(int32_t) * m)) ||
+      (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
+    delete h;
+    return rc;
+  }
+  if (!h->pin.h) {
+    delete h;
+    return fail(SNP_E_NOMEM, "pinned host allocation failed");
+  }
+  CK(cudaEventCreate(&h->ev[0]));
+  CK(cudaEventCreate(&h->ev[1]));
+  CK(cudaEventCreate(&h->evk[0]));
+  CK(cudaEventCreate(&h->evk[1]));
+  *out = h;
+  return SNP_OK;
+}
+
+int snp_free(snp_handle h) {
+  if (!h) return SNP_OK;
+  cudaSetDevice(h->device);
+  for (auto& e : h->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->evk)
+    if (e) cudaEventDestroy(e);
+  delete h;
+  return SNP_OK;
+}
+
+int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uint64_t* psi) {
+  g_err.clear();
+  if (!h || !C || !psi || capacity < 0 || (capacity > 0 && !out)) return fail(SNP_E_INVALID, "bad arguments");
+  CK(cudaSetDevice(h->device));
+  const int m = h->m;
+  std::vector<int32_t> c(m);
+  CK(cudaMemcpy(c.data(), C, sizeof(int32_t) * m, cudaMemcpyDefault));
+  for (int j = 0; j < m; ++j) {
+    if (c[j] < 0) return fail(SNP_E_INVALID, "C[%d] = %d < 0", j, c[j]);
+    if (c[j] > INT32_MAX - h->gain[j]) return fail(SNP_E_OVERFLOW, "C[%d] = %d: a child could leave int32", j, c[j]);
+  }
+  TRY(h->d_tmp.reserve(sizeof(int32_t) * m + 64));
+  int32_t* dC = h->d_tmp.as<int32_t>();
+  uint64_t* dpsi = reinterpret_cast<uint64_t*>(h->d_tmp.as<char>() + ((sizeof(int32_t) * m + 15) / 16) * 16);
+  CK(cudaMemcpy(dC, c.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
+  CK(cudaMemset(h->d_st.p, 0, sizeof(ChunkState)));
+  k_psi<<<1, kThreads, (size_t)kWarpsPerBlock * 2 * m * sizeof(int32_t)>>>(h->dev(), dC, 1, -1, dpsi,
+                                                                          h->d_st.as<ChunkState>());
+  CK(cudaGetLastError());
+  uint64_t ps = 0;
+  CK(cudaMemcpy(&ps, dpsi, sizeof ps, cudaMemcpyDeviceToHost));
+  *psi = ps;
+  const uint64_t n = std::min<uint64_t>(ps, (uint64_t)capacity);
+  if (n == 0) return SNP_OK;
+  int32_t* dst = out;
+  DevBuf tmp;
+  const bool dev_out = is_device_ptr(out);
+  if (!dev_out) {
+    TRY(tmp.reserve(sizeof(int32_t) * m * n));
+    dst = tmp.as<int32_t>();
+  }
+  const int blocks = grid_for((int64_t)n, kWarpsPerBlock, sm_count(h->device) * 8);
+  k_step_children<<<blocks, kThreads, claim_smem(m)>>>(h->dev(), dC, n, dst);
+  CK(cudaGetLastError());
+  if (!dev_out) CK(cudaMemcpy(out, dst, sizeof(int32_t) * m * n, cudaMemcpyDeviceToHost));
+  CK(cudaDeviceSynchronize());
+  return SNP_OK;
+}
+
+int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags) {
+  g_err.clear();
+  if (!h || !o) return fail(SNP_E_INVALID, "bad arguments");
+  if (o->depth < 0) return fail(SNP_E_INVALID, "depth = %d < 0", o->depth);
+  if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_I8)
+    return fail(SNP_E_INVALID, "unknown transition %d", o->transition);
+  if (o->transition == SNP_T_TC_I8 && h->max_abs_m > 127)
+    return fail(SNP_E_RANGE, "int8 transition refused: |M_Pi| reaches %d > 127", h->max_abs_m);
+  CK(cudaSetDevice(h->device));
+  cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+  h->explored = false;
+  h->have_parents = false;
+  h->stats.clear();
+  h->depth_reached = 0;
+  const int m = h->m;
+  const int nsm = sm_count(h->device);
+  const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
+  const int64_t budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
+  if (o->transition == SNP_T_TC_I8) return fail(SNP_E_INVALID, "int8 tensor-core transition not built");
+
+  // Chunk size bound: staging of at most ~512 MiB.
+  uint64_t qmax = o->chunk > 0 ? (uint64_t)o->chunk
+                               : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 29) / (4ull * m)));
+  qmax = std::min<uint64_t>(qmax, 1ull << 30);
+  // Pool: exact when capped, growing otherwise.
+  int64_t rows_plan = 1 << 12;
+  if (cap > 0) {
+    const long double want = 1.0L + (long double)o->depth * (long double)cap;
+    rows_plan = want > 2.0e9L ? (int64_t)2000000000 : (int64_t)want;
+  }
+  if (budget > 0 && cap == 0) {
+    const long double want = 1.0L + (long double)o->depth * (long double)budget;
+    if (want < 2.0e9L) rows_plan = std::max<int64_t>(rows_plan, std::min<int64_t>((int64_t)want, 1 << 20));
+  }
+  if (h->pool_rows < rows_plan) {
+    TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * rows_plan));
+    h->pool_rows = rows_plan;
+  }
+  if (o->record_parents) {
+    TRY(h->d_rec_parent.reserve(sizeof(int64_t) * h->pool_rows));
+    TRY(h->d_rec_index.reserve(sizeof(uint64_t) * h->pool_rows));
+    h->rec_rows = h->pool_rows;
+  }
+  TRY(ensure_chunk_buffers(h, std::min<uint64_t>(qmax, 1 << 16), st));
+
+  // Root level: C0.
+  h->n_rows = 1;
+  CK(cudaMemcpyAsync(h->d_pool.p, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+  if (o->record_parents) {
+    const int64_t rp = -1;
+    const uint64_t ri = 0;
+    CK(cudaMemcpyAsync(h->d_rec_parent.p, &rp, sizeof rp, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(h->d_rec_index.p, &ri, sizeof ri, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
+  {
+    const uint64_t want =
+        (uint64_t)((long double)(rows_plan + (int64_t)std::min<uint64_t>(qmax, 1 << 16)) * 4.0L / 3.0L / kBucket) + 1;
+    TRY(rebuild_table(h, pow2_at_least(want), st));
+  }
+  snp_depth_info s0;
+  std::memset(&s0, 0, sizeof s0);
+  s0.new_configs = 1;
+  h->stats.push_back(s0);
+  int64_t level_lo = 0, level_hi = 1;
+  int64_t tombs = 0;
+  double rate = 1.0;  // new configurations per candidate, for chunk sizing
+
+  for (int d = 1; d <= o->depth; ++d) {
+    snp_depth_info sd;
+    std::memset(&sd, 0, sizeof sd);
+    const int64_t P = level_hi - level_lo;
+    sd.parents = P;
+    CK(cudaEventRecord(h->ev[0], st));
+    if (h->psi_cap < P + 1) {
+      TRY(h->d_psi.reserve(sizeof(uint64_t) * (P + 1)));
+      TRY(h->d_off.reserve(sizeof(uint64_t) * (P + 1)));
+      TRY(h->d_scan_tmp.reserve(scan_temp_bytes(P + 1, 8)));
+      h->psi_cap = P + 1;
+    }
+    const int32_t* parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
+    CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
+    CK(cudaMemsetAsync(h->d_psi.as<uint64_t>() + P, 0, sizeof(uint64_t), st));
+    k_psi<<<grid_for(P, kWarpsPerBlock, nsm * 16), kThreads, (size_t)kWarpsPerBlock * 2 * m * sizeof(int32_t), st>>>(
+        h->dev(), parents, P, o->max_expand_value, h->d_psi.as<uint64_t>(), h->d_st.as<ChunkState>());
+    CK(cudaGetLastError());
+    sd.launches += 1 + scan_u64_sat(h->d_psi.as<uint64_t>(), h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
+    CK(cudaGetLastError());
+    uint64_t total = 0;
+    CK(cudaMemcpyAsync(h->pin.u64, h->d_off.as<uint64_t>() + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    TRY(check_device_errors(h, st, "applicability scan"));
+    total = *h->pin.u64;
+    sd.candidates = total;
+    const uint64_t T = budget > 0 ? std::min<uint64_t>(total, (uint64_t)budget) : total;
+    uint64_t remaining = cap > 0 ? (uint64_t)cap : ~0ull;
+    uint64_t g0 = 0, examined = 0;
+    int64_t nnew = 0;
+    bool capped = false;
+    while (g0 < T && !capped) {
+      uint64_t Q = std::min<uint64_t>(T - g0, qmax);
+      if (o->chunk <= 0 && cap > 0) {
+        const double want = (double)remaining / std::max(rate, 1.0 / 1024.0) * 1.25 + 4096.0;
+        if (want < (double)Q) Q = std::max<uint64_t>((uint64_t)want, std::min<uint64_t>(T - g0, 1 << 16));
+      }
+      // Room for every candidate of the chunk being new.
+      const uint64_t may_add = std::min<uint64_t>(Q, remaining);
+      if ((uint64_t)h->n_rows + may_add > (uint64_t)h->pool_rows) {
+        if ((uint64_t)h->n_rows + may_add > 0x7FFFFFF0ull) return fail(SNP_E_NOMEM, "more than 2^31 configurations");
+        const int64_t want = std::max<int64_t>(h->pool_rows * 2, h->n_rows + (int64_t)may_add);
+        TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
+        h->pool_rows = want;
+        parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
+        if (o->record_parents) {
+          TRY(h->d_rec_parent.reserve(sizeof(int64_t) * want, st, true));
+          TRY(h->d_rec_index.reserve(sizeof(uint64_t) * want, st, true));
+          h->rec_rows = want;
+        }
+      }
+      const uint64_t nslots = h->nbuckets * kBucket;
+      if ((long double)(h->n_rows + tombs) + (long double)Q > 0.75L * (long double)nslots) {
+        uint64_t nb = h->nbuckets;
+        while ((long double)(h->n_rows + Q) > 0.5L * (long double)(nb * kBucket)) nb *= 2;
+        TRY(rebuild_table(h, nb, st));
+        tombs = 0;
+      }
+      TRY(ensure_chunk_buffers(h, Q, st));
+      CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
+      {
+        ClaimArgs a;
+        a.sys = h->dev();
+        a.parents = parents;
+        a.off = h->d_off.as<uint64_t>();
+        a.P = P;
+        a.g0 = g0;
+        a.Q = (uint32_t)Q;
+        a.run = 32;
+        a.table = h->table();
+        a.pool = h->d_pool.as<int32_t>();
+        a.staging = h->d_staging.as<int32_t>();
+        a.gmin = h->d_gmin.as<uint32_t>();
+        a.slot_of = h->d_slot_of.as<uint32_t>();
+        a.st = h->d_st.as<ChunkState>();
+        const int blocks = grid_for((int64_t)((Q + a.run - 1) / a.run), kWarpsPerBlock, nsm * 16);
+        if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
+        k_claim<<<blocks, kThreads, claim_smem(m), st>>>(a);
+        CK(cudaGetLastError());
+        if (o->kernel_timing) CK(cudaEventRecord(h->evk[1], st));
+        sd.launches += 1;
+      }
+      const uint32_t nwords = (uint32_t)((Q + 31) / 32);
+      k_mark<<<grid_for((int64_t)Q, 256, nsm * 8), 256, 0, st>>>(h->d_gmin.as<uint32_t>(), h->d_bits.as<uint32_t>(),
+                                                                   h->d_srow.as<uint32_t>(), (uint32_t)Q,
+                                                                   h->d_st.as<ChunkState>());
+      launch_popc(h->d_bits.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, st);
+      sd.launches += 2 + scan_u32(h->d_wbase.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, h->d_scan_tmp.p, st);
+      CommitArgs c;
+      c.sys = h->dev();
+      c.nwords = nwords;
+      c.bits = h->d_bits.as<uint32_t>();
+      c.wbase = h->d_wbase.as<uint32_t>();
+      c.srow = h->d_srow.as<uint32_t>();
+      c.slot_of = h->d_slot_of.as<uint32_t>();
+      c.staging = h->d_staging.as<int32_t>();
+      c.table = h->table();
+      c.pool = h->d_pool.as<int32_t>();
+      c.row_base = h->n_rows;
+      c.remaining = remaining;
+      c.rec_parent = o->record_parents ? h->d_rec_parent.as<int64_t>() : nullptr;
+      c.rec_index = o->record_parents ? h->d_rec_index.as<uint64_t>() : nullptr;
+      c.off = h->d_off.as<uint64_t>();
+      c.P = P;
+      c.parent_base = level_lo;
+      c.g0 = g0;
+      c.st = h->d_st.as<ChunkState>();
+      k_commit<<<grid_for(nwords, kWarpsPerBlock, nsm * 16), kThreads, 0, st>>>(c);
+      CK(cudaGetLastError());
+      k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_bits.as<uint32_t>(), nwords);
+      CK(cudaGetLastError());
+      sd.launches += 2;
+      TRY(check_device_errors(h, st, "expand/claim/commit"));
+      const ChunkState cs = *h->pin.h;
+      if (o->kernel_timing) {
+        float kms = 0.f;
+        CK(cudaEventElapsedTime(&kms, h->evk[0], h->evk[1]));
+        sd.expand_ms += kms;
+      }
+      {
+        // algorithmic bytes of the expand kernel (include/snp.h, snp_depth_info)
+        const int64_t row = 4ll * m;
+        const int64_t dups = (int64_t)Q - (int64_t)cs.n_alloc;
+        const int64_t nparents = (int64_t)(cs.p_last - cs.p_first + 1);
+        sd.expand_bytes += (int64_t)Q * 8 + dups * row + (int64_t)cs.n_alloc * (row + 8) + nparents * row;
+      }
+      const uint64_t acc = std::min<uint64_t>(cs.n_alloc, remaining);
+      tombs += (int64_t)(cs.n_alloc - acc);
+      nnew += (int64_t)acc;
+      h->n_rows += (int64_t)acc;
+      if (remaining != ~0ull) remaining -= acc;
+      if (cs.capped) {
+        examined = g0 + cs.last_lid + 1;
+        capped = true;
+      } else {
+        examined = g0 + Q;
+      }
+      rate = std::max(1e-6, (double)cs.n_alloc / (double)Q);
+      g0 += Q;
+      sd.chunks += 1;
+    }
+    CK(cudaEventRecord(h->ev[1], st));
+    CK(cudaEventSynchronize(h->ev[1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+    sd.ms = ms;
+    sd.new_configs = nnew;
+    sd.examined = (int64_t)examined;
+    sd.truncated = examined < total ? 1 : 0;
+    h->stats.push_back(sd);
+    if (nnew == 0) break;
+    h->depth_reached = d;
+    level_lo = level_hi;
+    level_hi = h->n_rows;
+  }
+  h->explored = true;
+  h->have_parents = o->record_parents != 0;
+  if (depth_reached) *depth_reached = h->depth_reached;
+  if (truncated_flags)
+    for (int d = 0; d <= o->depth; ++d)
+      truncated_flags[d] = d < (int)h->stats.size() ? h->stats[d].truncated : 0;
+  return SNP_OK;
+}
+
+int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int64_t* per_depth_new) {
+  g_err.clear();
+  if (!h || !n) return fail(SNP_E_INVALID, "bad arguments");
+  if (!h->explored) return fail(SNP_E_STATE, "no exploration to report");
+  *n = h->n_rows;
+  if (per_depth_new)
+    for (int d = 0; d <= h->depth_reached; ++d) per_depth_new[d] = h->stats[d].new_configs;
+  if (capacity < h->n_rows) return fail(SNP_E_BUFFER, "capacity %lld < %lld rows", (long long)capacity, (long long)h->n_rows);
+  if (!out) return fail(SNP_E_INVALID, "out is NULL");
+  CK(cudaSetDevice(h->device));
+  CK(cudaMemcpy(out, h->d_pool.p, sizeof(int32_t) * (size_t)h->m * h->n_rows, cudaMemcpyDefault));
+  return SNP_OK;
+}
+
+int snp_parents(snp_handle h, int64_t* parent, uint64_t* index, int64_t capacity, int64_t* n) {
+  g_err.clear();
+  if (!h || !n) return fail(SNP_E_INVALID, "bad arguments");
+  if (!h->explored || !h->have_parents) return fail(SNP_E_STATE, "no parent records (set record_parents)");
+  *n = h->n_rows;
+  if (capacity < h->n_rows) return fail(SNP_E_BUFFER, "capacity %lld < %lld", (long long)capacity, (long long)h->n_rows);
+  CK(cudaSetDevice(h->device));
+  if (parent) CK(cudaMemcpy(parent, h->d_rec_parent.p, sizeof(int64_t) * h->n_rows, cudaMemcpyDefault));
+  if (index) CK(cudaMemcpy(index, h->d_rec_index.p, sizeof(uint64_t) * h->n_rows, cudaMemcpyDefault));
+  return SNP_OK;
+}
+
+int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out) {
+  g_err.clear();
+  if (!h || !out) return fail(SNP_E_INVALID, "bad arguments");
+  if (!h->explored) return fail(SNP_E_STATE, "no exploration");
+  if (d < 0 || d >= (int)h->stats.size()) return fail(SNP_E_INVALID, "depth %d outside [0, %d)", d, (int)h->stats.size());
+  *out = h->stats[d];
+  return SNP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Kernel entry points of the single-system BFS (declarations shared by the
+// launch code in snp_api.cu and the definitions in snp_kernels.cu).
+#pragma once
+
+#include "snp_device.cuh"
+
+namespace snp {
+
+struct ClaimArgs {
+  DevSys sys;
+  const int32_t* parents;     // frontier rows, contiguous [P x m]
+  const uint64_t* off;        // [P + 1] exclusive prefix sums of Psi (saturating)
+  int64_t P;
+  uint64_t g0;                // first candidate of the chunk
+  uint32_t Q;                 // candidates in the chunk
+  uint32_t run;               // consecutive candidates per warp task
+  DevTable table;
+  const int32_t* pool;        // committed configurations
+  int32_t* staging;           // [Q x m] configurations first claimed in this chunk
+  uint32_t* gmin;             // [Q] smallest chunk-local candidate index per staging row
+  uint32_t* slot_of;          // [Q] table slot per staging row
+  ChunkState* st;
+};
+
+struct CommitArgs {
+  DevSys sys;
+  uint32_t nwords;            // ceil(Q / 32)
+  const uint32_t* bits;       // [nwords] first-occurrence bitmap over chunk-local indices
+  const uint32_t* wbase;      // [nwords] exclusive prefix of popcounts
+  const uint32_t* srow;       // [Q] staging row of each first occurrence
+  const uint32_t* slot_of;
+  const int32_t* staging;
+  DevTable table;
+  int32_t* pool;
+  int64_t row_base;           // pool row of rank 0
+  uint64_t remaining;         // how many more configurations the depth may accept
+  // parent records (optional)
+  int64_t* rec_parent;        // [rows] or nullptr
+  uint64_t* rec_index;
+  const uint64_t* off;
+  int64_t P;
+  int64_t parent_base;        // discovery index of frontier row 0
+  uint64_t g0;
+  ChunkState* st;
+};
+
+__global__ void k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi,
+                      ChunkState* st);
+__global__ void k_claim(ClaimArgs a);
+__global__ void k_mark(const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t Q, ChunkState* st);
+__global__ void k_commit(CommitArgs a);
+__global__ void k_clear_bits(uint32_t* bits, uint32_t nwords);
+__global__ void k_insert_rows(DevSys s, const int32_t* pool, int64_t r0, int64_t r1, DevTable t, ChunkState* st);
+__global__ void k_step_children(DevSys s, const int32_t* C, uint64_t n, int32_t* out);
+__global__ void k_fill_u64(unsigned long long* p, uint64_t n, unsigned long long v);
+
+// Device-wide exclusive scans (n elements, in -> out; "total" gets the sum).
+// Saturating for u64 (sums of Psi), plain for u32.
+size_t scan_temp_bytes(int64_t n, size_t elem);
+// Each returns the number of kernels it launched.
+int scan_u64_sat(const uint64_t* in, uint64_t* out, int64_t n, void* temp, cudaStream_t st);
+int scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t st);
+void launch_popc(const uint32_t* bits, uint32_t* cnt, uint32_t nwords, cudaStream_t st);
+
+}  // namespace snp

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer work: everything must match bit for bit -- the discovery-ordered
+configurations, the per-depth counts of new configurations and examined
+candidates, the sums of Psi and the truncation flags.
+"""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+import bruteforce as bf
+import oracle
+import snp_synth
+from conftest import GOLDEN, parse_configs, read_golden
+
+pytestmark = pytest.mark.gpu
+
+
+def digest(configs: np.ndarray) -> str:
+    return hashlib.sha256(np.ascontiguousarray(configs, dtype="<i4").tobytes()).hexdigest()
+
+
+def golden_digests():
+    with open(os.path.join(GOLDEN, "oracle_digests.json")) as f:
+        return json.load(f)
+
+
+def explore_both(gpu, system, depth, cap=0, budget=0, max_expand=-1, chunk=0, **kw):
+    s = gpu.System(system)
+    s.explore(depth, cap=cap, budget=budget, max_expand=max_expand, chunk=chunk, **kw)
+    e = oracle.Oracle(system).explore(depth, cap=cap, budget=budget, max_expand=max_expand)
+    return s, e
+
+
+def assert_same(s, e):
+    got = s.reachable()
+    assert got.shape == e.configs.shape
+    assert (got == e.configs).all()
+    stats = s.depth_stats()
+    assert len(stats) == len(e.depths)
+    for d, (a, b) in enumerate(zip(stats, e.depths)):
+        assert a.new == b.new, d
+        if d > 0:
+            assert a.examined == b.examined, d
+            assert a.candidates == b.candidates, d
+            assert a.truncated == b.truncated, d
+    assert s.depth_reached == e.depth_reached
+    assert s.per_depth_new() == [d.new for d in e.depths[: e.depth_reached + 1]]
+
+
+# --- the paper's example ---
+
+def test_paper_example_depth10(gpu):
+    s, e = explore_both(gpu, snp_synth.paper_example(), 10)
+    assert_same(s, e)
+    assert s.per_depth_new() == [1, 2, 4, 6, 6, 6, 5, 5, 5, 5, 5]
+
+
+def test_paper_replay_reproduces_allgenck(gpu):
+    g = read_golden("paper_run.txt")
+    s, e = explore_both(gpu, snp_synth.paper_example(), 1000, max_expand=9)
+    assert_same(s, e)
+    assert ["-".join(str(int(x)) for x in r) for r in s.reachable()] == g["allGenCk"].split()
+
+
+def test_paper_exact_reading(gpu):
+    s, e = explore_both(gpu, snp_synth.paper_example(exact=True), 100)
+    assert_same(s, e)
+    assert s.count() == 8
+
+
+def test_step_matches_oracle_and_paper(gpu):
+    paper = snp_synth.paper_example()
+    s = gpu.System(paper)
+    kids, psi = s.step([2, 1, 1])
+    assert psi == 2
+    assert ["-".join(str(int(x)) for x in r) for r in kids] == read_golden("paper_run.txt")["after_C0"].split()[1:]
+    rng = np.random.default_rng(3)
+    o = oracle.Oracle(paper)
+    for _ in range(50):
+        C = rng.integers(0, 12, size=3).astype(np.int32)
+        kids, psi = s.step(C)
+        assert psi == o.psi(C)
+        assert (kids == o.step(C)).all()
+
+
+def test_step_with_device_buffers(gpu):
+    import torch
+    system = snp_synth.random_64(1)
+    s = gpu.System(system)
+    o = oracle.Oracle(system)
+    C = torch.tensor(system.c0, dtype=torch.int32, device="cuda")
+    out = torch.zeros((5000, system.m), dtype=torch.int32, device="cuda")
+    psi = gpu.snp_step(s.h, C, 5000, out)
+    assert psi == o.psi(system.c0) == 147456
+    assert (out.cpu().numpy() == o.step(system.c0, cap=5000)).all()
+
+
+# --- small random systems, every truncation mode, several chunk sizes ---
+
+@pytest.mark.parametrize("cap,budget,chunk", [(0, 0, 0), (1, 0, 0), (3, 0, 1), (0, 7, 0), (5, 11, 3), (2, 1, 0),
+                                              (4, 0, 2)])
+def test_tiny_systems(gpu, cap, budget, chunk):
+    rng = np.random.default_rng(1000 + 7 * cap + 13 * budget + chunk)
+    for _ in range(30):
+        system = bf.tiny_system(rng, m_max=4, r_max=9)
+        s, e = explore_both(gpu, system, 5, cap=cap, budget=budget, chunk=chunk)
+        assert_same(s, e)
+
+
+@pytest.mark.parametrize("m", [1, 2, 31, 32, 33, 63, 64, 65, 100, 255, 256, 257, 511, 1024])
+def test_neuron_counts(gpu, m):
+    system = snp_synth.random_system(500 + m, m, (1, 4), (1, min(8, max(1, m - 1))), (0, 6), "sparse")
+    s, e = explore_both(gpu, system, 3, cap=300, budget=3000)
+    assert_same(s, e)
+
+
+def test_batch_style_systems(gpu):
+    for system in snp_synth.batch_systems(6):
+        s, e = explore_both(gpu, system, 4, cap=1 << 9, budget=1 << 13)
+        assert_same(s, e)
+
+
+# --- the 64-neuron workload ---
+
+@pytest.mark.parametrize("chunk", [0, 1000, 4097, 65536])
+def test_random64_small_all_chunkings(gpu, chunk):
+    g = golden_digests()["random64_seed1_small"]
+    system = snp_synth.random_64(1)
+    s = gpu.System(system)
+    p = g["params"]
+    s.explore(p["depth"], cap=p["cap"], budget=p["budget"], chunk=chunk)
+    got = s.reachable()
+    assert digest(got) == g["sha256"]
+    st = s.depth_stats()
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in st] == g["per_depth"]
+
+
+def test_random64_small_against_oracle_directly(gpu):
+    s, e = explore_both(gpu, snp_synth.random_64(1), 3, cap=1 << 12, budget=1 << 16)
+    assert_same(s, e)
+
+
+@pytest.mark.slow
+def test_random64_full_size(gpu):
+    """Depth 8, cap 2^20, budget 2^24 (the benchmark's launch configuration)."""
+    g = golden_digests()["random64_seed1_full"]
+    system = snp_synth.random_64(1)
+    s = gpu.System(system)
+    p = g["params"]
+    s.explore(p["depth"], cap=p["cap"], budget=p["budget"], record_parents=True)
+    got = s.reachable()
+    assert got.shape[0] == g["count"]
+    st = s.depth_stats()
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in st] == g["per_depth"]
+    assert digest(got) == g["sha256"]
+    # sampled: each configuration is its recorded parent's child at the recorded index
+    par, idx = s.parents()
+    o = oracle.Oracle(system)
+    rng = np.random.default_rng(0)
+    for k in rng.choice(got.shape[0] - 1, size=200, replace=False) + 1:
+        ch = o.child(got[par[k]], int(idx[k]))
+        assert ch is not None and (ch == got[k]).all()
+
+
+def test_dense1024_small(gpu):
+    g = golden_digests()["dense1024_seed3_small"]
+    system = snp_synth.dense_1024(3)
+    s = gpu.System(system)
+    p = g["params"]
+    s.explore(p["depth"], cap=p["cap"], budget=p["budget"])
+    st = s.depth_stats()
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in st] == g["per_depth"]
+    assert digest(s.reachable()) == g["sha256"]
+
+
+# --- parent records, streams, device outputs ---
+
+def test_parent_records(gpu):
+    system = snp_synth.random_64(2)
+    s = gpu.System(system)
+    s.explore(3, cap=5000, budget=80000, record_parents=True)
+    rows = s.reachable()
+    par, idx = s.parents()
+    assert par[0] == -1 and idx[0] == 0
+    o = oracle.Oracle(system)
+    for k in range(1, rows.shape[0], 97):
+        assert (o.child(rows[par[k]], int(idx[k])) == rows[k]).all()
+    # the parent of a depth-d configuration lies in depth d - 1
+    per = s.per_depth_new()
+    start = np.cumsum([0] + per)
+    for d in range(1, len(per)):
+        sl = slice(start[d], start[d + 1])
+        assert (par[sl] >= start[d - 1]).all() and (par[sl] < start[d]).all()
+
+
+def test_explore_on_a_side_stream_into_device_memory(gpu):
+    import torch
+    system = snp_synth.random_64(1)
+    s = gpu.System(system)
+    stream = torch.cuda.Stream()
+    s.explore(3, cap=1 << 12, budget=1 << 16, stream=stream)
+    n = s.count()
+    out = torch.empty((n, system.m), dtype=torch.int32, device="cuda")
+    gpu.snp_reachable(s.h, out, n)
+    e = oracle.Oracle(system).explore(3, cap=1 << 12, budget=1 << 16)
+    assert (out.cpu().numpy() == e.configs).all()
+
+
+def test_repeated_explores_reuse_the_handle(gpu):
+    system = snp_synth.random_64(1)
+    s = gpu.System(system)
+    e = oracle.Oracle(system).explore(2, cap=1 << 10, budget=1 << 14)
+    for cap in (1 << 10, 1 << 12, 1 << 10):
+        s.explore(2, cap=cap, budget=1 << 14)
+    assert (s.reachable() == e.configs).all()
+
+
+# --- edge cases and errors ---
+
+def test_depth_zero_and_quiet_system(gpu):
+    system = snp_synth.random_64(1)
+    s = gpu.System(system)
+    s.explore(0)
+    assert s.count() == 1 and (s.reachable()[0] == system.c0).all()
+    quiet = snp_synth.make_system(3, [0, 1], [5, 5], [0, 0], [1, 1], [1, 1], [[1], [2], []], [0, 0, 0])
+    s, e = explore_both(gpu, quiet, 5)
+    assert_same(s, e)
+    assert s.count() == 1 and s.depth_reached == 0
+
+
+def test_cap_one_and_budget_one(gpu):
+    system = snp_synth.random_64(3)
+    for cap, budget in [(1, 0), (0, 1), (1, 1)]:
+        s, e = explore_both(gpu, system, 4, cap=cap, budget=budget)
+        assert_same(s, e)
+
+
+def test_overflow_is_reported(gpu):
+    big = 2 ** 31 - 3
+    system = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 5], [[1], [0]], [big, big])
+    s = gpu.System(system)
+    with pytest.raises(gpu.SnpError) as ei:
+        s.explore(3)
+    assert ei.value.code == gpu.SNP_E_OVERFLOW
+    with pytest.raises(gpu.SnpError) as ei:
+        s.step(system.c0)
+    assert ei.value.code == gpu.SNP_E_OVERFLOW
+
+
+def test_state_and_buffer_errors(gpu):
+    s = gpu.System(snp_synth.paper_example())
+    with pytest.raises(gpu.SnpError) as ei:
+        gpu.snp_reachable(s.h, None, 0)
+    assert ei.value.code == gpu.SNP_E_STATE
+    s.explore(3)
+    out = np.zeros((2, 3), dtype=np.int32)
+    with pytest.raises(gpu.SnpError) as ei:
+        gpu.snp_reachable(s.h, out, 2)
+    assert ei.value.code == gpu.SNP_E_BUFFER
+    with pytest.raises(gpu.SnpError) as ei:
+        gpu.snp_parents(s.h, None, None, 100)
+    assert ei.value.code == gpu.SNP_E_STATE
