@@ -334,7 +334,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
     args = ap.parse_args()
+    if args.depth > 0:
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], depth=args.depth)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -194,7 +194,7 @@ int ensure_chunk_buffers(snp_system* h, uint64_t q, cudaStream_t st) {
   return SNP_OK;
 }
 
-// Clears the table and inserts rows [0, n) of the pool.
+// Clears the table and inserts rows [0, n) of the pool (2 launches).
 int rebuild_table(snp_system* h, uint64_t nbuckets, cudaStream_t st) {
   TRY(h->d_slots.reserve(nbuckets * kBucket * sizeof(unsigned long long)));
   h->nbuckets = nbuckets;
@@ -448,6 +448,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
   snp_depth_info s0;
   std::memset(&s0, 0, sizeof s0);
   s0.new_configs = 1;
+  s0.launches = 2;  // the table build above
   h->stats.push_back(s0);
   int64_t level_lo = 0, level_hi = 1;
   int64_t tombs = 0;
@@ -508,6 +509,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         uint64_t nb = h->nbuckets;
         while ((long double)(h->n_rows + Q) > 0.5L * (long double)(nb * kBucket)) nb *= 2;
         TRY(rebuild_table(h, nb, st));
+        sd.launches += 2;
         tombs = 0;
       }
       TRY(ensure_chunk_buffers(h, Q, st));
