@@ -189,6 +189,36 @@ int snp_parents(snp_handle h, int64_t* parent, uint64_t* index, int64_t capacity
  * exploration.  Errors: SNP_E_STATE, SNP_E_INVALID. */
 int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out);
 
+/* snp_explore without allocating memory: the paper has no counterpart; this
+ * is for callers that may not allocate device memory at the moment they need
+ * an exploration (a framework's caching allocator holds the free memory,
+ * contexts such as host callbacks where cudaMalloc may not be called, loops
+ * that must not block on the allocator).  It runs the same search as
+ * snp_explore and writes the same configurations in the same order, but
+ * allocates neither device nor host memory: the configurations go straight
+ * into the caller's device buffer out[capacity * m], which also serves as the
+ * working pool, and every other buffer comes from one fixed 64 MiB device
+ * array inside the library, held by every GPU that loads the library until
+ * the process exits.  All calls share that array and each leaves its contents
+ * behind; a call clears what must start empty, and calls whose work overlaps
+ * on the GPU (other streams or threads) race on it.  The first call on a
+ * device looks up the array's address; make that first call before any
+ * stream capture.
+ *  opts           as for snp_explore; transition must be SNP_T_SPARSE_I32
+ *                 and record_parents 0.  Uses opts->stream.
+ *  out            device memory, capacity rows of m int32.
+ *  capacity       1 <= capacity <= 2^20 configurations (the array's limit);
+ *                 larger values are refused with SNP_E_INVALID.
+ *  *n             configurations written (C0 first, discovery order).
+ *  depth_reached  (host, may be NULL) as for snp_explore.
+ *  per_depth_new  (host, [opts->depth + 1], may be NULL) new configurations
+ *                 per depth, index 0 being C0's level.
+ * The handle's own exploration state is not touched.  Errors: SNP_E_INVALID,
+ * SNP_E_BUFFER (capacity reached while candidates remain), SNP_E_OVERFLOW,
+ * SNP_E_TIMEOUT, SNP_E_INTERNAL, SNP_E_CUDA. */
+int snp_explore_static(snp_handle h, const snp_explore_opts* opts, int32_t* out, int64_t capacity, int64_t* n,
+                       int32_t* depth_reached, int64_t* per_depth_new);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char* snp_last_error(void);
 

@@ -41,7 +41,7 @@ ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOME
 
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
-           "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version"]
+           "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static"]
 
 
 class SnpError(RuntimeError):
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
     lib.snp_reachable.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
     lib.snp_parents.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
     lib.snp_depth_stats.argtypes = [vp, i32, ctypes.POINTER(snp_depth_info)]
+    lib.snp_explore_static.argtypes = [vp, ctypes.POINTER(snp_explore_opts), vp, i64, ctypes.POINTER(i64),
+                                       ctypes.POINTER(i32), vp]
     lib.snp_last_error.restype = ctypes.c_char_p
     lib.snp_last_error.argtypes = []
     lib.snp_abi_version.restype = ctypes.c_int
@@ -185,6 +187,17 @@ def snp_parents(h, parent, index, capacity: int) -> int:
     n = ctypes.c_int64()
     _check(load_library().snp_parents(h, _ptr(parent), _ptr(index), int(capacity), ctypes.byref(n)))
     return n.value
+
+
+def snp_explore_static(h, opts: snp_explore_opts, out, capacity: int,
+                       per_depth_new: Optional[np.ndarray] = None) -> Tuple[int, int]:
+    """Exploration into the caller's device buffer `out`, allocating nothing.
+    Returns (configurations written, depth reached)."""
+    n = ctypes.c_int64()
+    dr = ctypes.c_int32()
+    _check(load_library().snp_explore_static(h, ctypes.byref(opts), _ptr(out), int(capacity), ctypes.byref(n),
+                                             ctypes.byref(dr), _ptr(per_depth_new)))
+    return n.value, dr.value
 
 
 def snp_depth_stats(h, d: int) -> snp_depth_info:

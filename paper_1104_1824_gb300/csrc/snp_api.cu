@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -654,3 +655,241 @@ int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Exploration without allocation (snp_explore_static).
+//
+// Some callers cannot allocate device memory when they need an exploration:
+// code that runs while a framework's caching allocator owns all free device
+// memory, host callbacks and other contexts where cudaMalloc may not be
+// called, and latency-critical loops that must never block on the allocator.
+// For them, snp_explore_static takes the output buffer from the caller (it
+// doubles as the configuration pool) and carves every other buffer it needs
+// (hash table, staging rows, first-occurrence bitmap, Psi prefix sums, scan
+// temporaries, counters) out of one array compiled into this library.
+//
+// The array is fixed at kStaticScratchBytes; every GPU that loads the library
+// holds it until the process exits.  Calls share it and each call leaves its
+// contents behind: a call clears what must start empty (table, bitmap,
+// counters) before use, and two calls whose work overlaps on the GPU (other
+// streams, other threads) race on it.  The first call on a device looks up the
+// array's device address (cudaGetSymbolAddress) with that device current; make
+// that first call before any stream capture.
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = 64ull << 20;    // 64 MiB
+constexpr uint64_t kStaticSlots = 1ull << 21;           // hash slots (16 MiB)
+constexpr int64_t kStaticMaxRows = 1ll << 20;           // configurations per call
+constexpr size_t kStaticStagingBytes = 24ull << 20;     // rows claimed per pass
+constexpr int kStaticMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once).
+int static_scratch(int device, unsigned char** out) {
+  if (device < 0 || device >= kStaticMaxDevices) return fail(SNP_E_INVALID, "device %d out of range", device);
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(SNP_E_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+    g_static_addr[device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_static_addr[device]);
+  return SNP_OK;
+}
+
+struct StaticLayout {
+  ChunkState* st;
+  unsigned long long* slots;
+  uint64_t* psi;
+  uint64_t* off;
+  void* scan_tmp;
+  int32_t* staging;
+  uint32_t *gmin, *slot_of, *srow, *bits, *wbase;
+  uint64_t q;  // candidates per pass
+};
+
+// Carves the scratch array; every piece starts on a 256-byte boundary.
+bool static_layout(unsigned char* base, int m, StaticLayout* L) {
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base + at;
+    at += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  uint64_t q = std::min<uint64_t>(1ull << 16, kStaticStagingBytes / (4ull * m));
+  q &= ~31ull;
+  L->q = q;
+  L->st = reinterpret_cast<ChunkState*>(take(256));
+  L->slots = reinterpret_cast<unsigned long long*>(take(kStaticSlots * sizeof(unsigned long long)));
+  L->psi = reinterpret_cast<uint64_t*>(take((kStaticMaxRows + 1) * sizeof(uint64_t)));
+  L->off = reinterpret_cast<uint64_t*>(take((kStaticMaxRows + 1) * sizeof(uint64_t)));
+  L->scan_tmp = take(std::max(scan_temp_bytes(kStaticMaxRows + 1, 8), scan_temp_bytes((int64_t)q / 32 + 1, 4)));
+  L->staging = reinterpret_cast<int32_t*>(take(q * 4ull * m));
+  L->gmin = reinterpret_cast<uint32_t*>(take(q * 4));
+  L->slot_of = reinterpret_cast<uint32_t*>(take(q * 4));
+  L->srow = reinterpret_cast<uint32_t*>(take(q * 4));
+  L->bits = reinterpret_cast<uint32_t*>(take((q / 32 + 1) * 4));
+  L->wbase = reinterpret_cast<uint32_t*>(take((q / 32 + 1) * 4));
+  return at <= kStaticScratchBytes;
+}
+
+}  // namespace
+
+extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32_t* out, int64_t capacity,
+                                  int64_t* n, int32_t* depth_reached, int64_t* per_depth_new) {
+  g_err.clear();
+  if (!h || !o || !out || !n) return fail(SNP_E_INVALID, "bad arguments");
+  if (o->depth < 0) return fail(SNP_E_INVALID, "depth = %d < 0", o->depth);
+  if (o->transition != SNP_T_SPARSE_I32) return fail(SNP_E_INVALID, "only the sparse int32 transition runs here");
+  if (o->record_parents) return fail(SNP_E_INVALID, "parent records need allocation; use snp_explore");
+  if (capacity < 1) return fail(SNP_E_BUFFER, "capacity %lld < 1", (long long)capacity);
+  if (capacity > kStaticMaxRows)
+    return fail(SNP_E_INVALID, "capacity %lld exceeds the static scratch limit of %lld configurations",
+                (long long)capacity, (long long)kStaticMaxRows);
+  if (!is_device_ptr(out)) return fail(SNP_E_INVALID, "out must be device memory");
+  CK(cudaSetDevice(h->device));
+  unsigned char* base = nullptr;
+  TRY(static_scratch(h->device, &base));
+  StaticLayout L;
+  if (!static_layout(base, h->m, &L)) return fail(SNP_E_INTERNAL, "static scratch layout does not fit");
+  cudaStream_t st = static_cast<cudaStream_t>(o->stream);
+  const int m = h->m;
+  const int nsm = sm_count(h->device);
+  const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
+  const int64_t budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
+  const uint64_t qmax = o->chunk > 0 ? std::min<uint64_t>((uint64_t)o->chunk, L.q) : L.q;
+  const DevTable table{L.slots, kStaticSlots / kBucket - 1};
+  ChunkState* hst = h->pin.h;
+
+  // Start state: C0 in row 0 of out, an empty table holding C0, a clear bitmap.
+  CK(cudaMemcpyAsync(out, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
+  CK(cudaMemsetAsync(L.bits, 0, sizeof(uint32_t) * (L.q / 32 + 1), st));
+  auto clear_and_insert = [&](int64_t rows) -> int {
+    k_fill_u64<<<grid_for((int64_t)kStaticSlots, 256, nsm * 32), 256, 0, st>>>(L.slots, kStaticSlots, kEmpty);
+    CK(cudaGetLastError());
+    k_insert_rows<<<grid_for(rows, kWarpsPerBlock, nsm * 64), kThreads, 0, st>>>(h->dev(), out, 0, rows, table, L.st);
+    CK(cudaGetLastError());
+    return SNP_OK;
+  };
+  TRY(clear_and_insert(1));
+  int64_t n_rows = 1, level_lo = 0, level_hi = 1, tombs = 0;
+  int32_t reached = 0;
+  if (per_depth_new) {
+    per_depth_new[0] = 1;
+    for (int d = 1; d <= o->depth; ++d) per_depth_new[d] = 0;
+  }
+  double rate = 1.0;
+
+  for (int d = 1; d <= o->depth; ++d) {
+    const int64_t P = level_hi - level_lo;
+    const int32_t* parents = out + (size_t)level_lo * m;
+    CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
+    CK(cudaMemsetAsync(L.psi + P, 0, sizeof(uint64_t), st));
+    k_psi<<<grid_for(P, kWarpsPerBlock, nsm * 16), kThreads, (size_t)kWarpsPerBlock * 2 * m * sizeof(int32_t), st>>>(
+        h->dev(), parents, P, o->max_expand_value, L.psi, L.st);
+    CK(cudaGetLastError());
+    scan_u64_sat(L.psi, L.off, P + 1, L.scan_tmp, st);
+    CK(cudaMemcpyAsync(h->pin.u64, L.off + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hst, L.st, sizeof(ChunkState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hst->error & kErrOverflow) return fail(SNP_E_OVERFLOW, "a spike count could leave the int32 range");
+    if (hst->error) return fail(SNP_E_INTERNAL, "device consistency check failed (bits 0x%x)", hst->error);
+    const uint64_t total = *h->pin.u64;
+    const uint64_t T = budget > 0 ? std::min<uint64_t>(total, (uint64_t)budget) : total;
+    uint64_t remaining = cap > 0 ? (uint64_t)cap : ~0ull;
+    uint64_t g0 = 0;
+    int64_t nnew = 0;
+    bool capped = false;
+    while (g0 < T && !capped) {
+      uint64_t Q = std::min<uint64_t>(T - g0, qmax);
+      if (o->chunk <= 0 && cap > 0) {
+        const double want = (double)remaining / std::max(rate, 1.0 / 1024.0) * 1.25 + 4096.0;
+        if (want < (double)Q) Q = std::max<uint64_t>((uint64_t)want, std::min<uint64_t>(T - g0, 1 << 12));
+      }
+      // At most `room` more rows fit in out: the pass commits no more than that
+      // and fails if it found more new configurations than fit.
+      const uint64_t room = (uint64_t)(capacity - n_rows);
+      const uint64_t accept = std::min<uint64_t>(remaining, room);
+      const bool cap_limits = remaining <= room;  // the frontier cap, not the buffer, bounds this pass
+      if ((long double)(n_rows + tombs) + (long double)Q > 0.75L * (long double)kStaticSlots) {
+        TRY(clear_and_insert(n_rows));  // drops tombstones; n_rows + Q always fits
+        tombs = 0;
+      }
+      CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
+      ClaimArgs a;
+      a.sys = h->dev();
+      a.parents = parents;
+      a.off = L.off;
+      a.P = P;
+      a.g0 = g0;
+      a.Q = (uint32_t)Q;
+      a.run = 32;
+      a.table = table;
+      a.pool = out;
+      a.staging = L.staging;
+      a.gmin = L.gmin;
+      a.slot_of = L.slot_of;
+      a.st = L.st;
+      k_claim<<<grid_for((int64_t)((Q + a.run - 1) / a.run), kWarpsPerBlock, nsm * 16), kThreads, claim_smem(m), st>>>(a);
+      CK(cudaGetLastError());
+      const uint32_t nwords = (uint32_t)((Q + 31) / 32);
+      k_mark<<<grid_for((int64_t)Q, 256, nsm * 8), 256, 0, st>>>(L.gmin, L.bits, L.srow, (uint32_t)Q, L.st);
+      launch_popc(L.bits, L.wbase, nwords, st);
+      scan_u32(L.wbase, L.wbase, nwords, L.scan_tmp, st);
+      CommitArgs c;
+      c.sys = h->dev();
+      c.nwords = nwords;
+      c.bits = L.bits;
+      c.wbase = L.wbase;
+      c.srow = L.srow;
+      c.slot_of = L.slot_of;
+      c.staging = L.staging;
+      c.table = table;
+      c.pool = out;
+      c.row_base = n_rows;
+      c.remaining = accept;
+      c.rec_parent = nullptr;
+      c.rec_index = nullptr;
+      c.off = L.off;
+      c.P = P;
+      c.parent_base = level_lo;
+      c.g0 = g0;
+      c.st = L.st;
+      k_commit<<<grid_for(nwords, kWarpsPerBlock, nsm * 16), kThreads, 0, st>>>(c);
+      CK(cudaGetLastError());
+      k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(L.bits, nwords);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(hst, L.st, sizeof(ChunkState), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (hst->error & kErrTimeout) return fail(SNP_E_TIMEOUT, "bounded wait for a hash slot ran out");
+      if (hst->error) return fail(SNP_E_INTERNAL, "device consistency check failed (bits 0x%x)", hst->error);
+      if (hst->n_alloc > room && room < remaining)
+        return fail(SNP_E_BUFFER, "capacity %lld reached at depth %d with new configurations left",
+                    (long long)capacity, d);
+      const uint64_t acc = std::min<uint64_t>(hst->n_alloc, accept);
+      tombs += (int64_t)(hst->n_alloc - acc);
+      nnew += (int64_t)acc;
+      n_rows += (int64_t)acc;
+      if (remaining != ~0ull) remaining -= acc;
+      capped = hst->capped != 0 && cap_limits;
+      rate = std::max(1e-6, (double)hst->n_alloc / (double)Q);
+      g0 += Q;
+    }
+    if (per_depth_new) per_depth_new[d] = nnew;
+    if (nnew == 0) break;
+    reached = d;
+    level_lo = level_hi;
+    level_hi = n_rows;
+  }
+  *n = n_rows;
+  if (depth_reached) *depth_reached = reached;
+  return SNP_OK;
+}
