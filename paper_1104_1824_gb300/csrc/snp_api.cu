@@ -119,7 +119,7 @@ struct snp_system {
   // device copies of the system
   DevBuf d_first_rule, d_rule, d_csr, d_gain, d_M8;
   // exploration state
-  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_psi, d_off, d_scan_tmp, d_st,
+  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_psi, d_off, d_scan_tmp, d_st,
       d_rec_parent, d_rec_index, d_tmp;
   int64_t pool_rows = 0;  // capacity in rows
   uint64_t nbuckets = 0;
@@ -189,8 +189,10 @@ int ensure_chunk_buffers(snp_system* h, uint64_t q, cudaStream_t st) {
   TRY(h->d_srow.reserve(sizeof(uint32_t) * q));
   TRY(h->d_bits.reserve(sizeof(uint32_t) * words));
   TRY(h->d_wbase.reserve(sizeof(uint32_t) * words));
+  TRY(h->d_own.reserve(sizeof(uint32_t) * words));
   TRY(h->d_scan_tmp.reserve(scan_temp_bytes((int64_t)words, 4)));
   CK(cudaMemsetAsync(h->d_bits.p, 0, sizeof(uint32_t) * words, st));
+  CK(cudaMemsetAsync(h->d_own.p, 0, sizeof(uint32_t) * words, st));
   h->q_cap = q;
   return SNP_OK;
 }
@@ -523,24 +525,24 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         a.P = P;
         a.g0 = g0;
         a.Q = (uint32_t)Q;
-        a.run = 32;
+        a.run = 0;
         a.table = h->table();
         a.pool = h->d_pool.as<int32_t>();
         a.staging = h->d_staging.as<int32_t>();
         a.gmin = h->d_gmin.as<uint32_t>();
         a.slot_of = h->d_slot_of.as<uint32_t>();
+        a.ownbits = h->d_own.as<uint32_t>();
         a.st = h->d_st.as<ChunkState>();
-        const int blocks = grid_for((int64_t)((Q + a.run - 1) / a.run), kWarpsPerBlock, nsm * 16);
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
-        k_claim<<<blocks, kThreads, claim_smem(m), st>>>(a);
+        launch_expand(a, st, nsm);
         CK(cudaGetLastError());
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[1], st));
         sd.launches += 1;
       }
       const uint32_t nwords = (uint32_t)((Q + 31) / 32);
-      k_mark<<<grid_for((int64_t)Q, 256, nsm * 8), 256, 0, st>>>(h->d_gmin.as<uint32_t>(), h->d_bits.as<uint32_t>(),
-                                                                   h->d_srow.as<uint32_t>(), (uint32_t)Q,
-                                                                   h->d_st.as<ChunkState>());
+      k_mark<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_own.as<uint32_t>(), h->d_gmin.as<uint32_t>(),
+                                                               h->d_bits.as<uint32_t>(), h->d_srow.as<uint32_t>(),
+                                                               nwords, h->d_st.as<ChunkState>());
       launch_popc(h->d_bits.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, st);
       sd.launches += 2 + scan_u32(h->d_wbase.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, h->d_scan_tmp.p, st);
       CommitArgs c;
@@ -711,7 +713,7 @@ struct StaticLayout {
   uint64_t* off;
   void* scan_tmp;
   int32_t* staging;
-  uint32_t *gmin, *slot_of, *srow, *bits, *wbase;
+  uint32_t *gmin, *slot_of, *srow, *bits, *wbase, *own;
   uint64_t q;  // candidates per pass
 };
 
@@ -737,6 +739,7 @@ bool static_layout(unsigned char* base, int m, StaticLayout* L) {
   L->srow = reinterpret_cast<uint32_t*>(take(q * 4));
   L->bits = reinterpret_cast<uint32_t*>(take((q / 32 + 1) * 4));
   L->wbase = reinterpret_cast<uint32_t*>(take((q / 32 + 1) * 4));
+  L->own = reinterpret_cast<uint32_t*>(take((q / 32 + 1) * 4));
   return at <= kStaticScratchBytes;
 }
 
@@ -772,6 +775,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
   CK(cudaMemcpyAsync(out, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
   CK(cudaMemsetAsync(L.bits, 0, sizeof(uint32_t) * (L.q / 32 + 1), st));
+  CK(cudaMemsetAsync(L.own, 0, sizeof(uint32_t) * (L.q / 32 + 1), st));
   auto clear_and_insert = [&](int64_t rows) -> int {
     k_fill_u64<<<grid_for((int64_t)kStaticSlots, 256, nsm * 32), 256, 0, st>>>(L.slots, kStaticSlots, kEmpty);
     CK(cudaGetLastError());
@@ -831,17 +835,18 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       a.P = P;
       a.g0 = g0;
       a.Q = (uint32_t)Q;
-      a.run = 32;
+      a.run = 0;
       a.table = table;
       a.pool = out;
       a.staging = L.staging;
       a.gmin = L.gmin;
       a.slot_of = L.slot_of;
+      a.ownbits = L.own;
       a.st = L.st;
-      k_claim<<<grid_for((int64_t)((Q + a.run - 1) / a.run), kWarpsPerBlock, nsm * 16), kThreads, claim_smem(m), st>>>(a);
+      launch_expand(a, st, nsm);
       CK(cudaGetLastError());
       const uint32_t nwords = (uint32_t)((Q + 31) / 32);
-      k_mark<<<grid_for((int64_t)Q, 256, nsm * 8), 256, 0, st>>>(L.gmin, L.bits, L.srow, (uint32_t)Q, L.st);
+      k_mark<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(L.own, L.gmin, L.bits, L.srow, nwords, L.st);
       launch_popc(L.bits, L.wbase, nwords, st);
       scan_u32(L.wbase, L.wbase, nwords, L.scan_tmp, st);
       CommitArgs c;

@@ -5,7 +5,7 @@
 //              Psi = prod_n max(1, omega_n) (Eq. psi), saturating;
 //   scan       exclusive prefix sums of Psi give each parent's first candidate;
 //   per chunk of candidates [g0, g0 + Q) in canonical order:
-//     k_claim  steps (b)-(d): decode the spiking vector, C' = C + S . M_Pi
+//     k_expand steps (b)-(d) (snp_expand.cu): decode the spiking vector, C' = C + S . M_Pi
 //              (Eq. next-config), fingerprint, look C' up; a key never seen is
 //              claimed in the table and staged, and every candidate holding a
 //              staged key lowers that key's first-occurrence index;
@@ -23,86 +23,6 @@ namespace {
 constexpr int kWarpsPerBlock = 4;
 
 __device__ __forceinline__ void set_error(ChunkState* st, uint32_t bits) { atomicOr(&st->error, bits); }
-
-// Looks C' (in w.buf, fingerprint h) up and, if absent, claims it for
-// chunk-local candidate lid.  Writes staging rows and first-occurrence
-// indices as described at the top of the file.
-__device__ __forceinline__ void probe_and_claim(const ClaimArgs& a, const int32_t* buf, uint64_t h, uint32_t lid,
-                                                int lane) {
-  const int m = a.sys.m;
-  const uint32_t fp = fp32_of(h);
-  uint64_t bucket = h & a.table.bmask;
-  for (uint64_t probes = 0; probes <= a.table.bmask; ++probes, bucket = (bucket + 1) & a.table.bmask) {
-    unsigned long long* bs = a.table.slots + bucket * kBucket;
-    for (;;) {  // re-read the bucket after a lost race
-      unsigned long long v = (lane < kBucket) ? ld_acquire(bs + lane) : kEmpty;
-      const bool emp = lane < kBucket && v == kEmpty;
-      const bool mat = lane < kBucket && v != kEmpty && (uint32_t)(v >> 32) == fp && (uint32_t)v != kRowTomb;
-      const uint32_t em = __ballot_sync(0xffffffffu, emp);
-      uint32_t mm = __ballot_sync(0xffffffffu, mat);
-      const int fe = em ? __ffs(em) - 1 : kBucket;
-      mm &= (fe >= 32) ? 0xffffffffu : ((1u << fe) - 1u);
-      while (mm) {
-        const int L = __ffs(mm) - 1;
-        mm &= mm - 1;
-        uint32_t row = (uint32_t)__shfl_sync(0xffffffffu, v, L);
-        if (row == kRowReserved) {  // claimed, not yet published: wait (bounded)
-          unsigned long long w = 0;
-          if (lane == 0) {
-            int spins = 0;
-            do {
-              w = ld_acquire(bs + L);
-              if ((uint32_t)w != kRowReserved) break;
-              __nanosleep(64);
-            } while (++spins < kSpinLimit);
-          }
-          w = __shfl_sync(0xffffffffu, w, 0);
-          row = (uint32_t)w;
-          if (row == kRowReserved) {
-            if (lane == 0) set_error(a.st, kErrTimeout);
-            return;
-          }
-          if (row == kRowTomb) continue;
-        }
-        __threadfence();
-        const int32_t* other = (row & kPending) ? a.staging + (size_t)(row & ~kPending) * m
-                                                : a.pool + (size_t)row * m;
-        if (rows_equal(buf, other, m, lane)) {
-          if ((row & kPending) && lane == 0) atomicMin(a.gmin + (row & ~kPending), lid);
-          return;  // seen before (an earlier chunk or depth), or staged in this chunk
-        }
-      }
-      if (fe >= kBucket) break;  // bucket full: next bucket
-      unsigned long long old = 0;
-      if (lane == 0)
-        old = atomicCAS(bs + fe, kEmpty, ((unsigned long long)fp << 32) | kRowReserved);
-      old = __shfl_sync(0xffffffffu, old, 0);
-      if (old != kEmpty) continue;  // lost the race for this slot: look again
-      // Owner: stage C', record the claim, then publish the slot.
-      uint32_t srow = 0;
-      if (lane == 0) srow = atomicAdd(&a.st->n_alloc, 1u);
-      srow = __shfl_sync(0xffffffffu, srow, 0);
-      if (srow >= a.Q) {
-        if (lane == 0) {
-          set_error(a.st, kErrStaging);
-          atomicExch(bs + fe, ((unsigned long long)fp << 32) | kRowTomb);
-        }
-        return;
-      }
-      int32_t* dst = a.staging + (size_t)srow * m;
-      for (int n = lane; n < m; n += 32) __stcg(dst + n, buf[n]);
-      if (lane == 0) {
-        a.gmin[srow] = lid;
-        a.slot_of[srow] = (uint32_t)(bucket * kBucket + fe);
-      }
-      __threadfence();
-      __syncwarp();
-      if (lane == 0) atomicExch(bs + fe, ((unsigned long long)fp << 32) | (kPending | srow));
-      return;
-    }
-  }
-  if (lane == 0) set_error(a.st, kErrTableFull);
-}
 
 }  // namespace
 
@@ -135,50 +55,28 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_psi(DevSys s, const int
   }
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_claim(ClaimArgs a) {
-  extern __shared__ int32_t smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int m = a.sys.m;
-  WarpParent w;
-  w.par = smem + (size_t)wib * 3 * m;
-  w.msk = reinterpret_cast<uint32_t*>(w.par + m);
-  w.buf = w.par + 2 * m;
-  const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
-  const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerBlock;
-  for (uint64_t task = (uint64_t)blockIdx.x * kWarpsPerBlock + wib; task < ntasks; task += nw) {
-    const uint64_t la = task * a.run;
-    const uint64_t lb = min(la + a.run, (uint64_t)a.Q);
-    int64_t p = warp_find_parent(a.off, a.P, a.g0 + la, lane);
-    uint64_t p_lo = __ldg(a.off + p), p_hi = __ldg(a.off + p + 1);
-    if (task == 0 && lane == 0) a.st->p_first = (unsigned long long)p;
-    load_parent(a.sys, a.parents + (size_t)p * m, w, lane);
-    for (uint64_t l = la; l < lb; ++l) {
-      const uint64_t g = a.g0 + l;
-      if (g >= p_hi) {
-        do {
-          ++p;
-          p_lo = p_hi;
-          p_hi = __ldg(a.off + p + 1);
-        } while (g >= p_hi);
-        load_parent(a.sys, a.parents + (size_t)p * m, w, lane);
-      }
-      build_child(a.sys, w, g - p_lo, lane);
-      const uint64_t h = fingerprint(a.sys, w.buf, lane);
-      probe_and_claim(a, w.buf, h, (uint32_t)l, lane);
+// One bit per first occurrence: every candidate lid that claimed a key
+// (ownbits) names the key's first candidate gmin[lid]; clears ownbits and
+// counts the claimed keys into st->n_alloc.
+__global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
+                       ChunkState* st) {
+  uint32_t cnt = 0;
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
+    uint32_t word = ownbits[w];
+    if (!word) continue;
+    ownbits[w] = 0;
+    cnt += __popc(word);
+    while (word) {
+      const uint32_t o = w * 32u + (uint32_t)(__ffs(word) - 1);
+      word &= word - 1;
+      const uint32_t f = gmin[o];
+      atomicOr(bits + (f >> 5), 1u << (f & 31));
+      srow[f] = o;
     }
-    if (task + 1 == ntasks && lane == 0) a.st->p_last = (unsigned long long)p;
   }
-}
-
-// One bit per first occurrence: staging row s holds a distinct key whose
-// first candidate (chunk-local) is gmin[s].
-__global__ void k_mark(const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t Q, ChunkState* st) {
-  const uint32_t n = min(st->n_alloc, Q);
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const uint32_t lid = gmin[s];
-    atomicOr(bits + (lid >> 5), 1u << (lid & 31));
-    srow[lid] = s;
-  }
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, k);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->n_alloc, cnt);
 }
 
 __global__ void k_popc(const uint32_t* bits, uint32_t* cnt, uint32_t nwords) {

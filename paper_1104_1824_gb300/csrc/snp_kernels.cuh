@@ -16,9 +16,10 @@ struct ClaimArgs {
   uint32_t run;               // consecutive candidates per warp task
   DevTable table;
   const int32_t* pool;        // committed configurations
-  int32_t* staging;           // [Q x m] configurations first claimed in this chunk
-  uint32_t* gmin;             // [Q] smallest chunk-local candidate index per staging row
-  uint32_t* slot_of;          // [Q] table slot per staging row
+  int32_t* staging;           // [Q x m] row lid = candidate lid's configuration if lid claimed a new key
+  uint32_t* gmin;             // [Q] per claiming lid: smallest chunk-local candidate holding its key
+  uint32_t* slot_of;          // [Q] per claiming lid: its table slot
+  uint32_t* ownbits;          // [Q / 32 + 1] bit lid set iff candidate lid claimed a new key
   ChunkState* st;
 };
 
@@ -46,8 +47,10 @@ struct CommitArgs {
 
 __global__ void k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi,
                       ChunkState* st);
-__global__ void k_claim(ClaimArgs a);
-__global__ void k_mark(const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t Q, ChunkState* st);
+// Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
+int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
+__global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
+                       ChunkState* st);
 __global__ void k_commit(CommitArgs a);
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords);
 __global__ void k_insert_rows(DevSys s, const int32_t* pool, int64_t r0, int64_t r1, DevTable t, ChunkState* st);
