@@ -117,7 +117,8 @@ struct snp_system {
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_M8;
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_M8;
+  std::vector<unsigned long long> colkey, rowkey;
   // exploration state
   DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_psi, d_off, d_scan_tmp, d_st,
       d_rec_parent, d_rec_index, d_tmp;
@@ -145,6 +146,8 @@ struct snp_system {
     s.rule = d_rule.as<int4>();
     s.csr = d_csr.as<int2>();
     s.gain = d_gain.as<int32_t>();
+    s.colkey = d_colkey.as<unsigned long long>();
+    s.rowkey = d_rowkey.as<unsigned long long>();
     return s;
   }
   DevTable table() const { return DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }
@@ -312,6 +315,19 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     }
   h->gain.resize(m);
   for (int j = 0; j < m; ++j) h->gain[j] = (int32_t)std::min<int64_t>(g[j], INT32_MAX);
+  // Hash multipliers R[j] (odd, from the SplitMix64 finaliser) and each rule's
+  // hash increment H[r] = sum_j M[r][j] * R[j] (mod 2^64).
+  h->colkey.resize(m);
+  for (int j = 0; j < m; ++j) {
+    uint64_t z = 0x9E3779B97F4A7C15ull * (uint64_t)(j + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    h->colkey[j] = (z ^ (z >> 31)) | 1ull;
+  }
+  h->rowkey.assign(R + 1, 0ull);
+  for (int r = 0; r < R; ++r)
+    for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e)
+      h->rowkey[r] += (uint64_t)(int64_t)h->csr[e].y * h->colkey[h->csr[e].x];
   int rc = SNP_OK;
   auto up = [&](DevBuf& b, const void* src, size_t bytes) -> int {
     if ((rc = b.reserve(std::max<size_t>(bytes, 16))) != SNP_OK) return rc;
@@ -322,6 +338,8 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_rule, h->rule.data(), sizeof(int4) * (R + 1))) ||
       (rc = up(h->d_csr, h->csr.data(), sizeof(int2) * std::max<size_t>(h->csr.size(), 1))) ||
       (rc = up(h->d_gain, h->gain.data(), sizeof(int32_t) * m)) ||
+      (rc = up(h->d_colkey, h->colkey.data(), sizeof(unsigned long long) * m)) ||
+      (rc = up(h->d_rowkey, h->rowkey.data(), sizeof(unsigned long long) * (R + 1))) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;
     return rc;
@@ -365,8 +383,7 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
   uint64_t* dpsi = reinterpret_cast<uint64_t*>(h->d_tmp.as<char>() + ((sizeof(int32_t) * m + 15) / 16) * 16);
   CK(cudaMemcpy(dC, c.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
   CK(cudaMemset(h->d_st.p, 0, sizeof(ChunkState)));
-  k_psi<<<1, kThreads, (size_t)kWarpsPerBlock * 2 * m * sizeof(int32_t)>>>(h->dev(), dC, 1, -1, dpsi,
-                                                                          h->d_st.as<ChunkState>());
+  launch_psi(h->dev(), dC, 1, -1, dpsi, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
   CK(cudaGetLastError());
   uint64_t ps = 0;
   CK(cudaMemcpy(&ps, dpsi, sizeof ps, cudaMemcpyDeviceToHost));
@@ -472,8 +489,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     const int32_t* parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
     CK(cudaMemsetAsync(h->d_psi.as<uint64_t>() + P, 0, sizeof(uint64_t), st));
-    k_psi<<<grid_for(P, kWarpsPerBlock, nsm * 16), kThreads, (size_t)kWarpsPerBlock * 2 * m * sizeof(int32_t), st>>>(
-        h->dev(), parents, P, o->max_expand_value, h->d_psi.as<uint64_t>(), h->d_st.as<ChunkState>());
+    launch_psi(h->dev(), parents, P, o->max_expand_value, h->d_psi.as<uint64_t>(), h->d_st.as<ChunkState>(), st, nsm);
     CK(cudaGetLastError());
     sd.launches += 1 + scan_u64_sat(h->d_psi.as<uint64_t>(), h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
     CK(cudaGetLastError());
@@ -564,7 +580,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
       c.parent_base = level_lo;
       c.g0 = g0;
       c.st = h->d_st.as<ChunkState>();
-      k_commit<<<grid_for(nwords, kWarpsPerBlock, nsm * 16), kThreads, 0, st>>>(c);
+      k_commit<<<grid_for(nwords, 8, nsm * 16), 256, 0, st>>>(c);
       CK(cudaGetLastError());
       k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_bits.as<uint32_t>(), nwords);
       CK(cudaGetLastError());
@@ -797,8 +813,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
     const int32_t* parents = out + (size_t)level_lo * m;
     CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
     CK(cudaMemsetAsync(L.psi + P, 0, sizeof(uint64_t), st));
-    k_psi<<<grid_for(P, kWarpsPerBlock, nsm * 16), kThreads, (size_t)kWarpsPerBlock * 2 * m * sizeof(int32_t), st>>>(
-        h->dev(), parents, P, o->max_expand_value, L.psi, L.st);
+    launch_psi(h->dev(), parents, P, o->max_expand_value, L.psi, L.st, st, nsm);
     CK(cudaGetLastError());
     scan_u64_sat(L.psi, L.off, P + 1, L.scan_tmp, st);
     CK(cudaMemcpyAsync(h->pin.u64, L.off + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -868,7 +883,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       c.parent_base = level_lo;
       c.g0 = g0;
       c.st = L.st;
-      k_commit<<<grid_for(nwords, kWarpsPerBlock, nsm * 16), kThreads, 0, st>>>(c);
+      k_commit<<<grid_for(nwords, 8, nsm * 16), 256, 0, st>>>(c);
       CK(cudaGetLastError());
       k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(L.bits, nwords);
       CK(cudaGetLastError());

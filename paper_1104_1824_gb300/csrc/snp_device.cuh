@@ -34,6 +34,8 @@ struct DevSys {
   const int4* rule;           // [R + 1] {i, j, c, csr begin}; rule[R].w = nnz
   const int2* csr;            // [nnz] {column, value}: nonzeros of M_Pi, row by row
   const int32_t* gain;        // [m] largest increase of column j in one step
+  const unsigned long long* colkey;  // [m] random odd multiplier R[j] of column j
+  const unsigned long long* rowkey;  // [R] H[r] = sum over row r of M_Pi of M[r][j] * R[j] (mod 2^64)
 };
 
 struct DevTable {
@@ -70,10 +72,12 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 31);
 }
 
-// One column's share of the fingerprint; the fingerprint of C is the sum over
-// columns mod 2^64, so any partition of the columns can compute it.
-__device__ __forceinline__ uint64_t col_hash(int j, int32_t v) {
-  return mix64(((uint64_t)(uint32_t)j << 32) | (uint32_t)v);
+// Linear hash of a configuration: h(C) = sum_j C[j] * R[j] (mod 2^64).  It is
+// additive over columns (any partition of the columns can compute it) and over
+// Eq. next-config: h(C + S . M_Pi) = h(C) + sum of H[r] over the rules S uses.
+// The table key is mix64(h); equality is always decided by a full compare.
+__device__ __forceinline__ uint64_t col_hash(const DevSys& s, int j, int32_t v) {
+  return (uint64_t)(uint32_t)v * __ldg(s.colkey + j);
 }
 
 // a^x in L(a^i (a^j)*) and x >= c (Section 2.1, rule (b-1)).
@@ -195,10 +199,11 @@ __device__ __forceinline__ void build_child(const DevSys& s, WarpParent& w, uint
   __syncwarp();
 }
 
+// Table key of the configuration in buf (warp-cooperative).
 __device__ __forceinline__ uint64_t fingerprint(const DevSys& s, const int32_t* buf, int lane) {
   uint64_t h = 0;
-  for (int n = lane; n < s.m; n += 32) h += col_hash(n, buf[n]);
-  return warp_sum_u64(h);
+  for (int n = lane; n < s.m; n += 32) h += col_hash(s, n, buf[n]);
+  return mix64(warp_sum_u64(h));
 }
 
 __device__ __forceinline__ uint32_t fp32_of(uint64_t h) {

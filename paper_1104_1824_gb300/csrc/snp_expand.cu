@@ -1,37 +1,43 @@
 // The expand kernel: steps (b), (c) and (d) for one chunk of candidates.
 //
-// A warp takes a run of consecutive candidates (parent p, spiking-vector
-// indices t, t+1, ...).  It decodes the first index in full (mixed radix of
-// the per-neuron choice counts, Eq. psi, last neuron least significant) and
-// builds C' = C + S . M_Pi (Eq. next-config) in shared memory.  Each following
-// index is one increment of that mixed-radix counter: only the neurons whose
-// digit changes (on average fewer than two) swap the old rule's row of M_Pi
-// for the new rule's row, so C' is updated, not rebuilt.  Each candidate's C'
-// is copied to a per-warp tile row with its fingerprint.  Every batch of up to
-// 32 tile rows is then resolved lane-parallel: lane k probes the hash table
-// for row k, compares full keys, and either finds the key (seen before, or
-// staged earlier in this chunk: then it lowers that key's first-occurrence
-// index) or claims an empty slot, stages its row and publishes the slot.
+// A warp takes a run of consecutive candidates of one parent (spiking-vector
+// indices t0, t0 + 1, ...).  It keeps a base: the digits of t0 in the mixed
+// radix of the per-neuron choice counts (Eq. psi; last neuron least
+// significant), the child C' = C + S . M_Pi of t0 (Eq. next-config) and its
+// linear hash.  A batch of up to 32 candidates is then built lane-parallel:
+// lane k adds k to the base's digits (only the few least significant
+// non-trivial neurons change), copies the base row into its own tile row and
+// swaps the changed neurons' rows of M_Pi (hash: swaps their H[r]).  Lane k
+// then resolves its row: it probes the hash table, compares full keys, and
+// either finds the key (seen before, or staged earlier in this chunk: then it
+// lowers that key's first-occurrence index) or claims an empty slot, stages
+// its row and publishes the slot.  The base then moves on by the batch size.
 #include "snp_kernels.cuh"
 
 namespace snp {
 
 namespace {
 
+constexpr int kLowDigits = 16;  // least significant non-trivial neurons tracked per parent
+
 struct ExpandSmem {
   int32_t* tile;              // [B][ts] candidate rows
-  unsigned long long* hk;     // [B] fingerprints
   int32_t* par;               // [m4] parent
-  int32_t* buf;               // [m4] current child
+  int32_t* buf;               // [m4] base child
   uint32_t* msk;              // [m4] applicable-rule masks
-  uint8_t* dig;               // [m4] current digit per neuron
+  uint8_t* dig;               // [m4] base digits
+  int32_t* low;               // [kLowDigits] least significant non-trivial neurons, least first
+  int* nlow;                  // [1] entries of low
+  uint32_t* plow;             // [1] product of their choice counts (capped at 2^31)
+  uint32_t* vlow;             // [1] value of the base's digits on them (< plow)
+  unsigned long long* hbase;  // [1] linear hash of the base child
 };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
 __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
   const int m4 = round4(m);
-  size_t b = (size_t)B * ts * 4 + (size_t)B * 8 + (size_t)m4 * 12 + (size_t)m4;
+  size_t b = (size_t)B * ts * 4 + (size_t)m4 * 12 + 96 + (size_t)m4;
   return (b + 15) & ~size_t(15);
 }
 
@@ -39,16 +45,30 @@ __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long 
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ void apply_row(const DevSys& s, int32_t* buf, int r, int sign) {
+__device__ __forceinline__ int rule_of(const DevSys& s, const ExpandSmem& w, int n, int d) {
+  return __ldg(s.first_rule + n) + nth_set_bit(w.msk[n], d);
+}
+
+// row += sign * (row r of M_Pi); the row is private to the calling lane
+__device__ __forceinline__ void add_row_private(const DevSys& s, int32_t* row, int r, int sign) {
   const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
   for (int e = e0; e < e1; ++e) {
     const int2 cv = __ldg(s.csr + e);
-    atomicAdd(&buf[cv.x], sign * cv.y);
+    row[cv.x] += sign * cv.y;
   }
 }
 
-// Step (a) for the parent row: masks and the mixed-radix place value of the
-// neurons owned by later lanes (neuron 0 most significant).
+__device__ __forceinline__ void add_row_shared(const DevSys& s, int32_t* row, int r, int sign) {
+  const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
+  for (int e = e0; e < e1; ++e) {
+    const int2 cv = __ldg(s.csr + e);
+    atomicAdd(&row[cv.x], sign * cv.y);
+  }
+}
+
+// Step (a) for the parent row: masks, the list of the least significant
+// non-trivial neurons, and the mixed-radix place value of the neurons owned by
+// later lanes (neuron 0 most significant).
 __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const int32_t* __restrict__ row, ExpandSmem& w,
                                                  int lane) {
   __syncwarp();
@@ -73,12 +93,35 @@ __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const int32_t*
   }
   const uint64_t a = __shfl_down_sync(0xffffffffu, v, 1);
   __syncwarp();
+  // least significant non-trivial neurons, scanning 32 neurons at a time from the end
+  int count = 0;
+  for (int top = s.m - 1; top >= 0 && count < kLowDigits; top -= 32) {
+    const int n = top - lane;
+    const bool nt = n >= 0 && __popc(w.msk[n]) > 1;
+    const uint32_t b = __ballot_sync(0xffffffffu, nt);
+    const int rank = __popc(b & ((1u << lane) - 1u));
+    if (nt && count + rank < kLowDigits) w.low[count + rank] = n;
+    count += __popc(b);
+  }
+  if (lane == 0) {
+    const int nl = min(count, kLowDigits);
+    uint64_t pl = 1;
+    for (int i = 0; i < nl; ++i) {
+      pl *= (uint64_t)__popc(w.msk[w.low[i]]);
+      if (pl > (1ull << 31)) pl = 1ull << 31;
+    }
+    *w.nlow = nl;
+    *w.plow = (uint32_t)pl;
+  }
+  __syncwarp();
   return lane == 31 ? 1ull : a;
 }
 
-// Decodes index t in full and builds C' = C + S . M_Pi in w.buf.
+// The base becomes candidate t of the loaded parent: digits, child, hash.
 __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint64_t t, uint64_t after, int lane) {
   for (int n = lane; n < s.m; n += 32) w.buf[n] = w.par[n];
+  uint64_t hp = 0;
+  for (int n = lane; n < s.m; n += 32) hp += col_hash(s, n, w.par[n]);
   __syncwarp();
   const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
   uint64_t q = (after > t) ? 0ull : t / after;
@@ -99,52 +142,88 @@ __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint
       q /= radix;
     }
     w.dig[n] = (uint8_t)d;
-    apply_row(s, w.buf, __ldg(s.first_rule + n) + nth_set_bit(mask, (int)d), 1);
+    const int r = __ldg(s.first_rule + n) + nth_set_bit(mask, (int)d);
+    add_row_shared(s, w.buf, r, 1);
+    hp += __ldg(s.rowkey + r);
   }
+  hp = warp_sum_u64(hp);
   __syncwarp();
-}
-
-// Index t -> t + 1 (t + 1 < Psi): the carry enters at the last neuron; lanes
-// whose non-trivial digits are all at their maximum pass it on and wrap.
-__device__ __forceinline__ void step_one(const DevSys& s, ExpandSmem& w, int lane) {
-  const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
-  bool full = true;
-  for (int n = n0; n < n1; ++n) {
-    const int r = __popc(w.msk[n]);
-    if (r > 1 && w.dig[n] != r - 1) full = false;
-  }
-  const uint32_t stop = __ballot_sync(0xffffffffu, !full);
-  const int L = 31 - __clz(stop);
-  if (lane >= L) {
-    for (int n = n1 - 1; n >= n0; --n) {
-      const uint32_t mask = w.msk[n];
-      const int r = __popc(mask);
-      if (r <= 1) continue;
-      const int d = w.dig[n];
-      const int nd = (d == r - 1) ? 0 : d + 1;
-      const int base = __ldg(s.first_rule + n);
-      apply_row(s, w.buf, base + nth_set_bit(mask, d), -1);
-      apply_row(s, w.buf, base + nth_set_bit(mask, nd), 1);
-      w.dig[n] = (uint8_t)nd;
-      if (nd != 0) break;  // the increment is absorbed here
+  if (lane == 0) {
+    *w.hbase = hp;
+    uint64_t v = 0, place = 1;
+    for (int i = 0; i < *w.nlow && place < (1ull << 31); ++i) {
+      const int n = w.low[i];
+      v += place * w.dig[n];
+      place *= __popc(w.msk[n]);
     }
+    const uint64_t cap = (uint64_t)*w.plow - 1;
+    *w.vlow = (uint32_t)(v < cap ? v : cap);
   }
   __syncwarp();
 }
 
+// Adds k to the base digits of the low neurons (k < the product of their
+// radices); calls f(neuron, old digit, new digit) for each changed one.
+template <typename F>
+__device__ __forceinline__ void add_to_digits(const ExpandSmem& w, uint32_t k, F&& f) {
+  const int nl = *w.nlow;
+  for (int i = 0; i < nl && k; ++i) {
+    const int n = w.low[i];
+    const uint32_t r = __popc(w.msk[n]);
+    const uint32_t d = w.dig[n];
+    const uint32_t sum = d + k;
+    const uint32_t nd = sum % r;
+    k = sum / r;
+    if (nd != d) f(n, (int)d, (int)nd);
+  }
+}
+
+template <bool VEC>
+__device__ __forceinline__ void copy_row(const int32_t* src, int32_t* dst, int m) {
+  if (VEC) {
+    const int4* a = reinterpret_cast<const int4*>(src);
+    int4* b = reinterpret_cast<int4*>(dst);
+    for (int j = 0; j < (m >> 2); ++j) b[j] = a[j];
+    return;
+  }
+  for (int j = 0; j < m; ++j) dst[j] = src[j];
+}
+
+// Full-key compare; branch-free in groups of 8 loads so that the loads of a
+// group are in flight together.
 template <bool VEC>
 __device__ __forceinline__ bool row_equal_lane(const int32_t* row, const int32_t* other, int m) {
   if (VEC) {
     const int4* a = reinterpret_cast<const int4*>(row);
     const int4* b = reinterpret_cast<const int4*>(other);
-    for (int j = 0; j < (m >> 2); ++j) {
-      const int4 x = a[j], y = __ldcg(b + j);
-      if (x.x != y.x || x.y != y.y || x.z != y.z || x.w != y.w) return false;
+    const int n4 = m >> 2;
+    for (int j0 = 0; j0 < n4; j0 += 8) {
+      int4 y[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < n4) y[u] = __ldcg(b + j0 + u);
+      int diff = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < n4) {
+          const int4 x = a[j0 + u];
+          diff |= (x.x ^ y[u].x) | (x.y ^ y[u].y) | (x.z ^ y[u].z) | (x.w ^ y[u].w);
+        }
+      if (diff) return false;
     }
     return true;
   }
-  for (int j = 0; j < m; ++j)
-    if (row[j] != __ldcg(other + j)) return false;
+  for (int j0 = 0; j0 < m; j0 += 8) {
+    int y[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (j0 + u < m) y[u] = __ldcg(other + j0 + u);
+    int diff = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (j0 + u < m) diff |= row[j0 + u] ^ y[u];
+    if (diff) return false;
+  }
   return true;
 }
 
@@ -159,13 +238,14 @@ __device__ __forceinline__ void stage_row_lane(const int32_t* row, int32_t* dst,
   for (int j = 0; j < m; ++j) __stcg(dst + j, row[j]);
 }
 
-// Step (d) for one candidate, by one lane, independently of the other lanes
-// (no warp-collective operation, so a lane may wait on another lane's slot).
+// Step (d) for one candidate, by one lane, without waiting on any other lane:
+// returns false when the key may sit in a slot that another lane or warp has
+// reserved but not yet published; the caller then tries again in a later pass.
 template <bool VEC>
-__device__ __forceinline__ void resolve_lane(const ClaimArgs& a, const int32_t* row, uint64_t h, uint32_t lid) {
+__device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid) {
   const int m = a.sys.m;
-  const uint32_t fp = fp32_of(h);
-  uint64_t bucket = h & a.table.bmask;
+  const uint32_t fp = fp32_of(key);
+  uint64_t bucket = key & a.table.bmask;
   for (uint64_t probes = 0; probes <= a.table.bmask; ++probes, bucket = (bucket + 1) & a.table.bmask) {
     unsigned long long* bs = a.table.slots + bucket * kBucket;
     unsigned long long v[kBucket];
@@ -188,26 +268,14 @@ __device__ __forceinline__ void resolve_lane(const ClaimArgs& a, const int32_t* 
             a.slot_of[lid] = (uint32_t)(bucket * kBucket + j);
             atomicOr(a.ownbits + (lid >> 5), 1u << (lid & 31));
             st_release(bs + j, ((unsigned long long)fp << 32) | (kPending | lid));
-            return;
+            return true;
           }
           x = old;  // someone else took the slot: look at what is there now
           continue;
         }
         const uint32_t rf = (uint32_t)x;
         if ((uint32_t)(x >> 32) != fp || rf == kRowTomb) break;
-        if (rf == kRowReserved) {  // claimed but not yet published: bounded wait
-          int spins = 0;
-          do {
-            x = ld_acquire(bs + j);
-            if ((uint32_t)x != kRowReserved) break;
-            __nanosleep(64);
-          } while (++spins < kSpinLimit);
-          if ((uint32_t)x == kRowReserved) {
-            atomicOr(&a.st->error, kErrTimeout);
-            return;
-          }
-          continue;
-        }
+        if (rf == kRowReserved) return false;  // published soon: try again later
         const int32_t* other;
         if (rf & kPending) {
           (void)ld_acquire(bs + j);  // orders the staged row's reads after the publish
@@ -217,17 +285,18 @@ __device__ __forceinline__ void resolve_lane(const ClaimArgs& a, const int32_t* 
         }
         if (row_equal_lane<VEC>(row, other, m)) {
           if (rf & kPending) atomicMin(a.gmin + (rf & ~kPending), lid);
-          return;
+          return true;
         }
         break;
       }
     }
   }
   atomicOr(&a.st->error, kErrTableFull);
+  return true;
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(256, 1) k_expand(ClaimArgs a, int B, int ts) {
+__global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   const DevSys& s = a.sys;
@@ -235,11 +304,15 @@ __global__ void __launch_bounds__(256, 1) k_expand(ClaimArgs a, int B, int ts) {
   ExpandSmem w;
   unsigned char* base = smem_raw + (size_t)wib * expand_warp_bytes(m, B, ts);
   w.tile = reinterpret_cast<int32_t*>(base);
-  w.hk = reinterpret_cast<unsigned long long*>(base + (size_t)B * ts * 4);
-  w.par = reinterpret_cast<int32_t*>(w.hk + B);
+  w.par = w.tile + (size_t)B * ts;
   w.buf = w.par + m4;
   w.msk = reinterpret_cast<uint32_t*>(w.buf + m4);
-  w.dig = reinterpret_cast<uint8_t*>(w.msk + m4);
+  w.low = reinterpret_cast<int32_t*>(w.msk + m4);               // 64 bytes
+  w.nlow = w.low + kLowDigits;                                    // +64
+  w.plow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 1);   // +68
+  w.vlow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 2);   // +72
+  w.hbase = reinterpret_cast<unsigned long long*>(w.low + kLowDigits + 4);  // +80
+  w.dig = reinterpret_cast<uint8_t*>(w.low) + 96;
 
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
   const uint64_t nw = (uint64_t)gridDim.x * wpb;
@@ -251,38 +324,70 @@ __global__ void __launch_bounds__(256, 1) k_expand(ClaimArgs a, int B, int ts) {
     if (task == 0 && lane == 0) a.st->p_first = (unsigned long long)p;
     uint64_t after = parent_state(s, a.parents + (size_t)p * m, w, lane);
     decode_full(s, w, a.g0 + la - p_lo, after, lane);
-    for (uint64_t l = la; l < lb;) {
-      const int nb = (int)min((uint64_t)B, lb - l);
-      for (int k = 0; k < nb; ++k) {
-        int32_t* trow = w.tile + k * ts;
-        uint64_t hp = 0;
-        for (int n = lane; n < m; n += 32) {
-          const int32_t x = w.buf[n];
-          trow[n] = x;
-          hp += col_hash(n, x);
-        }
-        hp = warp_sum_u64(hp);
-        if (lane == 0) w.hk[k] = hp;
-        __syncwarp();
-        const uint64_t gn = a.g0 + l + k + 1;
-        if (l + k + 1 < lb) {
-          if (gn >= p_hi) {
-            do {
-              ++p;
-              p_lo = p_hi;
-              p_hi = __ldg(a.off + p + 1);
-            } while (gn >= p_hi);
-            after = parent_state(s, a.parents + (size_t)p * m, w, lane);
-            decode_full(s, w, gn - p_lo, after, lane);
-          } else {
-            step_one(s, w, lane);
-          }
-        }
+    uint64_t l = la;
+    while (l < lb) {
+      const uint64_t g = a.g0 + l;
+      // a batch never crosses a parent, nor a rollover of the tracked low digits
+      const uint32_t room = *w.plow - *w.vlow;
+      const int nb = (int)min(min(min((uint64_t)B, lb - l), p_hi - g), (uint64_t)room);
+      if (nb <= 0) {  // cannot happen: every bound above is positive
+        if (lane == 0) atomicOr(&a.st->error, kErrInternal);
+        break;
       }
-      __syncwarp();
-      if (lane < nb) resolve_lane<VEC>(a, w.tile + lane * ts, w.hk[lane], (uint32_t)(l + lane));
-      __syncwarp();
+      bool done = true;
+      uint64_t key = 0;
+      if (lane < nb) {
+        int32_t* trow = w.tile + lane * ts;
+        copy_row<VEC>(w.buf, trow, m);
+        uint64_t h = *w.hbase;
+        add_to_digits(w, (uint32_t)lane, [&](int n, int d, int nd) {
+          const int r_old = rule_of(s, w, n, d), r_new = rule_of(s, w, n, nd);
+          add_row_private(s, trow, r_old, -1);
+          add_row_private(s, trow, r_new, 1);
+          h += __ldg(s.rowkey + r_new) - __ldg(s.rowkey + r_old);
+        });
+        key = mix64(h);
+        done = false;
+      }
+      // Passes over the batch until every lane has resolved its candidate; a
+      // lane never waits inside a pass, so owners in this warp publish first.
+      for (int pass = 0;; ++pass) {
+        if (!done) done = resolve_lane<VEC>(a, w.tile + lane * ts, key, (uint32_t)(l + lane));
+        if (__all_sync(0xffffffffu, done)) break;
+        if (pass >= kSpinLimit) {
+          if (!done) atomicOr(&a.st->error, kErrTimeout);
+          break;
+        }
+        __nanosleep(32);
+      }
       l += nb;
+      if (l >= lb) break;
+      const uint64_t gn = a.g0 + l;
+      if (gn >= p_hi) {  // next parent
+        do {
+          ++p;
+          p_lo = p_hi;
+          p_hi = __ldg(a.off + p + 1);
+        } while (gn >= p_hi);
+        after = parent_state(s, a.parents + (size_t)p * m, w, lane);
+        decode_full(s, w, gn - p_lo, after, lane);
+      } else if ((uint32_t)nb == room) {  // the low digits roll over: decode in full
+        decode_full(s, w, gn - p_lo, after, lane);
+      } else {  // same parent: the base moves on by nb
+        if (lane == 0) {
+          uint64_t h = *w.hbase;
+          add_to_digits(w, (uint32_t)nb, [&](int n, int d, int nd) {
+            const int r_old = rule_of(s, w, n, d), r_new = rule_of(s, w, n, nd);
+            add_row_private(s, w.buf, r_old, -1);
+            add_row_private(s, w.buf, r_new, 1);
+            h += __ldg(s.rowkey + r_new) - __ldg(s.rowkey + r_old);
+            w.dig[n] = (uint8_t)nd;
+          });
+          *w.hbase = h;
+          *w.vlow += (uint32_t)nb;
+        }
+        __syncwarp();
+      }
     }
     if (task + 1 == ntasks && lane == 0) a.st->p_last = (unsigned long long)p;
   }
@@ -292,14 +397,14 @@ __global__ void __launch_bounds__(256, 1) k_expand(ClaimArgs a, int B, int ts) {
 
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const int m = a.sys.m;
-  const int ts = round4(m) + 4;                       // tile row stride (words), 16-byte aligned
-  int B = (int)std::min<size_t>(32, std::max<size_t>(4, (16u << 10) / (4u * ts)));
+  const int ts = round4(m) + 4;  // tile row stride (words): 16-byte aligned, rotates banks
+  const int B = (int)std::min<size_t>(32, std::max<size_t>(1, (32u << 10) / (4u * ts)));
   const size_t per_warp = expand_warp_bytes(m, B, ts);
-  int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (96u << 10) / per_warp));
+  const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (100u << 10) / per_warp));
   const size_t smem = per_warp * wpb;
-  a.run = (uint32_t)(4 * B);
+  a.run = (uint32_t)(8 * B);
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
-  const int per_sm = (int)std::max<size_t>(1, (200u << 10) / smem);
+  const int per_sm = (int)std::max<size_t>(1, (220u << 10) / smem);
   const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm * per_sm);
   const bool vec = (m % 4) == 0;
   auto fn = vec ? k_expand<true> : k_expand<false>;

@@ -26,33 +26,73 @@ __device__ __forceinline__ void set_error(ChunkState* st, uint32_t bits) { atomi
 
 }  // namespace
 
-// Step (a) and Eq. psi for every frontier row; flags rows whose children could
-// leave int32, and gives Psi = 0 to rows not to be expanded (max_expand).
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_psi(DevSys s, const int32_t* rows, int64_t P,
-                                                             int32_t max_expand, uint64_t* psi, ChunkState* st) {
-  extern __shared__ int32_t smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  WarpParent w;
-  w.par = smem + (size_t)wib * 2 * s.m;
-  w.msk = reinterpret_cast<uint32_t*>(w.par + s.m);
-  w.buf = nullptr;
-  const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
-  for (int64_t p = (int64_t)blockIdx.x * kWarpsPerBlock + wib; p < P; p += nw) {
-    const int32_t* row = rows + (size_t)p * s.m;
-    load_parent(s, row, w, lane);
-    bool over = false, skip = false;
-    for (int n = lane; n < s.m; n += 32) {
-      const int32_t x = w.par[n];
-      over |= x > INT32_MAX - __ldg(s.gain + n);
-      skip |= max_expand >= 0 && x > max_expand;
-    }
-    over = __any_sync(0xffffffffu, over);
-    skip = __any_sync(0xffffffffu, skip);
-    if (lane == 0) {
-      psi[p] = skip ? 0ull : w.psi;
-      if (over && !skip) set_error(st, kErrOverflow);
-    }
+// Step (a) and Eq. psi for every frontier row, one lane per row: counts each
+// neuron's applicable rules, Psi = prod max(1, omega) (saturating); flags rows
+// whose children could leave int32 and gives Psi = 0 to rows not to be
+// expanded (max_expand).  The rule table sits in shared memory when it fits.
+template <bool SMEM, bool VEC>
+__global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand,
+                                             uint64_t* psi, ChunkState* st) {
+  extern __shared__ __align__(16) unsigned char psi_smem[];
+  const int m = s.m;
+  const int4* rule = s.rule;
+  const int32_t* fr = s.first_rule;
+  if (SMEM) {
+    int4* r4 = reinterpret_cast<int4*>(psi_smem);
+    int32_t* f4 = reinterpret_cast<int32_t*>(r4 + s.R);
+    for (int i = threadIdx.x; i < s.R; i += blockDim.x) r4[i] = s.rule[i];
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) f4[i] = s.first_rule[i];
+    __syncthreads();
+    rule = r4;
+    fr = f4;
   }
+  bool over = false;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t* row = rows + (size_t)p * m;
+    uint64_t prod = 1;
+    bool skip = false, ov = false;
+    int r = fr[0];
+    for (int n0 = 0; n0 < m; n0 += 4) {
+      int x4[4];
+      if (VEC) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(row + n0));
+        x4[0] = v.x, x4[1] = v.y, x4[2] = v.z, x4[3] = v.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x4[u] = (n0 + u < m) ? __ldg(row + n0 + u) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = n0 + u;
+        if (n >= m) break;
+        const int32_t x = x4[u];
+        const int r1 = fr[n + 1];
+        uint32_t cnt = 0;
+        for (; r < r1; ++r) cnt += rule_applies(x, rule[r]) ? 1u : 0u;
+        if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
+        ov |= x > INT32_MAX - __ldg(s.gain + n);
+        skip |= max_expand >= 0 && x > max_expand;
+      }
+    }
+    psi[p] = skip ? 0ull : prod;
+    over |= ov && !skip;
+  }
+  if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
+}
+
+int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ChunkState* st,
+               cudaStream_t stream, int nsm) {
+  const size_t table = (size_t)s.R * sizeof(int4) + (size_t)(s.m + 1) * sizeof(int32_t);
+  const bool smem = table <= (96u << 10);
+  const bool vec = (s.m % 4) == 0;
+  const int threads = 256;
+  const int64_t want = (P + threads - 1) / threads;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
+  auto fn = smem ? (vec ? k_psi<true, true> : k_psi<true, false>) : (vec ? k_psi<false, true> : k_psi<false, false>);
+  const size_t bytes = smem ? table : 0;
+  if (bytes > (48u << 10)) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  fn<<<blocks, threads, bytes, stream>>>(s, rows, P, max_expand, psi, st);
+  return 1;
 }
 
 // One bit per first occurrence: every candidate lid that claimed a key
@@ -84,46 +124,55 @@ __global__ void k_popc(const uint32_t* bits, uint32_t* cnt, uint32_t nwords) {
     cnt[i] = __popc(bits[i]);
 }
 
+// Largest p in [0, P) with off[p] <= g, by one thread.
+__device__ __forceinline__ int64_t find_parent(const uint64_t* off, int64_t P, uint64_t g) {
+  int64_t lo = 0, hi = P;
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (__ldg(off + mid) <= g) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 // Accepts first occurrences of rank < remaining (discovery order), rejects the
-// rest.  One warp per bitmap word.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_commit(CommitArgs a) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+// rest.  One warp per bitmap word, one lane per set bit.
+__global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
+  const int lane = threadIdx.x & 31;
   const int m = a.sys.m;
-  const uint64_t nw = (uint64_t)gridDim.x * kWarpsPerBlock;
-  for (uint64_t wd = (uint64_t)blockIdx.x * kWarpsPerBlock + wib; wd < a.nwords; wd += nw) {
+  const bool vec = (m % 4) == 0;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t wd = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wd < a.nwords; wd += nw) {
     const uint32_t word = a.bits[wd];
-    uint32_t rest = word;
-    while (rest) {
-      const int b = __ffs(rest) - 1;
-      rest &= rest - 1;
-      const uint32_t lid = (uint32_t)wd * 32u + (uint32_t)b;
-      const uint64_t rank = (uint64_t)a.wbase[wd] + __popc(word & ((1u << b) - 1u));
-      const uint32_t s = a.srow[lid];
-      unsigned long long* slot = a.table.slots + a.slot_of[s];
-      const unsigned long long hi = (*slot) & 0xFFFFFFFF00000000ull;
-      if (rank < a.remaining) {
-        const int64_t row = a.row_base + (int64_t)rank;
-        const int32_t* src = a.staging + (size_t)s * m;
-        int32_t* dst = a.pool + (size_t)row * m;
-        for (int n = lane; n < m; n += 32) dst[n] = __ldcg(src + n);
-        if (lane == 0) {
-          *slot = hi | (uint32_t)row;
-          if (rank + 1 == a.remaining) {
-            a.st->capped = 1;
-            a.st->last_lid = lid;
-          }
-        }
-        if (a.rec_parent) {
-          const uint64_t g = a.g0 + lid;
-          const int64_t p = warp_find_parent(a.off, a.P, g, lane);
-          if (lane == 0) {
-            a.rec_parent[row] = a.parent_base + p;
-            a.rec_index[row] = g - a.off[p];
-          }
-        }
-      } else if (lane == 0) {
-        *slot = hi | kRowTomb;
+    if (!((word >> lane) & 1u)) continue;
+    const uint32_t lid = (uint32_t)wd * 32u + (uint32_t)lane;
+    const uint64_t rank = (uint64_t)a.wbase[wd] + __popc(word & ((1u << lane) - 1u));
+    const uint32_t s = a.srow[lid];
+    unsigned long long* slot = a.table.slots + a.slot_of[s];
+    const unsigned long long hi = (*slot) & 0xFFFFFFFF00000000ull;
+    if (rank < a.remaining) {
+      const int64_t row = a.row_base + (int64_t)rank;
+      const int32_t* src = a.staging + (size_t)s * m;
+      int32_t* dst = a.pool + (size_t)row * m;
+      if (vec) {
+        const int4* s4 = reinterpret_cast<const int4*>(src);
+        int4* d4 = reinterpret_cast<int4*>(dst);
+        for (int j = 0; j < (m >> 2); ++j) d4[j] = __ldcg(s4 + j);
+      } else {
+        for (int j = 0; j < m; ++j) dst[j] = __ldcg(src + j);
       }
+      *slot = hi | (uint32_t)row;
+      if (rank + 1 == a.remaining) {
+        a.st->capped = 1;
+        a.st->last_lid = lid;
+      }
+      if (a.rec_parent) {
+        const uint64_t g = a.g0 + lid;
+        const int64_t p = find_parent(a.off, a.P, g);
+        a.rec_parent[row] = a.parent_base + p;
+        a.rec_index[row] = g - __ldg(a.off + p);
+      }
+    } else {
+      *slot = hi | kRowTomb;
     }
   }
 }
@@ -140,9 +189,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_insert_rows(DevSys s, c
   const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t r = r0 + (int64_t)blockIdx.x * kWarpsPerBlock + wib; r < r1; r += nw) {
     const int32_t* row = pool + (size_t)r * s.m;
-    uint64_t h = 0;
-    for (int n = lane; n < s.m; n += 32) h += col_hash(n, row[n]);
-    h = warp_sum_u64(h);
+    const uint64_t h = fingerprint(s, row, lane);
     if (lane == 0) {
       const unsigned long long val = ((unsigned long long)fp32_of(h) << 32) | (uint32_t)r;
       uint64_t b = h & t.bmask;

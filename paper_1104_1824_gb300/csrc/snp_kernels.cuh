@@ -45,8 +45,9 @@ struct CommitArgs {
   ChunkState* st;
 };
 
-__global__ void k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi,
-                      ChunkState* st);
+// Step (a) and Psi for P frontier rows; returns the launches made.
+int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ChunkState* st,
+               cudaStream_t stream, int nsm);
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
