@@ -42,12 +42,17 @@ WORKLOADS = {
     "random64": dict(seed=1, depth=8, cap=1 << 20, budget=1 << 24,
                      desc="random SNP system seed 1: m=64, 2-3 rules/neuron, a^i(a^j)* with i U[1,4], j U{0,1,2}, "
                           "c U[1,i], p U{1,2} (15% forgetting), out-degree 4, C0 U[0,6]; BFS depth 8, "
-                          "frontier cap 2^20, candidate budget 2^24, sparse int32 transition"),
+                          "frontier cap 2^20, candidate budget 2^24",
+                     # the oracle runs the workload's first two depths, exactly
+                     cpu_sample=dict(depth=2, cap=1 << 20, budget=1 << 24),
+                     ref_sample=dict(depth=2, cap=1 << 16, budget=1 << 20)),
+    "dense1024": dict(seed=3, depth=4, cap=1 << 22, budget=1 << 26, chunk=1 << 16,
+                      desc="random SNP system seed 3: m=1024, 4 rules/neuron (R=4096), out-degree 64, c U[1,8], "
+                           "i U[c,8], j U{0,1,2}, p U[1,8], C0 U[0,16]; BFS depth 4, frontier cap 2^22, candidate "
+                           "budget 2^26, 65536 spiking vectors per pass",
+                      cpu_sample=dict(depth=1, cap=1 << 12, budget=1 << 14),
+                      ref_sample=dict(depth=1, cap=1 << 11, budget=1 << 13)),
 }
-# The CPU baseline runs the oracle on the workload's first two depths, exactly.
-CPU_SAMPLE = dict(depth=2, cap=1 << 20, budget=1 << 24)
-# Each step of the reference arm: the first two depths with a smaller cap and budget.
-REF_SAMPLE = dict(depth=2, cap=1 << 16, budget=1 << 20)
 
 
 def rank_info():
@@ -57,7 +62,7 @@ def rank_info():
 def make_system(name):
     import snp_synth
     w = WORKLOADS[name]
-    return snp_synth.random_64(w["seed"])
+    return snp_synth.random_64(w["seed"]) if name == "random64" else snp_synth.dense_1024(w["seed"])
 
 
 class ClockSampler:
@@ -181,7 +186,9 @@ def bench_ours(args):
     system = make_system(args.workload)
     s = snp.System(system)
     stream = torch.cuda.Stream(device=dev)
-    kw = dict(cap=w["cap"], budget=w["budget"], stream=stream)
+    tc = args.transition == "tc"
+    kw = dict(cap=w["cap"], budget=w["budget"], stream=stream, chunk=w.get("chunk", 0),
+              transition=snp.SNP_T_TC_I8 if tc else snp.SNP_T_SPARSE_I32)
     for _ in range(args.warmup):
         s.explore(w["depth"], **kw)
     if world > 1:
@@ -223,41 +230,58 @@ def bench_ours(args):
         ms_max, total_all, launches_all = ms, total_new, launches
     value = total_all / (ms_max * 1e-3)
 
-    # roofline of the dominant kernel (the expand kernel: steps (b)-(d) per candidate)
-    peak, peak_kind = measured_peaks()
-    achieved = expand_bytes / (expand_ms * 1e-3) / 1e9 if expand_ms > 0 else None
-    traffic = profiled_traffic(args.workload)
     nlaunch_expand = sum(x.chunks for x in st) * args.steps
-    roofline = {
-        "kernel": "k_claim (expand: decode, C' = C + S.M, fingerprint, probe/claim)",
-        "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
-        "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-        "frac": round(achieved / peak, 4) if achieved else None,
-        "algorithmic_bytes_per_launch": int(expand_bytes / max(1, nlaunch_expand)),
-        "avg_launch_ms": round(expand_ms / max(1, nlaunch_expand), 4),
-        "traffic": (int(traffic["bytes_per_candidate"] * candidates / max(1, nlaunch_expand)) if traffic else None),
-        "expand_share_of_step": round(expand_ms / ms, 4) if ms > 0 else None,
-    }
+    if tc:
+        # the tensor-core pass: dense 2 * R * m int8 operations per candidate
+        peak = snp.snp_tc_peak_tops(20000)
+        ops = 2.0 * system.R * system.m * candidates
+        achieved = ops / (expand_ms * 1e-3) / 1e12 if expand_ms > 0 else None
+        roofline = {
+            "kernel": "k_tc_digits + k_tc_rows (mma.sync m16n8k32 s8) + k_resolve_rows, per pass",
+            "bound": "tensor", "achieved": round(achieved, 2) if achieved else None, "peak": round(peak, 1),
+            "peak_kind": "measured mma.sync m16n8k32 s8 rate on this GPU (snp_tc_peak_tops)", "unit": "TOPS",
+            "frac": round(achieved / peak, 4) if achieved else None,
+            "algorithmic_ops_per_launch": int(ops / max(1, nlaunch_expand)),
+            "avg_launch_ms": round(expand_ms / max(1, nlaunch_expand), 4), "traffic": None,
+            "expand_share_of_step": round(expand_ms / ms, 4) if ms > 0 else None,
+        }
+    else:
+        # the expand kernel: steps (b)-(d) per candidate
+        peak, peak_kind = measured_peaks()
+        achieved = expand_bytes / (expand_ms * 1e-3) / 1e9 if expand_ms > 0 else None
+        traffic = profiled_traffic(args.workload)
+        roofline = {
+            "kernel": "k_expand (decode, C' = C + S.M, hash, probe/compare/claim)",
+            "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+            "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+            "frac": round(achieved / peak, 4) if achieved else None,
+            "algorithmic_bytes_per_launch": int(expand_bytes / max(1, nlaunch_expand)),
+            "avg_launch_ms": round(expand_ms / max(1, nlaunch_expand), 4),
+            "traffic": (int(traffic["bytes_per_candidate"] * candidates / max(1, nlaunch_expand)) if traffic else None),
+            "expand_share_of_step": round(expand_ms / ms, 4) if ms > 0 else None,
+        }
 
     e2e = None
     if not args.no_e2e:
         e2e = bench_e2e(args, system, w, snp, torch, dev)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        new, dt = run_cpu_baseline(system, CPU_SAMPLE)
+        cs = w["cpu_sample"]
+        new, dt = run_cpu_baseline(system, cs)
         cpu = {"value": round(new / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"the workload's first {CPU_SAMPLE['depth']} depths exactly (cap 2^20, budget 2^24): "
+               "sample": f"the workload's first {cs['depth']} depth(s) with cap {cs['cap']} and budget {cs['budget']}: "
                          f"{new} new configurations in {dt:.2f} s, single-threaded C++ oracle",
                "seconds": round(dt, 2)}
     if rank == 0:
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8" if tc else "int32", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w['desc']}", "depth": w["depth"], "frontier_cap": w["cap"],
-                       "candidate_budget": w["budget"], "transition": "sparse_i32",
+                       "candidate_budget": w["budget"], "transition": "tc_i8" if tc else "sparse_i32",
                        "new_per_step": total_new // args.steps,
-                       "l2": "inputs larger than L2 (2.1 GB of configurations written per step)",
+                       "l2": f"inputs larger than L2 ({total_new // args.steps * system.m * 4 / 1e9:.1f} GB of "
+                             "configurations written per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "per_depth": per_depth,
             "roofline": roofline,
@@ -287,6 +311,8 @@ def bench_e2e(args, system, w, snp, torch, dev):
         h = snp.snp_load_system(system.m, *arrays)
         o = snp.snp_explore_opts_init()
         o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
+        o.chunk = w.get("chunk", 0)
+        o.transition = snp.SNP_T_TC_I8 if args.transition == "tc" else snp.SNP_T_SPARSE_I32
         snp.snp_explore(h, o)
         n = snp.snp_reachable_count(h)
         if host_out is None or host_out.shape[0] < n:
@@ -306,15 +332,16 @@ def bench_reference(args):
     if rank != 0:
         return
     system = make_system(args.workload)
+    rs = WORKLOADS[args.workload]["ref_sample"]
     for _ in range(args.warmup):
-        run_cpu_baseline(system, REF_SAMPLE)
+        run_cpu_baseline(system, rs)
     total_new, total_s = 0, 0.0
     for _ in range(args.steps):
-        new, dt = run_cpu_baseline(system, REF_SAMPLE)
+        new, dt = run_cpu_baseline(system, rs)
         total_new += new
         total_s += dt
     value = total_new / total_s
-    sample = (f"per step the workload's first {REF_SAMPLE['depth']} depths with cap 2^16 and budget 2^20 "
+    sample = (f"per step the workload's first {rs['depth']} depth(s) with cap {rs['cap']} and budget {rs['budget']} "
               f"({total_new // args.steps} new configurations), single-threaded C++ oracle")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_s / args.steps * 1e3, 3),
@@ -335,6 +362,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
+    ap.add_argument("--transition", choices=["sparse", "tc"], default="sparse",
+                    help="step (c): sparse int32 gather, or the exact int8 tensor-core product")
     args = ap.parse_args()
     if args.depth > 0:
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], depth=args.depth)

@@ -50,7 +50,7 @@ extern "C" {
 
 /* Transition forms for step (c). */
 #define SNP_T_SPARSE_I32 0 /* gather over M_Pi's nonzeros, int32 on the CUDA cores */
-#define SNP_T_TC_I8 1      /* dense 0/1 x int8 tensor-core product, int32 accumulation */
+#define SNP_T_TC_I8 1      /* dense 0/1 x int8 tensor-core product (mma.sync s8), int32 accumulation */
 
 /* Saturation value of Psi and of sums of Psi: "at least 2^64 - 1". */
 #define SNP_PSI_SAT UINT64_MAX
@@ -218,6 +218,14 @@ int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out);
  * SNP_E_TIMEOUT, SNP_E_INTERNAL, SNP_E_CUDA. */
 int snp_explore_static(snp_handle h, const snp_explore_opts* opts, int32_t* out, int64_t capacity, int64_t* n,
                        int32_t* depth_reached, int64_t* per_depth_new);
+
+/* Measures the int8 tensor-core rate of the current device (mma.sync
+ * m16n8k32, s8 x s8 -> s32, the instruction SNP_T_TC_I8 uses): *tops receives
+ * tera-operations per second (2 per multiply-add) over `iters` rounds of 8
+ * independent products per warp on 8 blocks per SM.  A measurement utility for
+ * the tensor-core roofline; the paper has no counterpart.  Allocates a small
+ * device buffer.  Returns 0, or 1 (bad arguments), 3 (no memory), 4 (CUDA). */
+int snp_tc_peak_tops(int32_t iters, double* tops);
 
 /* Message for the last failed call on this thread ("" if none). */
 const char* snp_last_error(void);

@@ -41,7 +41,8 @@ ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOME
 
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
-           "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static"]
+           "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
+           "snp_tc_peak_tops"]
 
 
 class SnpError(RuntimeError):
@@ -95,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     lib.snp_depth_stats.argtypes = [vp, i32, ctypes.POINTER(snp_depth_info)]
     lib.snp_explore_static.argtypes = [vp, ctypes.POINTER(snp_explore_opts), vp, i64, ctypes.POINTER(i64),
                                        ctypes.POINTER(i32), vp]
+    lib.snp_tc_peak_tops.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     lib.snp_last_error.restype = ctypes.c_char_p
     lib.snp_last_error.argtypes = []
     lib.snp_abi_version.restype = ctypes.c_int
@@ -198,6 +200,15 @@ def snp_explore_static(h, opts: snp_explore_opts, out, capacity: int,
     _check(load_library().snp_explore_static(h, ctypes.byref(opts), _ptr(out), int(capacity), ctypes.byref(n),
                                              ctypes.byref(dr), _ptr(per_depth_new)))
     return n.value, dr.value
+
+
+def snp_tc_peak_tops(iters: int = 20000) -> float:
+    """Measured int8 tensor-core rate (mma.sync m16n8k32) of the current device, TOPS."""
+    v = ctypes.c_double()
+    rc = load_library().snp_tc_peak_tops(int(iters), ctypes.byref(v))
+    if rc != 0:
+        raise SnpError(SNP_E_CUDA, f"snp_tc_peak_tops returned {rc}")
+    return v.value
 
 
 def snp_depth_stats(h, d: int) -> snp_depth_info:

@@ -117,7 +117,11 @@ struct snp_system {
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_M8;
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey;
+  // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
+  DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash;
+  int32_t Rp = 0, mp = 0, mt_rows = 0;
+  uint64_t tc_cap = 0;  // candidates the tensor-core chunk buffers hold
   std::vector<unsigned long long> colkey, rowkey;
   // exploration state
   DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_psi, d_off, d_scan_tmp, d_st,
@@ -197,6 +201,40 @@ int ensure_chunk_buffers(snp_system* h, uint64_t q, cudaStream_t st) {
   CK(cudaMemsetAsync(h->d_bits.p, 0, sizeof(uint32_t) * words, st));
   CK(cudaMemsetAsync(h->d_own.p, 0, sizeof(uint32_t) * words, st));
   h->q_cap = q;
+  return SNP_OK;
+}
+
+// Tensor-core form: M_Pi^T in int8 (zero padded) and the rule maps, uploaded
+// on first use; chunk buffers for up to q candidates.
+int tc_prepare(snp_system* h, uint64_t q, cudaStream_t st) {
+  if (!h->d_MT.p) {
+    const int m = h->m, R = h->R;
+    h->Rp = (R + 31) / 32 * 32;
+    h->mp = (m + 3) / 4 * 4;
+    h->mt_rows = (m + 127) / 128 * 128;
+    std::vector<int8_t> mt((size_t)h->mt_rows * h->Rp, 0);
+    for (int r = 0; r < R; ++r)
+      for (int j = 0; j < m; ++j) mt[(size_t)j * h->Rp + r] = (int8_t)h->M[(size_t)r * m + j];
+    std::vector<int16_t> rn(h->Rp, -1);
+    std::vector<uint8_t> rk(h->Rp, 0);
+    for (int r = 0; r < R; ++r) {
+      rn[r] = (int16_t)h->rule_neuron[r];
+      rk[r] = (uint8_t)(r - h->first_rule[h->rule_neuron[r]]);
+    }
+    TRY(h->d_MT.reserve(mt.size()));
+    TRY(h->d_rn.reserve(sizeof(int16_t) * h->Rp));
+    TRY(h->d_rk.reserve(h->Rp));
+    CK(cudaMemcpy(h->d_MT.p, mt.data(), mt.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_rn.p, rn.data(), sizeof(int16_t) * h->Rp, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_rk.p, rk.data(), h->Rp, cudaMemcpyHostToDevice));
+  }
+  if (h->tc_cap < q) {
+    TRY(h->d_loc.reserve((size_t)q * h->mp));
+    TRY(h->d_pidx.reserve(sizeof(uint32_t) * q));
+    TRY(h->d_rows.reserve(sizeof(int32_t) * (size_t)q * h->m));
+    TRY(h->d_hash.reserve(sizeof(unsigned long long) * q));
+    h->tc_cap = q;
+  }
   return SNP_OK;
 }
 
@@ -423,12 +461,17 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
   const int nsm = sm_count(h->device);
   const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
   const int64_t budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
-  if (o->transition == SNP_T_TC_I8) return fail(SNP_E_INVALID, "int8 tensor-core transition not built");
+  const bool tc = o->transition == SNP_T_TC_I8;
 
-  // Chunk size bound: staging of at most ~512 MiB.
+  // Chunk size bound: staging of at most ~512 MiB; the tensor-core form works
+  // on chunks of at most 65536 spiking vectors.
   uint64_t qmax = o->chunk > 0 ? (uint64_t)o->chunk
                                : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 29) / (4ull * m)));
   qmax = std::min<uint64_t>(qmax, 1ull << 30);
+  if (tc) {
+    qmax = std::min<uint64_t>(qmax, 1ull << 16);
+    TRY(tc_prepare(h, qmax, st));
+  }
   // Pool: exact when capped, growing otherwise.
   int64_t rows_plan = 1 << 12;
   if (cap > 0) {
@@ -550,10 +593,21 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         a.ownbits = h->d_own.as<uint32_t>();
         a.st = h->d_st.as<ChunkState>();
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
-        launch_expand(a, st, nsm);
+        if (tc) {
+          launch_tc_digits(a.sys, parents, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
+                           h->d_pidx.as<uint32_t>(), st, nsm);
+          CK(cudaMemsetAsync(h->d_hash.p, 0, sizeof(unsigned long long) * Q, st));
+          launch_tc_rows(a.sys, parents, h->d_loc.as<uint8_t>(), h->mp, h->d_pidx.as<uint32_t>(), (uint32_t)Q,
+                         h->d_MT.as<int8_t>(), h->Rp, h->d_rn.as<int16_t>(), h->d_rk.as<uint8_t>(),
+                         h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), st);
+          launch_resolve_rows(a, h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), st, nsm);
+          sd.launches += 3;
+        } else {
+          launch_expand(a, st, nsm);
+          sd.launches += 1;
+        }
         CK(cudaGetLastError());
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[1], st));
-        sd.launches += 1;
       }
       const uint32_t nwords = (uint32_t)((Q + 31) / 32);
       k_mark<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_own.as<uint32_t>(), h->d_gmin.as<uint32_t>(),

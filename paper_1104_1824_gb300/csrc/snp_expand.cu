@@ -393,7 +393,37 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   }
 }
 
+// Step (d) for rows already built in global memory (the tensor-core form):
+// one lane per candidate, the same bounded wait-free passes as k_expand.
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t* rows,
+                                                      const unsigned long long* hash) {
+  const int m = a.sys.m;
+  for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < a.Q; base += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t lid = base + threadIdx.x;
+    bool done = lid >= a.Q;
+    const uint64_t key = done ? 0ull : mix64(hash[lid]);
+    for (int pass = 0;; ++pass) {
+      if (!done) done = resolve_lane<VEC>(a, rows + lid * m, key, (uint32_t)lid);
+      if (__all_sync(0xffffffffu, done)) break;
+      if (pass >= kSpinLimit) {
+        if (!done) atomicOr(&a.st->error, kErrTimeout);
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+}
+
 }  // namespace
+
+void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, cudaStream_t st, int nsm) {
+  const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)a.Q + 255) / 256, (uint64_t)nsm * 8));
+  if (a.sys.m % 4 == 0)
+    k_resolve_rows<true><<<blocks, 256, 0, st>>>(a, rows, hash);
+  else
+    k_resolve_rows<false><<<blocks, 256, 0, st>>>(a, rows, hash);
+}
 
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const int m = a.sys.m;

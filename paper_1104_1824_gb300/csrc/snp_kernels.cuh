@@ -50,6 +50,15 @@ int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uin
                cudaStream_t stream, int nsm);
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
+// Step (d) for candidate rows already in global memory (rows[lid * m], hash[lid]).
+void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, cudaStream_t st, int nsm);
+// Tensor-core form of step (c) (snp_tc.cu).
+void launch_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P, uint64_t g0, uint32_t Q,
+                      uint8_t* loc, int mp, uint32_t* pidx, cudaStream_t st, int nsm);
+void launch_tc_rows(DevSys s, const int32_t* parents, const uint8_t* loc, int mp, const uint32_t* pidx, uint32_t Q,
+                    const int8_t* MT, int Rp, const int16_t* rn, const uint8_t* rk, int32_t* rows,
+                    unsigned long long* hash, cudaStream_t st);
+size_t tc_rows_smem(int mp);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);

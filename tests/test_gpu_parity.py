@@ -264,3 +264,70 @@ def test_state_and_buffer_errors(gpu):
     with pytest.raises(gpu.SnpError) as ei:
         gpu.snp_parents(s.h, None, None, 100)
     assert ei.value.code == gpu.SNP_E_STATE
+
+
+# --- the exact int8 tensor-core transition (SNP_T_TC_I8) ---
+
+def explore_tc(gpu, system, depth, **kw):
+    s = gpu.System(system)
+    s.explore(depth, transition=gpu.SNP_T_TC_I8, **kw)
+    return s
+
+
+def test_tc_paper_example_and_replay(gpu):
+    g = read_golden("paper_run.txt")
+    paper = snp_synth.paper_example()
+    s = explore_tc(gpu, paper, 10)
+    assert_same(s, oracle.Oracle(paper).explore(10))
+    s = explore_tc(gpu, paper, 1000, max_expand=9)
+    assert ["-".join(str(int(x)) for x in r) for r in s.reachable()] == g["allGenCk"].split()
+
+
+@pytest.mark.parametrize("cap,budget,chunk", [(0, 0, 0), (3, 0, 1), (5, 11, 3), (2, 1, 0)])
+def test_tc_tiny_systems(gpu, cap, budget, chunk):
+    rng = np.random.default_rng(2000 + 7 * cap + 13 * budget + chunk)
+    for _ in range(25):
+        system = bf.tiny_system(rng, m_max=4, r_max=9)
+        s = explore_tc(gpu, system, 5, cap=cap, budget=budget, chunk=chunk)
+        assert_same(s, oracle.Oracle(system).explore(5, cap=cap, budget=budget))
+
+
+@pytest.mark.parametrize("m", [1, 5, 31, 64, 100, 129, 257, 1024])
+def test_tc_neuron_counts(gpu, m):
+    system = snp_synth.random_system(700 + m, m, (1, 4), (1, min(8, max(1, m - 1))), (0, 6), "sparse")
+    s = explore_tc(gpu, system, 3, cap=300, budget=3000)
+    assert_same(s, oracle.Oracle(system).explore(3, cap=300, budget=3000))
+
+
+def test_tc_random64_small(gpu):
+    g = golden_digests()["random64_seed1_small"]
+    p = g["params"]
+    s = explore_tc(gpu, snp_synth.random_64(1), p["depth"], cap=p["cap"], budget=p["budget"])
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in s.depth_stats()] == g["per_depth"]
+    assert digest(s.reachable()) == g["sha256"]
+
+
+def test_tc_dense1024_matches_sparse_and_oracle(gpu):
+    g = golden_digests()["dense1024_seed3_small"]
+    p = g["params"]
+    system = snp_synth.dense_1024(3)
+    s = explore_tc(gpu, system, p["depth"], cap=p["cap"], budget=p["budget"])
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in s.depth_stats()] == g["per_depth"]
+    assert digest(s.reachable()) == g["sha256"]
+    sp = gpu.System(system)
+    sp.explore(p["depth"], cap=p["cap"], budget=p["budget"])
+    assert (sp.reachable() == s.reachable()).all()
+
+
+def test_tc_refuses_entries_beyond_int8(gpu):
+    system = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [200, 1], [[1], [0]], [3, 3])
+    s = gpu.System(system)
+    with pytest.raises(gpu.SnpError) as ei:
+        s.explore(2, transition=gpu.SNP_T_TC_I8)
+    assert ei.value.code == gpu.SNP_E_RANGE
+    s.explore(2)  # the sparse path takes it
+
+
+def test_tc_peak_probe(gpu):
+    tops = gpu.snp_tc_peak_tops(2000)
+    assert tops > 1.0
