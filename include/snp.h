@@ -101,6 +101,9 @@ typedef struct {
  *  stream            cudaStream_t to run on, or NULL for the default stream.
  *  kernel_timing     1: time the expand kernel of every pass with CUDA events
  *                    on `stream` (snp_depth_info.expand_ms).
+ *  tile              candidates a warp builds together (batch engine); <= 0:
+ *                    automatic.
+ *  warps             warps per CTA of the batch engine (4 or 8); <= 0: automatic.
  * Candidate order ("canonical order"): parents in discovery order; for each,
  * its valid spiking vectors in mixed-radix order with neuron 0's choice most
  * significant and the last neuron's least; a neuron's choices are its
@@ -115,8 +118,10 @@ typedef struct {
   int64_t chunk;
   void* stream;
   int32_t kernel_timing;
+  int32_t tile;
+  int32_t warps;
   int32_t reserved0;
-  int64_t reserved[3];
+  int64_t reserved[2];
 } snp_explore_opts;
 
 /* Statistics of one BFS depth (index 0 is the root level). */
@@ -188,6 +193,32 @@ int snp_parents(snp_handle h, int64_t* parent, uint64_t* index, int64_t capacity
 /* Statistics of depth d (0 <= d <= depth_reached + 1) of the last
  * exploration.  Errors: SNP_E_STATE, SNP_E_INVALID. */
 int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out);
+
+/* Breadth-first exploration of n independent systems at once (the batch
+ * engine): every system runs exactly what snp_explore would run on it with
+ * the same options, and afterwards each handle answers snp_reachable,
+ * snp_depth_stats and friends for its own exploration.  All systems advance
+ * together, one device launch per depth (captured in a CUDA graph); a CTA
+ * takes one system at a time and runs its whole depth.
+ *  hs        [n] host array of handles, all on the current device, distinct.
+ *  opts      depth, frontier_cap (required: 1 <= cap <= 2^20), candidate_budget,
+ *            max_expand_value, chunk (candidates per pass, <= 0: 2048),
+ *            tile, warps, stream; transition must be SNP_T_SPARSE_I32 and
+ *            record_parents 0.
+ *  statuses  (host, [n], may be NULL) per system: SNP_OK, SNP_E_OVERFLOW,
+ *            SNP_E_TIMEOUT or SNP_E_INTERNAL.
+ * The systems' configurations live in one device arena shared by the handles
+ * until each is freed or explored again.  Returns SNP_OK when the batch ran
+ * (check statuses), else SNP_E_INVALID, SNP_E_NOMEM, SNP_E_CUDA. */
+int snp_explore_batch(snp_handle* hs, int32_t n, const snp_explore_opts* opts, int32_t* statuses);
+
+/* Chooses the batch engine's pass size, tile and warps per CTA for this batch
+ * by timing the first two depths of each candidate setting (on the real
+ * systems; their previous results are discarded).  *chunk, *tile and *warps
+ * receive the fastest setting, for snp_explore_batch's options.  Errors as
+ * snp_explore_batch. */
+int snp_batch_autotune(snp_handle* hs, int32_t n, const snp_explore_opts* opts, int32_t* chunk, int32_t* tile,
+                       int32_t* warps);
 
 /* snp_explore without allocating memory: the paper has no counterpart; this
  * is for callers that may not allocate device memory at the moment they need

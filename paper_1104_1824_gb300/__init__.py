@@ -42,7 +42,7 @@ ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOME
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
            "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
-           "snp_tc_peak_tops"]
+           "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune"]
 
 
 class SnpError(RuntimeError):
@@ -62,7 +62,8 @@ class snp_explore_opts(ctypes.Structure):
                 ("frontier_cap", ctypes.c_int64), ("candidate_budget", ctypes.c_int64),
                 ("max_expand_value", ctypes.c_int32), ("record_parents", ctypes.c_int32),
                 ("chunk", ctypes.c_int64), ("stream", ctypes.c_void_p), ("kernel_timing", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("reserved", ctypes.c_int64 * 3)]
+                ("tile", ctypes.c_int32), ("warps", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("reserved", ctypes.c_int64 * 2)]
 
 
 class snp_depth_info(ctypes.Structure):
@@ -97,6 +98,9 @@ def load_library(path: str = LIB_PATH):
     lib.snp_explore_static.argtypes = [vp, ctypes.POINTER(snp_explore_opts), vp, i64, ctypes.POINTER(i64),
                                        ctypes.POINTER(i32), vp]
     lib.snp_tc_peak_tops.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+    lib.snp_explore_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(snp_explore_opts), vp]
+    lib.snp_batch_autotune.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(snp_explore_opts),
+                                       ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.snp_last_error.restype = ctypes.c_char_p
     lib.snp_last_error.argtypes = []
     lib.snp_abi_version.restype = ctypes.c_int
@@ -209,6 +213,41 @@ def snp_tc_peak_tops(iters: int = 20000) -> float:
     if rc != 0:
         raise SnpError(SNP_E_CUDA, f"snp_tc_peak_tops returned {rc}")
     return v.value
+
+
+def _handle_array(handles):
+    arr = (ctypes.c_void_p * len(handles))()
+    for k, h in enumerate(handles):
+        arr[k] = h.value if isinstance(h, ctypes.c_void_p) else h
+    return arr
+
+
+def snp_explore_batch(handles, opts: snp_explore_opts, statuses: Optional[np.ndarray] = None) -> None:
+    """Explores the systems of `handles` together (one launch per depth)."""
+    arr = _handle_array(handles)
+    _check(load_library().snp_explore_batch(arr, len(handles), ctypes.byref(opts), _ptr(statuses)))
+
+
+def snp_batch_autotune(handles, opts: snp_explore_opts) -> Tuple[int, int, int]:
+    """(chunk, tile, warps) that run this batch fastest."""
+    arr = _handle_array(handles)
+    c, t, w = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().snp_batch_autotune(arr, len(handles), ctypes.byref(opts), ctypes.byref(c), ctypes.byref(t),
+                                             ctypes.byref(w)))
+    return c.value, t.value, w.value
+
+
+def explore_batch(systems, depth: int, cap: int, budget: int = 0, max_expand: int = -1, chunk: int = 0,
+                  tile: int = 0, warps: int = 0, stream=None) -> np.ndarray:
+    """Convenience: snp_explore_batch over System objects; returns the statuses."""
+    o = snp_explore_opts_init()
+    o.depth, o.frontier_cap, o.candidate_budget, o.max_expand_value = int(depth), int(cap), int(budget), int(max_expand)
+    o.chunk, o.tile, o.warps, o.stream = int(chunk), int(tile), int(warps), _stream_handle(stream)
+    st = np.zeros(len(systems), dtype=np.int32)
+    snp_explore_batch([s.h for s in systems], o, st)
+    for s in systems:
+        s.depth_reached = max(d for d, x in enumerate(s.depth_stats()) if x.new > 0)
+    return st
 
 
 def snp_depth_stats(h, d: int) -> snp_depth_info:

@@ -8,12 +8,11 @@
 #include <string>
 #include <vector>
 
-#include "snp.h"
-#include "snp_kernels.cuh"
+#include "snp_host.h"
 
 using namespace snp;
 
-namespace {
+namespace snp {
 
 thread_local std::string g_err;
 
@@ -27,150 +26,18 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
-#define CK(x)                                                                                    \
-  do {                                                                                           \
-    cudaError_t e_ = (x);                                                                        \
-    if (e_ != cudaSuccess) {                                                                     \
-      if (e_ == cudaErrorMemoryAllocation) {                                                     \
-        cudaGetLastError();                                                                      \
-        return fail(SNP_E_NOMEM, "%s: %s", #x, cudaGetErrorString(e_));                          \
-      }                                                                                          \
-      return fail(SNP_E_CUDA, "%s (%s:%d): %s", #x, __FILE__, __LINE__, cudaGetErrorString(e_)); \
-    }                                                                                            \
-  } while (0)
-
-#define TRY(x)              \
-  do {                      \
-    int r_ = (x);           \
-    if (r_ != SNP_OK) return r_; \
-  } while (0)
-
-// A device allocation that grows on demand (contents are not preserved unless asked).
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  ~DevBuf() { release(); }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
   }
-  int reserve(size_t want, cudaStream_t st = nullptr, bool keep = false) {
-    if (want <= bytes) return SNP_OK;
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, want);
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      return fail(SNP_E_NOMEM, "cudaMalloc(%zu bytes): %s", want, cudaGetErrorString(e));
-    }
-    if (keep && p && bytes) {
-      e = cudaMemcpyAsync(q, p, bytes, cudaMemcpyDeviceToDevice, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) {
-        cudaFree(q);
-        return fail(SNP_E_CUDA, "grow copy: %s", cudaGetErrorString(e));
-      }
-    }
-    release();
-    p = q;
-    bytes = want;
-    return SNP_OK;
-  }
-  template <typename T>
-  T* as() const {
-    return static_cast<T*>(p);
-  }
-};
-
-// Pinned host words the depth loop reads back: chunk counters and one u64.
-struct PinnedState {
-  ChunkState* h = nullptr;
-  uint64_t* u64 = nullptr;
-  PinnedState() {
-    void* p = nullptr;
-    if (cudaMallocHost(&p, 256) == cudaSuccess) {
-      h = static_cast<ChunkState*>(p);
-      u64 = reinterpret_cast<uint64_t*>(static_cast<char*>(p) + 128);
-    }
-  }
-  ~PinnedState() {
-    if (h) cudaFreeHost(h);
-  }
-};
-
-uint64_t pow2_at_least(uint64_t x) {
-  uint64_t p = 1;
-  while (p < x) p <<= 1;
-  return p;
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-constexpr int kWarpsPerBlock = 4;
-constexpr int kThreads = kWarpsPerBlock * 32;
-
-}  // namespace
-
-struct snp_system {
-  int device = 0;
-  int32_t m = 0, R = 0, K = 1;
-  int32_t max_abs_m = 0;
-  std::vector<int32_t> c0, M, rule_neuron, rule_i, rule_j, first_rule, gain;
-  std::vector<int4> rule;
-  std::vector<int2> csr;
-  // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey;
-  // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
-  DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash;
-  int32_t Rp = 0, mp = 0, mt_rows = 0;
-  uint64_t tc_cap = 0;  // candidates the tensor-core chunk buffers hold
-  std::vector<unsigned long long> colkey, rowkey;
-  // exploration state
-  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_psi, d_off, d_scan_tmp, d_st,
-      d_rec_parent, d_rec_index, d_tmp;
-  int64_t pool_rows = 0;  // capacity in rows
-  uint64_t nbuckets = 0;
-  uint64_t q_cap = 0;     // staging capacity in rows
-  int64_t psi_cap = 0;    // parents
-  int64_t rec_rows = 0;
-  PinnedState pin;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaEvent_t evk[2] = {nullptr, nullptr};  // around the expand kernel
-  // results
-  bool explored = false;
-  bool have_parents = false;
-  int64_t n_rows = 0;
-  int32_t depth_reached = 0;
-  std::vector<snp_depth_info> stats;
-
-  DevSys dev() const {
-    DevSys s;
-    s.m = m;
-    s.R = R;
-    s.K = K;
-    s.first_rule = d_first_rule.as<int32_t>();
-    s.rule = d_rule.as<int4>();
-    s.csr = d_csr.as<int2>();
-    s.gain = d_gain.as<int32_t>();
-    s.colkey = d_colkey.as<unsigned long long>();
-    s.rowkey = d_rowkey.as<unsigned long long>();
-    return s;
-  }
-  DevTable table() const { return DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }
-};
+}  // namespace snp
 
 namespace {
-
-int grid_for(int64_t work_items, int per_block, int max_blocks) {
-  int64_t b = (work_items + per_block - 1) / per_block;
-  if (b < 1) b = 1;
-  if (b > max_blocks) b = max_blocks;
-  return (int)b;
-}
-
-int sm_count(int device) {
-  int n = 0;
-  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
-  return n > 0 ? n : 1;
-}
 
 size_t claim_smem(int m) { return (size_t)kWarpsPerBlock * 3 * m * sizeof(int32_t); }
 
@@ -279,15 +146,6 @@ int validate_desc(const snp_system_desc* d) {
   for (int j = 0; j < d->m; ++j)
     if (d->c0[j] < 0) return fail(SNP_E_INVALID, "c0[%d] = %d < 0", j, d->c0[j]);
   return SNP_OK;
-}
-
-bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 }  // namespace
@@ -457,6 +315,8 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
   h->have_parents = false;
   h->stats.clear();
   h->depth_reached = 0;
+  h->batch.reset();
+  h->result_pool = nullptr;
   const int m = h->m;
   const int nsm = sm_count(h->device);
   const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
@@ -683,6 +543,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     level_hi = h->n_rows;
   }
   h->explored = true;
+  h->result_pool = h->d_pool.as<int32_t>();
   h->have_parents = o->record_parents != 0;
   if (depth_reached) *depth_reached = h->depth_reached;
   if (truncated_flags)
@@ -701,7 +562,7 @@ int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int6
   if (capacity < h->n_rows) return fail(SNP_E_BUFFER, "capacity %lld < %lld rows", (long long)capacity, (long long)h->n_rows);
   if (!out) return fail(SNP_E_INVALID, "out is NULL");
   CK(cudaSetDevice(h->device));
-  CK(cudaMemcpy(out, h->d_pool.p, sizeof(int32_t) * (size_t)h->m * h->n_rows, cudaMemcpyDefault));
+  CK(cudaMemcpy(out, h->result_pool, sizeof(int32_t) * (size_t)h->m * h->n_rows, cudaMemcpyDefault));
   return SNP_OK;
 }
 

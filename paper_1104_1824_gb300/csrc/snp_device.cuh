@@ -107,13 +107,14 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 }
 
 // Largest p in [0, P) with off[p] <= g (off non-decreasing, off[0] = 0 <= g).
+// Loads through L2: off may have been written earlier in the same kernel.
 __device__ __forceinline__ int64_t warp_find_parent(const uint64_t* off, int64_t P, uint64_t g, int lane) {
   int64_t lo = 0, hi = P;
   while (hi - lo > 1) {
     int64_t n = hi - lo;
     int64_t step = (n + 31) / 32;
     int64_t idx = lo + (int64_t)lane * step;
-    bool ok = idx < hi && __ldg(off + idx) <= g;
+    bool ok = idx < hi && __ldcg(off + idx) <= g;
     uint32_t b = __ballot_sync(0xffffffffu, ok);
     int L = 31 - __clz(b);
     lo = lo + (int64_t)L * step;

@@ -295,14 +295,10 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
   return true;
 }
 
-template <bool VEC>
-__global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  const DevSys& s = a.sys;
-  const int m = s.m, m4 = round4(m);
+// Per-warp shared memory of the expand loop.
+__device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, int B, int ts) {
+  const int m4 = round4(m);
   ExpandSmem w;
-  unsigned char* base = smem_raw + (size_t)wib * expand_warp_bytes(m, B, ts);
   w.tile = reinterpret_cast<int32_t*>(base);
   w.par = w.tile + (size_t)B * ts;
   w.buf = w.par + m4;
@@ -313,14 +309,22 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   w.vlow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 2);   // +72
   w.hbase = reinterpret_cast<unsigned long long*>(w.low + kLowDigits + 4);  // +80
   w.dig = reinterpret_cast<uint8_t*>(w.low) + 96;
+  return w;
+}
 
+// Steps (b)-(d) for the tasks task0, task0 + tstride, ... of chunk a (a task
+// is a run of a.run consecutive candidates), by one warp.
+template <bool VEC>
+__device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, ExpandSmem& w, uint64_t task0,
+                                            uint64_t tstride, int lane) {
+  const DevSys& s = a.sys;
+  const int m = s.m;
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
-  const uint64_t nw = (uint64_t)gridDim.x * wpb;
-  for (uint64_t task = (uint64_t)blockIdx.x * wpb + wib; task < ntasks; task += nw) {
+  for (uint64_t task = task0; task < ntasks; task += tstride) {
     const uint64_t la = task * a.run;
     const uint64_t lb = min(la + a.run, (uint64_t)a.Q);
     int64_t p = warp_find_parent(a.off, a.P, a.g0 + la, lane);
-    uint64_t p_lo = __ldg(a.off + p), p_hi = __ldg(a.off + p + 1);
+    uint64_t p_lo = __ldcg(a.off + p), p_hi = __ldcg(a.off + p + 1);
     if (task == 0 && lane == 0) a.st->p_first = (unsigned long long)p;
     uint64_t after = parent_state(s, a.parents + (size_t)p * m, w, lane);
     decode_full(s, w, a.g0 + la - p_lo, after, lane);
@@ -367,7 +371,7 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
         do {
           ++p;
           p_lo = p_hi;
-          p_hi = __ldg(a.off + p + 1);
+          p_hi = __ldcg(a.off + p + 1);
         } while (gn >= p_hi);
         after = parent_state(s, a.parents + (size_t)p * m, w, lane);
         decode_full(s, w, gn - p_lo, after, lane);
@@ -391,6 +395,14 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
     }
     if (task + 1 == ntasks && lane == 0) a.st->p_last = (unsigned long long)p;
   }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  ExpandSmem w = expand_smem(smem_raw + (size_t)wib * expand_warp_bytes(a.sys.m, B, ts), a.sys.m, B, ts);
+  expand_warp<VEC>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
 }
 
 // Step (d) for rows already built in global memory (the tensor-core form):
@@ -441,6 +453,303 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   fn<<<blocks > 0 ? blocks : 1, wpb * 32, smem, st>>>(a, B, ts);
   return 1;
+}
+
+}  // namespace snp
+
+// ---------------------------------------------------------------------------
+// Batch engine: one launch runs depth d of every system of a batch.  A CTA
+// takes systems from a work queue; for each it runs the whole depth with block
+// barriers in place of the host: Psi of its frontier (Eq. psi), the saturating
+// scan, then passes of up to qc candidates -- expand (the same warp code as
+// k_expand), first-occurrence marks, ranks, commit -- until the frontier cap,
+// the candidate budget or the candidates run out.
+
+namespace snp {
+
+namespace {
+
+struct BatchScratch {
+  uint64_t* psi;   // [pmax + 1]
+  uint64_t* off;   // [pmax + 1]
+  int32_t* staging;
+  uint32_t *gmin, *slot_of, *srow, *own, *bits, *wbase;
+  ChunkState* st;
+};
+
+__device__ __forceinline__ BatchScratch batch_scratch(unsigned char* base, int64_t pmax, uint32_t qc, int m_max) {
+  size_t at = 0;
+  auto take = [&](size_t bytes) {
+    unsigned char* p = base + at;
+    at += (bytes + 255) & ~size_t(255);
+    return p;
+  };
+  BatchScratch b;
+  const int64_t npsi = (pmax + 1) > (int64_t)(qc / 32 + 1) ? (pmax + 1) : (int64_t)(qc / 32 + 1);
+  b.psi = reinterpret_cast<uint64_t*>(take((size_t)npsi * 8));
+  b.off = reinterpret_cast<uint64_t*>(take((pmax + 1) * 8));
+  b.staging = reinterpret_cast<int32_t*>(take((size_t)qc * m_max * 4));
+  b.gmin = reinterpret_cast<uint32_t*>(take(qc * 4));
+  b.slot_of = reinterpret_cast<uint32_t*>(take(qc * 4));
+  b.srow = reinterpret_cast<uint32_t*>(take(qc * 4));
+  b.own = reinterpret_cast<uint32_t*>(take((qc / 32 + 1) * 4));
+  b.bits = reinterpret_cast<uint32_t*>(take((qc / 32 + 1) * 4));
+  b.wbase = reinterpret_cast<uint32_t*>(take((qc / 32 + 1) * 4));
+  b.st = reinterpret_cast<ChunkState*>(take(sizeof(ChunkState)));
+  return b;
+}
+
+// Block-wide exclusive scan of v[0..n) in place (saturating u64), in tiles of blockDim.x.
+__device__ void block_scan_sat(uint64_t* v, int64_t n, uint64_t* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  uint64_t carry = 0;
+  for (int64_t t0 = 0; t0 < n; t0 += blockDim.x) {
+    const int64_t i = t0 + tid;
+    uint64_t inc = i < n ? v[i] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc = sat_add(y, inc);
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t ws = lane < nw ? wsum[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, ws, o);
+        if (lane >= o) ws = sat_add(y, ws);
+      }
+      if (lane < nw) wsum[lane] = ws;
+    }
+    __syncthreads();
+    const uint64_t before = sat_add(carry, warp > 0 ? wsum[warp - 1] : 0ull);
+    uint64_t ex = __shfl_up_sync(0xffffffffu, inc, 1);
+    if (lane == 0) ex = 0;
+    if (i < n) v[i] = sat_add(before, ex);
+    const uint64_t tile_total = wsum[nw - 1];
+    __syncthreads();
+    carry = sat_add(carry, tile_total);
+  }
+}
+
+}  // namespace
+
+__global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+    BatchSys& b = sys[i];
+    const int m = b.sys.m;
+    const int32_t* src = c0 + c0_off[i];
+    for (int j = lane; j < m; j += 32) b.pool[j] = src[j];
+    __syncwarp();
+    const uint64_t h = fingerprint(b.sys, b.pool, lane);
+    if (lane == 0) {
+      const unsigned long long val = ((unsigned long long)fp32_of(h) << 32) | 0u;
+      b.slots[(h & b.bmask) * kBucket] = val;  // the table is empty: first slot of its bucket
+    }
+  }
+}
+
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned int s_next;
+  __shared__ uint64_t s_wsum[kThreads / 32];
+  __shared__ unsigned int s_cnt, s_stop, s_capped, s_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kThreads / 32;
+  BatchScratch sc = batch_scratch(ba.scratch + (size_t)blockIdx.x * ba.scratch_stride, ba.pmax, ba.qc, ba.m_max);
+  for (;;) {
+    if (tid == 0) s_next = atomicAdd(ba.queue + ba.d, 1u);
+    __syncthreads();
+    const int32_t si = (int32_t)s_next;
+    __syncthreads();
+    if (si >= ba.n) return;
+    BatchSys* bs = ba.sys + si;
+    BatchDepthStat* stat = ba.stats + (size_t)si * (ba.depth + 1) + ba.d;
+    if (bs->done) continue;
+    const DevSys S = bs->sys;
+    const int m = S.m;
+    const int64_t P = bs->level_hi - bs->level_lo;
+    const int32_t* parents = bs->pool + (size_t)bs->level_lo * m;
+    if (tid == 0) {
+      ChunkState z = {};
+      *sc.st = z;
+    }
+    // step (a) and Psi, one thread per parent
+    bool over = false;
+    for (int64_t p = tid; p < P; p += kThreads) {
+      const int32_t* row = parents + (size_t)p * m;
+      uint64_t prod = 1;
+      bool skip = false, ov = false;
+      int r = __ldg(S.first_rule);
+      for (int n = 0; n < m; ++n) {
+        const int32_t x = row[n];
+        const int r1 = __ldg(S.first_rule + n + 1);
+        uint32_t cnt = 0;
+        for (; r < r1; ++r) cnt += rule_applies(x, __ldg(S.rule + r)) ? 1u : 0u;
+        if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
+        ov |= x > INT32_MAX - __ldg(S.gain + n);
+        skip |= ba.max_expand >= 0 && x > ba.max_expand;
+      }
+      sc.off[p] = skip ? 0ull : prod;
+      over |= ov && !skip;
+    }
+    if (tid == 0) sc.off[P] = 0;
+    if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&bs->error, kErrOverflow);
+    __threadfence();
+    __syncthreads();
+    block_scan_sat(sc.off, P + 1, s_wsum);
+    __threadfence();
+    __syncthreads();
+    const uint64_t total = sc.off[P];
+    const uint64_t T = ba.budget > 0 ? min(total, (uint64_t)ba.budget) : total;
+    uint64_t remaining = ba.cap > 0 ? (uint64_t)ba.cap : ~0ull;
+    uint64_t g0 = 0, examined = 0;
+    int64_t nnew = 0, n_rows = bs->n_rows;
+    int32_t chunks = 0;
+    bool capped = false;
+    ExpandSmem w = expand_smem(smem_raw + (size_t)warp * ba.warp_smem, m, ba.B, ba.ts);
+    if (tid == 0) s_stop = bs->error ? 1u : 0u;
+    __syncthreads();
+    while (g0 < T && !capped && !s_stop) {
+      const uint32_t Q = (uint32_t)min((uint64_t)ba.qc, T - g0);
+      ClaimArgs a;
+      a.sys = S;
+      a.parents = parents;
+      a.off = sc.off;
+      a.P = P;
+      a.g0 = g0;
+      a.Q = Q;
+      a.run = (uint32_t)ba.run;
+      a.table = DevTable{bs->slots, bs->bmask};
+      a.pool = bs->pool;
+      a.staging = sc.staging;
+      a.gmin = sc.gmin;
+      a.slot_of = sc.slot_of;
+      a.ownbits = sc.own;
+      a.st = sc.st;
+      if ((m & 3) == 0)
+        expand_warp<true>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+      else
+        expand_warp<false>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+      __threadfence();
+      __syncthreads();
+      // first-occurrence marks
+      const uint32_t nwords = (Q + 31) / 32;
+      if (tid == 0) s_cnt = 0;
+      __syncthreads();
+      uint32_t cnt = 0;
+      for (uint32_t wd = tid; wd < nwords; wd += kThreads) {
+        uint32_t word = sc.own[wd];
+        if (!word) continue;
+        sc.own[wd] = 0;
+        cnt += __popc(word);
+        while (word) {
+          const uint32_t o = wd * 32u + (uint32_t)(__ffs(word) - 1);
+          word &= word - 1;
+          const uint32_t f = sc.gmin[o];
+          atomicOr(sc.bits + (f >> 5), 1u << (f & 31));
+          sc.srow[f] = o;
+        }
+      }
+      if (cnt) atomicAdd(&s_cnt, cnt);
+      __threadfence();
+      __syncthreads();
+      const uint32_t n_alloc = s_cnt;
+      // ranks: exclusive scan of the words' popcounts
+      uint64_t* ranks = sc.psi;
+      for (uint32_t wd = tid; wd < nwords; wd += kThreads) ranks[wd] = __popc(__ldcg(sc.bits + wd));
+      __syncthreads();
+      block_scan_sat(ranks, nwords, s_wsum);
+      __threadfence();
+      __syncthreads();
+      // commit: warp per word, lane per set bit
+      const uint64_t accept = remaining;
+      for (uint32_t wd = warp; wd < nwords; wd += nwarps) {
+        const uint32_t word = __ldcg(sc.bits + wd);
+        if (!((word >> lane) & 1u)) continue;
+        const uint32_t lid = wd * 32u + (uint32_t)lane;
+        const uint64_t rank = __ldcg(ranks + wd) + __popc(word & ((1u << lane) - 1u));
+        const uint32_t o = __ldcg(sc.srow + lid);
+        unsigned long long* slot = bs->slots + __ldcg(sc.slot_of + o);
+        const unsigned long long hi = (*slot) & 0xFFFFFFFF00000000ull;
+        if (rank < accept) {
+          const int64_t row = n_rows + (int64_t)rank;
+          const int32_t* src = sc.staging + (size_t)o * m;
+          int32_t* dst = bs->pool + (size_t)row * m;
+          for (int j = 0; j < m; ++j) dst[j] = __ldcg(src + j);
+          *slot = hi | (uint32_t)row;
+          if (rank + 1 == accept) {
+            sc.st->capped = 1;
+            sc.st->last_lid = lid;
+          }
+        } else {
+          *slot = hi | kRowTomb;
+        }
+      }
+      __threadfence();
+      __syncthreads();
+      const uint64_t acc = min((uint64_t)n_alloc, accept);
+      nnew += (int64_t)acc;
+      n_rows += (int64_t)acc;
+      if (remaining != ~0ull) remaining -= acc;
+      if (tid == 0) {
+        s_capped = sc.st->capped;
+        s_last = sc.st->last_lid;
+        if (sc.st->error) atomicOr(&bs->error, sc.st->error);
+        s_stop = bs->error ? 1u : 0u;
+      }
+      for (uint32_t wd = tid; wd < nwords; wd += kThreads) sc.bits[wd] = 0;
+      __threadfence();
+      __syncthreads();
+      capped = s_capped != 0;
+      examined = capped ? g0 + s_last + 1 : g0 + Q;
+      g0 += Q;
+      ++chunks;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      stat->new_configs = nnew;
+      stat->examined = (int64_t)examined;
+      stat->candidates = total;
+      stat->truncated = examined < total ? 1 : 0;
+      stat->chunks = chunks;
+      bs->n_rows = n_rows;
+      if (nnew == 0) {
+        bs->done = 1;
+      } else {
+        bs->depth_reached = ba.d;
+        bs->level_lo = bs->level_hi;
+        bs->level_hi = n_rows;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+size_t batch_scratch_bytes(int64_t pmax, uint32_t qc, int m_max) {
+  auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return r((size_t)std::max<int64_t>(pmax + 1, qc / 32 + 1) * 8) + r((pmax + 1) * 8) + r((size_t)qc * m_max * 4) +
+         3 * r(qc * 4) + 3 * r((qc / 32 + 1) * 4) +
+         r(sizeof(ChunkState));
+}
+
+size_t expand_smem_bytes(int m_max, int B, int* ts) {
+  *ts = round4(m_max) + 4;
+  return expand_warp_bytes(m_max, B, *ts);
+}
+
+void launch_batch_depth(const BatchArgs& a, int blocks, int warps, cudaStream_t st) {
+  const size_t smem = a.warp_smem * warps;
+  if (warps == 4) {
+    cudaFuncSetAttribute(k_batch_depth<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch_depth<128><<<blocks, 128, smem, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_batch_depth<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch_depth<256><<<blocks, 256, smem, st>>>(a);
+  }
 }
 
 }  // namespace snp

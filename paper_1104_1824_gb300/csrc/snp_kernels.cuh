@@ -45,6 +45,55 @@ struct CommitArgs {
   ChunkState* st;
 };
 
+// ---------------------------------------------------------------------------
+// Batch engine: many independent systems advance one depth per launch.
+
+// One system of a batch (device memory; updated by the batch kernel).
+struct BatchSys {
+  DevSys sys;
+  int32_t* pool;               // configurations, discovery order, pool_rows rows
+  unsigned long long* slots;   // the system's own hash table
+  uint64_t bmask;              // buckets - 1
+  int64_t pool_rows;
+  int64_t level_lo, level_hi;  // current frontier: pool rows [level_lo, level_hi)
+  int64_t n_rows;
+  int32_t done;                // a depth found nothing new: the system is finished
+  uint32_t error;              // kErr* bits
+  int32_t depth_reached;
+  int32_t pad;
+};
+
+struct BatchDepthStat {
+  int64_t new_configs;
+  int64_t examined;
+  uint64_t candidates;
+  int32_t truncated;
+  int32_t chunks;
+};
+
+struct BatchArgs {
+  BatchSys* sys;               // [n]
+  BatchDepthStat* stats;       // [n][depth + 1]
+  int32_t n, depth, d;         // systems, planned depth, the depth this launch runs
+  int64_t cap, budget;
+  int32_t max_expand;
+  uint32_t qc;                 // candidates per pass
+  int32_t B, ts, run;          // expand tile rows, tile row stride (words), candidates per warp task
+  size_t warp_smem;            // bytes of shared memory per warp
+  unsigned int* queue;         // [depth + 1] work counters, zero before the launch
+  unsigned char* scratch;      // per-CTA scratch
+  size_t scratch_stride;
+  int64_t pmax;                // largest frontier a system may have
+  int32_t m_max;
+};
+
+// Bytes of per-CTA scratch for frontiers of up to pmax rows and passes of qc candidates.
+size_t batch_scratch_bytes(int64_t pmax, uint32_t qc, int m_max);
+// Per-warp shared memory of the expand loop for rows of up to m_max neurons.
+size_t expand_smem_bytes(int m_max, int B, int* ts);
+void launch_batch_depth(const BatchArgs& a, int blocks, int warps, cudaStream_t st);
+__global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n);
+
 // Step (a) and Psi for P frontier rows; returns the launches made.
 int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ChunkState* st,
                cudaStream_t stream, int nsm);
