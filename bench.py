@@ -52,6 +52,12 @@ WORKLOADS = {
                            "budget 2^26, 65536 spiking vectors per pass",
                       cpu_sample=dict(depth=1, cap=1 << 12, budget=1 << 14),
                       ref_sample=dict(depth=1, cap=1 << 11, budget=1 << 13)),
+    "batch4096": dict(n=4096, base_seed=1000, depth=6, cap=1 << 12, budget=1 << 16,
+                      desc="4096 independent random SNP systems (system s: seed 1000+s; m U[16,256], 1-4 rules/neuron, "
+                           "out-degree U[2,8], otherwise as random64), each explored to depth 6 with cap 2^12 and "
+                           "budget 2^16; one launch per depth for all systems (batch engine, CUDA graph)",
+                      cpu_sample=dict(systems=2, depth=6, cap=1 << 12, budget=1 << 16),
+                      ref_sample=dict(systems=1, depth=4, cap=1 << 12, budget=1 << 16)),
 }
 
 
@@ -62,6 +68,8 @@ def rank_info():
 def make_system(name):
     import snp_synth
     w = WORKLOADS[name]
+    if name == "batch4096":
+        return snp_synth.batch_systems(w["n"], w["base_seed"])
     return snp_synth.random_64(w["seed"]) if name == "random64" else snp_synth.dense_1024(w["seed"])
 
 
@@ -160,11 +168,14 @@ def profiled_traffic(workload: str):
 def run_cpu_baseline(system, sample):
     import oracle
     oracle.build()
-    o = oracle.Oracle(system)
-    t0 = time.perf_counter()
-    e = o.explore(sample["depth"], cap=sample["cap"], budget=sample["budget"])
-    dt = time.perf_counter() - t0
-    new = sum(d.new for d in e.depths[1:])
+    systems = system[: sample["systems"]] if isinstance(system, list) else [system]
+    new, dt = 0, 0.0
+    for x in systems:
+        o = oracle.Oracle(x)
+        t0 = time.perf_counter()
+        e = o.explore(sample["depth"], cap=sample["cap"], budget=sample["budget"])
+        dt += time.perf_counter() - t0
+        new += sum(d.new for d in e.depths[1:])
     return new, dt
 
 
@@ -184,6 +195,8 @@ def bench_ours(args):
 
     w = WORKLOADS[args.workload]
     system = make_system(args.workload)
+    if args.workload == "batch4096":
+        return bench_batch(args, w, system, snp, torch, dist, dev, rank, world, local)
     s = snp.System(system)
     stream = torch.cuda.Stream(device=dev)
     tc = args.transition == "tc"
@@ -296,6 +309,113 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
+def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
+    """Each rank explores its own copy of all systems (the systems would shard
+    across ranks without any exchange: weak scaling)."""
+    import numpy as np
+    handles = [snp.System(x) for x in systems]
+    hs = [h.h for h in handles]
+    stream = torch.cuda.Stream(device=dev)
+    o = snp.snp_explore_opts_init()
+    o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
+    o.stream = stream.cuda_stream
+    t0 = time.perf_counter()
+    chunk, tile, warps = snp.snp_batch_autotune(hs, o) if args.autotune else (2048, 0, 8)
+    tune_s = time.perf_counter() - t0
+    o.chunk, o.tile, o.warps = chunk, tile, warps
+    statuses = np.zeros(len(hs), dtype=np.int32)
+    for _ in range(args.warmup):
+        snp.snp_explore_batch(hs, o, statuses)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        snp.snp_explore_batch(hs, o, statuses)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    assert (statuses == 0).all(), statuses[statuses != 0][:8]
+    new_step, bytes_step, per_depth = 0, 0, {}
+    for h, x in zip(handles, systems):
+        st = h.depth_stats()
+        row = 4 * x.m
+        for d, a in enumerate(st):
+            if d == 0:
+                continue
+            new_step += a.new
+            dups = a.examined - a.new
+            bytes_step += a.examined * 8 + dups * row + a.new * (row + 8) + a.new * 2 * row + a.parents * row
+            per_depth.setdefault(d, 0)
+            per_depth[d] += a.new
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    else:
+        ms_max = ms
+    total_all = new_step * args.steps * world
+    value = total_all / (ms_max * 1e-3)
+    peak, peak_kind = measured_peaks()
+    achieved = bytes_step * args.steps / (ms * 1e-3) / 1e9
+    e2e = None
+    if not args.no_e2e:
+        arrays = [[np.ascontiguousarray(a, dtype=np.int32) for a in (x.rule_neuron, x.rule_i, x.rule_j, x.M, x.c0)]
+                  for x in systems]
+        h2d = sum(a.nbytes for arr in arrays for a in arr)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hh = [snp.snp_load_system(x.m, *arr) for x, arr in zip(systems, arrays)]
+        snp.snp_explore_batch(hh, o)
+        d2h, got = 0, 0
+        for hnd, x in zip(hh, systems):
+            n = snp.snp_reachable_count(hnd)
+            out = np.empty((n, x.m), dtype=np.int32)
+            snp.snp_reachable(hnd, out, n)
+            d2h += out.nbytes
+            got += n - 1
+        for hnd in hh:
+            snp.snp_free(hnd)
+        dt = time.perf_counter() - t0
+        e2e = {"value": round(got / dt, 1), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": 1, "ms_per_step": round(dt * 1e3, 1)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cs = w["cpu_sample"]
+        new, dt = run_cpu_baseline(systems, cs)
+        cpu = {"value": round(new / dt, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"the first {cs['systems']} systems of the batch, full settings: {new} new configurations "
+                         f"in {dt:.2f} s, single-threaded C++ oracle", "seconds": round(dt, 2)}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"batch4096: {w['desc']}", "systems": len(systems), "depth": w["depth"],
+                       "frontier_cap": w["cap"], "candidate_budget": w["budget"], "transition": "sparse_i32",
+                       "plan": {"chunk": chunk, "tile": tile, "warps": warps, "autotuned": bool(args.autotune),
+                                "autotune_s": round(tune_s, 2)},
+                       "new_per_step": new_step, "per_depth_new": [per_depth[d] for d in sorted(per_depth)],
+                       "l2": "inputs larger than L2 (pools of all systems, tens of GB)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": {"kernel": "k_batch_depth (one launch per depth, all systems)", "bound": "hbm",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "algorithmic_bytes_per_launch": int(bytes_step / w["depth"]),
+                         "avg_launch_ms": round(ms / args.steps / w["depth"], 3), "traffic": None},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (w["depth"] + 2) * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def bench_e2e(args, system, w, snp, torch, dev):
     """Host arrays in, every configuration back in pinned host memory, per step."""
     import numpy as np
@@ -362,6 +482,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
+    ap.add_argument("--autotune", action="store_true", help="batch4096: pick pass size, tile and warps first")
     ap.add_argument("--transition", choices=["sparse", "tc"], default="sparse",
                     help="step (c): sparse int32 gather, or the exact int8 tensor-core product")
     args = ap.parse_args()

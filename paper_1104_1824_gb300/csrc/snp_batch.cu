@@ -16,6 +16,17 @@ namespace snp {
 struct BatchArena {
   DevBuf sys, stats, pools, slots, scratch, queue, c0, c0_off;
   int32_t n = 0, depth = 0;
+  // shape the buffers and the captured graph were made for
+  std::vector<snp_system*> handles;
+  int64_t cap = 0, budget = 0;
+  int32_t max_expand = 0, blocks = 0, warps = 0, B = 0;
+  uint32_t qc = 0;
+  uint64_t nslots = 0;
+  size_t scratch_stride = 0, pool_bytes = 0;
+  cudaGraphExec_t exec = nullptr;
+  ~BatchArena() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
 };
 
 }  // namespace snp
@@ -75,14 +86,40 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   const int blocks = std::max(1, std::min<int>(nsm * blocks_per_sm, n));
   const size_t scratch_stride = (batch_scratch_bytes(cap, plan.qc, m_max) + 255) & ~size_t(255);
 
-  auto arena = std::make_shared<BatchArena>();
-  arena->n = n;
-  arena->depth = depth;
   size_t pool_bytes = 0;
   std::vector<size_t> pool_off(n);
   for (int32_t i = 0; i < n; ++i) {
     pool_off[i] = pool_bytes;
     pool_bytes += ((size_t)rows_per * hs[i]->m * sizeof(int32_t) + 255) & ~size_t(255);
+  }
+  // Reuse the arena (and its graph) of the previous batch over the same handles and shape.
+  std::shared_ptr<BatchArena> arena = hs[0]->batch;
+  bool same = arena && arena->n == n && arena->depth == depth && arena->cap == cap &&
+              arena->budget == (o->candidate_budget > 0 ? o->candidate_budget : 0) &&
+              arena->max_expand == o->max_expand_value && arena->blocks == blocks && arena->warps == warps &&
+              arena->B == B && arena->qc == plan.qc && arena->nslots == nslots && arena->pool_bytes == pool_bytes &&
+              arena->scratch_stride == scratch_stride;
+  for (int32_t i = 0; same && i < n; ++i) same = arena->handles[i] == hs[i] && hs[i]->batch == arena;
+  if (!same) {
+    arena = std::make_shared<BatchArena>();
+    arena->n = n;
+    arena->depth = depth;
+    arena->handles.assign(hs, hs + n);
+    arena->cap = cap;
+    arena->budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
+    arena->max_expand = o->max_expand_value;
+    arena->blocks = blocks;
+    arena->warps = warps;
+    arena->B = B;
+    arena->qc = plan.qc;
+    arena->nslots = nslots;
+    arena->pool_bytes = pool_bytes;
+    arena->scratch_stride = scratch_stride;
+    for (int32_t i = 0; i < n; ++i) {  // release older arenas before allocating
+      hs[i]->batch.reset();
+      hs[i]->result_pool = nullptr;
+      hs[i]->explored = false;
+    }
   }
   TRY(arena->sys.reserve(sizeof(BatchSys) * n));
   TRY(arena->stats.reserve(sizeof(BatchDepthStat) * n * (depth + 1)));
@@ -148,30 +185,29 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
   }
-  // depth launches, captured once and replayed as one graph
-  cudaStream_t cap_st = nullptr;
-  CK(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  CK(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
-  for (int d = 1; d <= depth; ++d) {
-    a.d = d;
-    launch_batch_depth(a, blocks, warps, cap_st);
-  }
-  cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);
-  if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
-  if (ce != cudaSuccess) {
+  // depth launches, captured once per arena and replayed as one graph
+  if (!arena->exec) {
+    cudaStream_t cap_st = nullptr;
+    CK(cudaStreamCreateWithFlags(&cap_st, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
+    for (int d = 1; d <= depth; ++d) {
+      a.d = d;
+      launch_batch_depth(a, blocks, warps, cap_st);
+    }
+    cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&arena->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     cudaStreamDestroy(cap_st);
-    return fail(SNP_E_CUDA, "batch graph: %s", cudaGetErrorString(ce));
+    if (ce != cudaSuccess) {
+      arena->exec = nullptr;
+      return fail(SNP_E_CUDA, "batch graph: %s", cudaGetErrorString(ce));
+    }
   }
   if (ms) CK(cudaEventRecord(e0, st));
-  ce = cudaGraphLaunch(exec, st);
+  cudaError_t ce = cudaGraphLaunch(arena->exec, st);
   if (ms && ce == cudaSuccess) ce = cudaEventRecord(e1, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  cudaGraphExecDestroy(exec);
-  cudaGraphDestroy(graph);
-  cudaStreamDestroy(cap_st);
   if (ce != cudaSuccess) return fail(SNP_E_CUDA, "batch run: %s", cudaGetErrorString(ce));
   if (ms) {
     CK(cudaEventElapsedTime(ms, e0, e1));
@@ -230,11 +266,6 @@ extern "C" int snp_explore_batch(snp_handle* hs, int32_t n, const snp_explore_op
   if (o->chunk > 0) plan.qc = (uint32_t)std::min<int64_t>(o->chunk, 1 << 16);
   if (o->tile > 0) plan.tile = std::min(o->tile, 32);
   if (o->warps > 0) plan.warps = o->warps;
-  for (int32_t i = 0; i < n; ++i) {  // a handle's earlier results go
-    hs[i]->batch.reset();
-    hs[i]->result_pool = nullptr;
-    hs[i]->explored = false;
-  }
   return batch_run(hs, n, o, plan, statuses, nullptr);
 }
 
