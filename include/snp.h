@@ -220,6 +220,49 @@ int snp_explore_batch(snp_handle* hs, int32_t n, const snp_explore_opts* opts, i
 int snp_batch_autotune(snp_handle* hs, int32_t n, const snp_explore_opts* opts, int32_t* chunk, int32_t* tile,
                        int32_t* warps);
 
+/* Serving: explorations submitted at any time run together on the device.
+ * The paper's simulator runs one system at a time; this loop serves many.  A
+ * server thread admits pending requests while its device memory allows (each
+ * request needs its pool, 4m (1 + depth * cap) bytes, and its hash table),
+ * then advances every admitted request by one depth per launch of the batch
+ * engine, so requests that arrive while others run join at the next launch
+ * (continuous batching).  A finished request's configurations are copied
+ * into its handle, which then answers snp_reachable and snp_depth_stats
+ * exactly as after snp_explore; its memory goes back to the server. */
+typedef struct {
+  int64_t submitted, completed, active, pending;
+  int64_t new_configs;  /* new configurations of the completed requests */
+  int64_t ticks;        /* batch launches */
+  double busy_ms;       /* host time spent running launches */
+  double span_ms;       /* first submit to last completion */
+  double p50_ms, p99_ms, max_ms;  /* latency: submit to result ready */
+} snp_server_info;
+
+/* Creates a server on the current device with hbm_budget bytes of device
+ * memory for requests and at most max_active requests on the device at once.
+ * Errors: SNP_E_INVALID, SNP_E_NOMEM, SNP_E_CUDA. */
+int snp_server_create(size_t hbm_budget, int32_t max_active, void** srv);
+
+/* Queues an exploration of h with opts (depth >= 1, 1 <= frontier_cap <= 2^20,
+ * SNP_T_SPARSE_I32, no parent records).  The caller must not use h until the
+ * request is reported finished.  *req_id identifies it in snp_server_poll.
+ * Errors: SNP_E_INVALID, SNP_E_NOMEM (larger than the server's memory). */
+int snp_server_submit(void* srv, snp_handle h, const snp_explore_opts* opts, uint64_t* req_id);
+
+/* Takes up to max finished requests: ids, latencies (ms, submit to result
+ * ready) and statuses (SNP_OK or the request's error), any of them NULL. */
+int snp_server_poll(void* srv, uint64_t* ids, double* latency_ms, int32_t* statuses, int32_t max, int32_t* n);
+
+/* Blocks until no request is pending or active.  Returns SNP_OK, or the error
+ * that stopped the server. */
+int snp_server_wait(void* srv);
+
+/* Counters and latency percentiles of the completed requests. */
+int snp_server_stats(void* srv, snp_server_info* out);
+
+/* Stops the server after its pending and active requests finish, and frees it. */
+int snp_server_destroy(void* srv);
+
 /* snp_explore without allocating memory: the paper has no counterpart; this
  * is for callers that may not allocate device memory at the moment they need
  * an exploration (a framework's caching allocator holds the free memory,

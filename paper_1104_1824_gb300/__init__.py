@@ -42,7 +42,8 @@ ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOME
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
            "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
-           "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune"]
+           "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune", "snp_server_create",
+           "snp_server_submit", "snp_server_poll", "snp_server_wait", "snp_server_stats", "snp_server_destroy"]
 
 
 class SnpError(RuntimeError):
@@ -73,6 +74,13 @@ class snp_depth_info(ctypes.Structure):
                 ("launches", ctypes.c_int64)]
 
 
+class snp_server_info(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("active", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("new_configs", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("busy_ms", ctypes.c_double), ("span_ms", ctypes.c_double), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -99,6 +107,12 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.POINTER(i32), vp]
     lib.snp_tc_peak_tops.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
     lib.snp_explore_batch.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(snp_explore_opts), vp]
+    lib.snp_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+    lib.snp_server_submit.argtypes = [vp, vp, ctypes.POINTER(snp_explore_opts), ctypes.POINTER(u64)]
+    lib.snp_server_poll.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(i32)]
+    lib.snp_server_wait.argtypes = [vp]
+    lib.snp_server_stats.argtypes = [vp, ctypes.POINTER(snp_server_info)]
+    lib.snp_server_destroy.argtypes = [vp]
     lib.snp_batch_autotune.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(snp_explore_opts),
                                        ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.snp_last_error.restype = ctypes.c_char_p
@@ -248,6 +262,41 @@ def explore_batch(systems, depth: int, cap: int, budget: int = 0, max_expand: in
     for s in systems:
         s.depth_reached = max(d for d, x in enumerate(s.depth_stats()) if x.new > 0)
     return st
+
+
+def snp_server_create(hbm_budget: int, max_active: int):
+    srv = ctypes.c_void_p()
+    _check(load_library().snp_server_create(int(hbm_budget), int(max_active), ctypes.byref(srv)))
+    return srv
+
+
+def snp_server_submit(srv, h, opts: snp_explore_opts) -> int:
+    rid = ctypes.c_uint64()
+    _check(load_library().snp_server_submit(srv, h, ctypes.byref(opts), ctypes.byref(rid)))
+    return rid.value
+
+
+def snp_server_poll(srv, max_n: int = 4096):
+    ids = np.zeros(max_n, dtype=np.uint64)
+    lat = np.zeros(max_n, dtype=np.float64)
+    sts = np.zeros(max_n, dtype=np.int32)
+    n = ctypes.c_int32()
+    _check(load_library().snp_server_poll(srv, _ptr(ids), _ptr(lat), _ptr(sts), int(max_n), ctypes.byref(n)))
+    return ids[: n.value], lat[: n.value], sts[: n.value]
+
+
+def snp_server_wait(srv) -> None:
+    _check(load_library().snp_server_wait(srv))
+
+
+def snp_server_stats(srv) -> snp_server_info:
+    info = snp_server_info()
+    _check(load_library().snp_server_stats(srv, ctypes.byref(info)))
+    return info
+
+
+def snp_server_destroy(srv) -> None:
+    load_library().snp_server_destroy(srv)
 
 
 def snp_depth_stats(h, d: int) -> snp_depth_info:

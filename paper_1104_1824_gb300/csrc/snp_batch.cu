@@ -144,6 +144,12 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     b.level_lo = 0;
     b.level_hi = 1;
     b.n_rows = 1;
+    b.cur_depth = 0;
+    b.target_depth = depth;
+    b.max_expand = o->max_expand_value;
+    b.cap = cap;
+    b.budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
+    b.stats = arena->stats.as<BatchDepthStat>() + (size_t)i * (depth + 1);
   }
   TRY(arena->c0.reserve(sizeof(int32_t) * c0.size()));
   TRY(arena->c0_off.reserve(sizeof(int64_t) * n));
@@ -152,7 +158,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   CK(cudaMemcpyAsync(arena->c0_off.p, c0_off.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(arena->stats.p, 0, sizeof(BatchDepthStat) * n * (depth + 1), st));
   CK(cudaMemsetAsync(arena->queue.p, 0, sizeof(unsigned int) * (depth + 1), st));
-  CK(cudaMemsetAsync(arena->scratch.p, 0, scratch_stride * blocks, st));
+  if (!same) CK(cudaMemsetAsync(arena->scratch.p, 0, scratch_stride * blocks, st));  // bitmaps start (and stay) clear
   k_fill_u64<<<grid_for((int64_t)(nslots * n), 256, nsm * 32), 256, 0, st>>>(arena->slots.as<unsigned long long>(),
                                                                              nslots * n, kEmpty);
   CK(cudaGetLastError());
@@ -163,12 +169,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   BatchArgs a;
   std::memset(&a, 0, sizeof a);
   a.sys = arena->sys.as<BatchSys>();
-  a.stats = arena->stats.as<BatchDepthStat>();
   a.n = n;
-  a.depth = depth;
-  a.cap = cap;
-  a.budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
-  a.max_expand = o->max_expand_value;
   a.qc = plan.qc;
   a.B = B;
   a.ts = ts;
@@ -192,7 +193,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(cap_st, cudaStreamCaptureModeThreadLocal));
     for (int d = 1; d <= depth; ++d) {
-      a.d = d;
+      a.launch = d;
       launch_batch_depth(a, blocks, warps, cap_st);
     }
     cudaError_t ce = cudaStreamEndCapture(cap_st, &graph);

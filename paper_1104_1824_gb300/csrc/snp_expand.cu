@@ -561,14 +561,17 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kThreads / 32;
   BatchScratch sc = batch_scratch(ba.scratch + (size_t)blockIdx.x * ba.scratch_stride, ba.pmax, ba.qc, ba.m_max);
   for (;;) {
-    if (tid == 0) s_next = atomicAdd(ba.queue + ba.d, 1u);
+    if (tid == 0) s_next = atomicAdd(ba.queue + ba.launch, 1u);
     __syncthreads();
     const int32_t si = (int32_t)s_next;
     __syncthreads();
     if (si >= ba.n) return;
     BatchSys* bs = ba.sys + si;
-    BatchDepthStat* stat = ba.stats + (size_t)si * (ba.depth + 1) + ba.d;
-    if (bs->done) continue;
+    const int32_t d = bs->cur_depth + 1;
+    if (bs->done || d > bs->target_depth) continue;
+    BatchDepthStat* stat = bs->stats + d;
+    const int64_t cap = bs->cap, budget = bs->budget;
+    const int32_t max_expand = bs->max_expand;
     const DevSys S = bs->sys;
     const int m = S.m;
     const int64_t P = bs->level_hi - bs->level_lo;
@@ -591,7 +594,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
         for (; r < r1; ++r) cnt += rule_applies(x, __ldg(S.rule + r)) ? 1u : 0u;
         if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
         ov |= x > INT32_MAX - __ldg(S.gain + n);
-        skip |= ba.max_expand >= 0 && x > ba.max_expand;
+        skip |= max_expand >= 0 && x > max_expand;
       }
       sc.off[p] = skip ? 0ull : prod;
       over |= ov && !skip;
@@ -604,8 +607,8 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
     __threadfence();
     __syncthreads();
     const uint64_t total = sc.off[P];
-    const uint64_t T = ba.budget > 0 ? min(total, (uint64_t)ba.budget) : total;
-    uint64_t remaining = ba.cap > 0 ? (uint64_t)ba.cap : ~0ull;
+    const uint64_t T = budget > 0 ? min(total, (uint64_t)budget) : total;
+    uint64_t remaining = cap > 0 ? (uint64_t)cap : ~0ull;
     uint64_t g0 = 0, examined = 0;
     int64_t nnew = 0, n_rows = bs->n_rows;
     int32_t chunks = 0;
@@ -649,7 +652,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
         while (word) {
           const uint32_t o = wd * 32u + (uint32_t)(__ffs(word) - 1);
           word &= word - 1;
-          const uint32_t f = sc.gmin[o];
+          const uint32_t f = o < Q ? sc.gmin[o] : 0xFFFFFFFFu;
+          if (f >= Q) {  // not a claim of this pass: record and skip
+            atomicOr(&sc.st->error, kErrInternal);
+            continue;
+          }
           atomicOr(sc.bits + (f >> 5), 1u << (f & 31));
           sc.srow[f] = o;
         }
@@ -717,10 +724,11 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       stat->truncated = examined < total ? 1 : 0;
       stat->chunks = chunks;
       bs->n_rows = n_rows;
+      bs->cur_depth = d;
       if (nnew == 0) {
         bs->done = 1;
       } else {
-        bs->depth_reached = ba.d;
+        bs->depth_reached = d;
         bs->level_lo = bs->level_hi;
         bs->level_hi = n_rows;
       }

@@ -101,6 +101,7 @@ int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uin
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st) {
   uint32_t cnt = 0;
+  const uint32_t limit = nwords * 32u;
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < nwords; w += gridDim.x * blockDim.x) {
     uint32_t word = ownbits[w];
     if (!word) continue;
@@ -110,6 +111,10 @@ __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, 
       const uint32_t o = w * 32u + (uint32_t)(__ffs(word) - 1);
       word &= word - 1;
       const uint32_t f = gmin[o];
+      if (f >= limit) {  // not a claim of this pass: record and skip
+        atomicOr(&st->error, kErrInternal);
+        continue;
+      }
       atomicOr(bits + (f >> 5), 1u << (f & 31));
       srow[f] = o;
     }

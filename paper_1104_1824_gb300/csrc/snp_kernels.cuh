@@ -60,7 +60,11 @@ struct BatchSys {
   int32_t done;                // a depth found nothing new: the system is finished
   uint32_t error;              // kErr* bits
   int32_t depth_reached;
-  int32_t pad;
+  int32_t cur_depth;           // depths completed so far
+  int32_t target_depth;        // depths to run
+  int32_t max_expand;
+  int64_t cap, budget;         // per-depth frontier cap (>= 1) and candidate budget (<= 0: none)
+  struct BatchDepthStat* stats;  // [target_depth + 1]
 };
 
 struct BatchDepthStat {
@@ -71,19 +75,19 @@ struct BatchDepthStat {
   int32_t chunks;
 };
 
+// One launch advances every system by one depth (cur_depth + 1), unless it
+// is finished or has run target_depth depths.
 struct BatchArgs {
   BatchSys* sys;               // [n]
-  BatchDepthStat* stats;       // [n][depth + 1]
-  int32_t n, depth, d;         // systems, planned depth, the depth this launch runs
-  int64_t cap, budget;
-  int32_t max_expand;
+  int32_t n;
+  int32_t launch;              // index of this launch (its work counter)
   uint32_t qc;                 // candidates per pass
   int32_t B, ts, run;          // expand tile rows, tile row stride (words), candidates per warp task
   size_t warp_smem;            // bytes of shared memory per warp
-  unsigned int* queue;         // [depth + 1] work counters, zero before the launch
+  unsigned int* queue;         // work counters, one per launch, zero before it
   unsigned char* scratch;      // per-CTA scratch
   size_t scratch_stride;
-  int64_t pmax;                // largest frontier a system may have
+  int64_t pmax;                // largest frontier a system may have (largest cap)
   int32_t m_max;
 };
 
