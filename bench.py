@@ -52,6 +52,13 @@ WORKLOADS = {
                            "budget 2^26, 65536 spiking vectors per pass",
                       cpu_sample=dict(depth=1, cap=1 << 12, budget=1 << 14),
                       ref_sample=dict(depth=1, cap=1 << 11, budget=1 << 13)),
+    # rate frozen at 0.8 x the measured batched capacity (125.8 requests/s, --calibrate, 2000 requests)
+    "serving": dict(requests=100000, seed=4, cap=1 << 12, budget=1 << 16, rate_per_s=100.0,
+                    desc="seeded Poisson stream of requests (seed 4); request k: random SNP system seed 10^7+k with "
+                         "m U[8,512], 2-3 rules/neuron, out-degree 4, otherwise as random64, BFS depth U[4,32], "
+                         "cap 2^12, budget 2^16; continuous batching on one GPU",
+                    cpu_sample=dict(systems=2, depth=6, cap=1 << 12, budget=1 << 16),
+                    ref_sample=dict(systems=1, depth=4, cap=1 << 12, budget=1 << 16)),
     "batch4096": dict(n=4096, base_seed=1000, depth=6, cap=1 << 12, budget=1 << 16,
                       desc="4096 independent random SNP systems (system s: seed 1000+s; m U[16,256], 1-4 rules/neuron, "
                            "out-degree U[2,8], otherwise as random64), each explored to depth 6 with cap 2^12 and "
@@ -194,6 +201,8 @@ def bench_ours(args):
     import paper_1104_1824_gb300 as snp
 
     w = WORKLOADS[args.workload]
+    if args.workload == "serving":
+        return bench_serving(args, w, snp, torch, rank)
     system = make_system(args.workload)
     if args.workload == "batch4096":
         return bench_batch(args, w, system, snp, torch, dist, dev, rank, world, local)
@@ -416,6 +425,89 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
         dist.destroy_process_group()
 
 
+def bench_serving(args, w, snp, torch, rank):
+    """The serving loop on the first --requests arrivals of the seeded stream.
+    --calibrate submits them all at once and reports the batched capacity
+    (requests/s) whose 0.8 fraction is frozen as the stream's rate."""
+    import numpy as np
+    import snp_synth
+    n = args.requests
+    rate = w["rate_per_s"] or 100.0
+    reqs = snp_synth.serving_requests(n, rate, seed=w["seed"])
+    t0 = time.perf_counter()
+    systems = [r.system() for r in reqs]
+    gen_s = time.perf_counter() - t0
+    handles = [snp.System(x) for x in systems]
+    o = [snp.snp_explore_opts_init() for _ in reqs]
+    for oo, r in zip(o, reqs):
+        oo.depth, oo.frontier_cap, oo.candidate_budget = r.depth, w["cap"], w["budget"]
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.5, 120 << 30))
+    srv = snp.snp_server_create(budget, args.max_active)
+    statuses, got = [], [0]
+    id_to_k = {}
+    stop = [False]
+
+    def consume():
+        # the client side: takes finished results and releases their handles
+        waiting = []
+        while not stop[0] or got[0] < n:
+            ids, lat, sts = snp.snp_server_poll(srv)
+            for i, st in zip(ids.tolist(), sts.tolist()):
+                statuses.append(st)
+                waiting.append(i)
+            got[0] += len(ids)
+            still = []
+            for i in waiting:
+                k = id_to_k.get(i)
+                if k is None:
+                    still.append(i)
+                else:
+                    handles[k].close()
+            waiting = still
+            if len(ids) == 0:
+                time.sleep(0.001)
+
+    import threading
+    consumer = threading.Thread(target=consume)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t_start = time.perf_counter()
+    consumer.start()
+    for k, r in enumerate(reqs):
+        if not args.calibrate:
+            delay = r.arrival_s - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+        rid = snp.snp_server_submit(srv, handles[k].h, o[k])
+        id_to_k[rid] = k
+    snp.snp_server_wait(srv)
+    wall = time.perf_counter() - t_start
+    clk = clocks.stop()
+    stop[0] = True
+    consumer.join()
+    info = snp.snp_server_stats(srv)
+    snp.snp_server_destroy(srv)
+    assert all(x == 0 for x in statuses), [x for x in statuses if x][:5]
+    value = info.new_configs / (info.span_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": round(info.span_ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": f"serving: {w['desc']}", "requests": n, "of_stream": w["requests"],
+                   "rate_per_s": None if args.calibrate else rate, "calibration": bool(args.calibrate),
+                   "max_active": args.max_active, "hbm_budget_gb": round(budget / 2 ** 30, 1),
+                   "system_generation_s": round(gen_s, 1)},
+        "serving": {"completed": info.completed, "new_configs": info.new_configs, "span_ms": round(info.span_ms, 1),
+                    "wall_s": round(wall, 2), "p50_ms": round(info.p50_ms, 2), "p99_ms": round(info.p99_ms, 2),
+                    "max_ms": round(info.max_ms, 2), "ticks": info.ticks, "busy_ms": round(info.busy_ms, 1),
+                    "capacity_req_per_s": round(info.completed / (info.span_ms * 1e-3), 2)},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def bench_e2e(args, system, w, snp, torch, dev):
     """Host arrays in, every configuration back in pinned host memory, per step."""
     import numpy as np
@@ -483,6 +575,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
     ap.add_argument("--autotune", action="store_true", help="batch4096: pick pass size, tile and warps first")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: arrivals of the stream to run")
+    ap.add_argument("--max-active", type=int, default=2048, help="serving: requests on the device at once")
+    ap.add_argument("--calibrate", action="store_true", help="serving: submit all at once, report the capacity")
     ap.add_argument("--transition", choices=["sparse", "tc"], default="sparse",
                     help="step (c): sparse int32 gather, or the exact int8 tensor-core product")
     args = ap.parse_args()

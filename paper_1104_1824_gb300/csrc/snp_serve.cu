@@ -171,7 +171,11 @@ int retire(snp_server* S, Request* r) {
   std::vector<BatchDepthStat> st(depth + 1);
   CK(cudaMemcpyAsync(st.data(), b.stats, sizeof(BatchDepthStat) * (depth + 1), cudaMemcpyDeviceToHost, S->st));
   const size_t bytes = sizeof(int32_t) * (size_t)b.n_rows * h->m;
-  TRY(h->d_pool.reserve(bytes));
+  if (h->d_pool.reserve(bytes) != SNP_OK) {  // this request fails; the server goes on
+    r->status = SNP_E_NOMEM;
+    h->explored = false;
+    return SNP_OK;
+  }
   h->pool_rows = std::max<int64_t>(h->pool_rows, b.n_rows);
   CK(cudaMemcpyAsync(h->d_pool.p, b.pool, bytes, cudaMemcpyDeviceToDevice, S->st));
   CK(cudaStreamSynchronize(S->st));
