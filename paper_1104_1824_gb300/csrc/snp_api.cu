@@ -100,6 +100,7 @@ int tc_prepare(snp_system* h, uint64_t q, cudaStream_t st) {
     TRY(h->d_pidx.reserve(sizeof(uint32_t) * q));
     TRY(h->d_rows.reserve(sizeof(int32_t) * (size_t)q * h->m));
     TRY(h->d_hash.reserve(sizeof(unsigned long long) * q));
+    TRY(h->d_red.reserve(q));
     h->tc_cap = q;
   }
   return SNP_OK;
@@ -220,6 +221,13 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     h->colkey[j] = (z ^ (z >> 31)) | 1ull;
   }
+  // eqmask[r]: earlier rules of r's neuron whose row of M_Pi equals r's (same consumption and production).
+  h->eqmask.assign(R + 1, 0u);
+  for (int r = 0; r < R; ++r) {
+    const int n = d->rule_neuron[r], r0 = h->first_rule[n];
+    for (int q = r0; q < r; ++q)
+      if (std::equal(&h->M[(size_t)q * m], &h->M[(size_t)q * m] + m, &h->M[(size_t)r * m])) h->eqmask[r] |= 1u << (q - r0);
+  }
   h->rowkey.assign(R + 1, 0ull);
   for (int r = 0; r < R; ++r)
     for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e)
@@ -236,6 +244,7 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_gain, h->gain.data(), sizeof(int32_t) * m)) ||
       (rc = up(h->d_colkey, h->colkey.data(), sizeof(unsigned long long) * m)) ||
       (rc = up(h->d_rowkey, h->rowkey.data(), sizeof(unsigned long long) * (R + 1))) ||
+      (rc = up(h->d_eqmask, h->eqmask.data(), sizeof(uint32_t) * (R + 1))) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;
     return rc;
@@ -455,12 +464,13 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
         if (tc) {
           launch_tc_digits(a.sys, parents, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
-                           h->d_pidx.as<uint32_t>(), st, nsm);
+                           h->d_pidx.as<uint32_t>(), h->d_red.as<uint8_t>(), st, nsm);
           CK(cudaMemsetAsync(h->d_hash.p, 0, sizeof(unsigned long long) * Q, st));
           launch_tc_rows(a.sys, parents, h->d_loc.as<uint8_t>(), h->mp, h->d_pidx.as<uint32_t>(), (uint32_t)Q,
                          h->d_MT.as<int8_t>(), h->Rp, h->d_rn.as<int16_t>(), h->d_rk.as<uint8_t>(),
                          h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), st);
-          launch_resolve_rows(a, h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), st, nsm);
+          launch_resolve_rows(a, h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), h->d_red.as<uint8_t>(),
+                              st, nsm);
           sd.launches += 3;
         } else {
           launch_expand(a, st, nsm);

@@ -36,7 +36,15 @@ struct DevSys {
   const int32_t* gain;        // [m] largest increase of column j in one step
   const unsigned long long* colkey;  // [m] random odd multiplier R[j] of column j
   const unsigned long long* rowkey;  // [R] H[r] = sum over row r of M_Pi of M[r][j] * R[j] (mod 2^64)
+  const uint32_t* eqmask;     // [R] positions of earlier rules of the same neuron with the same row of M_Pi
 };
+
+// Rule r, chosen for a neuron whose applicable rules are `mask`, gives the
+// same child as an earlier applicable rule with the same row of M_Pi: every
+// candidate choosing it repeats an earlier candidate of the same parent.
+__device__ __forceinline__ bool redundant_choice(const DevSys& s, uint32_t mask, int r) {
+  return (mask & __ldg(s.eqmask + r)) != 0u;
+}
 
 struct DevTable {
   unsigned long long* slots;  // [nbuckets * kBucket]: (fp32 << 32) | row

@@ -21,7 +21,9 @@ namespace {
 constexpr int kLowDigits = 16;  // least significant non-trivial neurons tracked per parent
 
 struct ExpandSmem {
-  int32_t* tile;              // [B][ts] candidate rows
+  int32_t* tile;              // [B][ts] rows of candidates waiting for a lookup
+  unsigned long long* keys;   // [B] their table keys
+  uint32_t* lids;             // [B] their chunk-local indices
   int32_t* par;               // [m4] parent
   int32_t* buf;               // [m4] base child
   uint32_t* msk;              // [m4] applicable-rule masks
@@ -31,13 +33,16 @@ struct ExpandSmem {
   uint32_t* plow;             // [1] product of their choice counts (capped at 2^31)
   uint32_t* vlow;             // [1] value of the base's digits on them (< plow)
   unsigned long long* hbase;  // [1] linear hash of the base child
+  int* nred;                  // [1] neurons of the base that use a redundant rule (a later duplicate)
 };
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
+__host__ __device__ inline size_t expand_keys_bytes(int B) { return ((size_t)B * 12 + 15) & ~size_t(15); }
+
 __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
   const int m4 = round4(m);
-  size_t b = (size_t)B * ts * 4 + (size_t)m4 * 12 + 96 + (size_t)m4;
+  size_t b = (size_t)B * ts * 4 + expand_keys_bytes(B) + (size_t)m4 * 12 + 96 + (size_t)m4;
   return (b + 15) & ~size_t(15);
 }
 
@@ -125,6 +130,7 @@ __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint
   __syncwarp();
   const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
   uint64_t q = (after > t) ? 0ull : t / after;
+  int red = 0;
   for (int n = n1 - 1; n >= n0; --n) {
     const uint32_t mask = w.msk[n];
     if (!mask) {
@@ -145,11 +151,15 @@ __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint
     const int r = __ldg(s.first_rule + n) + nth_set_bit(mask, (int)d);
     add_row_shared(s, w.buf, r, 1);
     hp += __ldg(s.rowkey + r);
+    red += redundant_choice(s, mask, r) ? 1 : 0;
   }
   hp = warp_sum_u64(hp);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) red += __shfl_xor_sync(0xffffffffu, red, o);
   __syncwarp();
   if (lane == 0) {
     *w.hbase = hp;
+    *w.nred = red;
     uint64_t v = 0, place = 1;
     for (int i = 0; i < *w.nlow && place < (1ull << 31); ++i) {
       const int n = w.low[i];
@@ -295,12 +305,32 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
   return true;
 }
 
+// Step (d) for the fill (<= 32) rows waiting in the tile, one per lane:
+// passes until every row is resolved; a lane never waits inside a pass, so
+// owners in this warp publish before anyone looks again.
+template <bool VEC>
+__device__ __forceinline__ void flush_tile(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
+  bool todo = lane < fill;
+  for (int pass = 0;; ++pass) {
+    if (todo && resolve_lane<VEC>(a, w.tile + lane * ts, w.keys[lane], w.lids[lane])) todo = false;
+    if (__all_sync(0xffffffffu, !todo)) break;
+    if (pass >= kSpinLimit) {
+      if (todo) atomicOr(&a.st->error, kErrTimeout);
+      break;
+    }
+    __nanosleep(32);
+  }
+  __syncwarp();
+}
+
 // Per-warp shared memory of the expand loop.
 __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, int B, int ts) {
   const int m4 = round4(m);
   ExpandSmem w;
   w.tile = reinterpret_cast<int32_t*>(base);
-  w.par = w.tile + (size_t)B * ts;
+  w.keys = reinterpret_cast<unsigned long long*>(w.tile + (size_t)B * ts);
+  w.lids = reinterpret_cast<uint32_t*>(w.keys + B);
+  w.par = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(w.keys) + expand_keys_bytes(B));
   w.buf = w.par + m4;
   w.msk = reinterpret_cast<uint32_t*>(w.buf + m4);
   w.low = reinterpret_cast<int32_t*>(w.msk + m4);               // 64 bytes
@@ -308,6 +338,7 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
   w.plow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 1);   // +68
   w.vlow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 2);   // +72
   w.hbase = reinterpret_cast<unsigned long long*>(w.low + kLowDigits + 4);  // +80
+  w.nred = w.low + kLowDigits + 6;                                // +88
   w.dig = reinterpret_cast<uint8_t*>(w.low) + 96;
   return w;
 }
@@ -329,6 +360,7 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
     uint64_t after = parent_state(s, a.parents + (size_t)p * m, w, lane);
     decode_full(s, w, a.g0 + la - p_lo, after, lane);
     uint64_t l = la;
+    int fill = 0;  // rows waiting in the tile
     while (l < lb) {
       const uint64_t g = a.g0 + l;
       // a batch never crosses a parent, nor a rollover of the tracked low digits
@@ -338,10 +370,25 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
         if (lane == 0) atomicOr(&a.st->error, kErrInternal);
         break;
       }
-      bool done = true;
-      uint64_t key = 0;
+      // a candidate using a redundant rule repeats an earlier one: no lookup needed
+      bool keep = false;
       if (lane < nb) {
-        int32_t* trow = w.tile + lane * ts;
+        int red = *w.nred;
+        add_to_digits(w, (uint32_t)lane, [&](int n, int d, int nd) {
+          const uint32_t mask = w.msk[n];
+          red += (redundant_choice(s, mask, rule_of(s, w, n, nd)) ? 1 : 0) -
+                 (redundant_choice(s, mask, rule_of(s, w, n, d)) ? 1 : 0);
+        });
+        keep = red == 0;
+      }
+      const uint32_t kept = __ballot_sync(0xffffffffu, keep);
+      if (fill + __popc(kept) > B) {  // no room for this batch's rows: resolve what waits
+        flush_tile<VEC>(a, w, ts, fill, lane);
+        fill = 0;
+      }
+      if (keep) {  // build the row in the next free tile slot
+        const int slot = fill + __popc(kept & ((1u << lane) - 1u));
+        int32_t* trow = w.tile + slot * ts;
         copy_row<VEC>(w.buf, trow, m);
         uint64_t h = *w.hbase;
         add_to_digits(w, (uint32_t)lane, [&](int n, int d, int nd) {
@@ -350,19 +397,14 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
           add_row_private(s, trow, r_new, 1);
           h += __ldg(s.rowkey + r_new) - __ldg(s.rowkey + r_old);
         });
-        key = mix64(h);
-        done = false;
+        w.keys[slot] = mix64(h);
+        w.lids[slot] = (uint32_t)(l + lane);
       }
-      // Passes over the batch until every lane has resolved its candidate; a
-      // lane never waits inside a pass, so owners in this warp publish first.
-      for (int pass = 0;; ++pass) {
-        if (!done) done = resolve_lane<VEC>(a, w.tile + lane * ts, key, (uint32_t)(l + lane));
-        if (__all_sync(0xffffffffu, done)) break;
-        if (pass >= kSpinLimit) {
-          if (!done) atomicOr(&a.st->error, kErrTimeout);
-          break;
-        }
-        __nanosleep(32);
+      fill += __popc(kept);
+      __syncwarp();
+      if (fill >= B || l + nb >= lb) {
+        flush_tile<VEC>(a, w, ts, fill, lane);
+        fill = 0;
       }
       l += nb;
       if (l >= lb) break;
@@ -380,14 +422,17 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       } else {  // same parent: the base moves on by nb
         if (lane == 0) {
           uint64_t h = *w.hbase;
+          int red = *w.nred;
           add_to_digits(w, (uint32_t)nb, [&](int n, int d, int nd) {
             const int r_old = rule_of(s, w, n, d), r_new = rule_of(s, w, n, nd);
             add_row_private(s, w.buf, r_old, -1);
             add_row_private(s, w.buf, r_new, 1);
             h += __ldg(s.rowkey + r_new) - __ldg(s.rowkey + r_old);
+            red += (redundant_choice(s, w.msk[n], r_new) ? 1 : 0) - (redundant_choice(s, w.msk[n], r_old) ? 1 : 0);
             w.dig[n] = (uint8_t)nd;
           });
           *w.hbase = h;
+          *w.nred = red;
           *w.vlow += (uint32_t)nb;
         }
         __syncwarp();
@@ -409,11 +454,11 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
 // one lane per candidate, the same bounded wait-free passes as k_expand.
 template <bool VEC>
 __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t* rows,
-                                                      const unsigned long long* hash) {
+                                                      const unsigned long long* hash, const uint8_t* redundant) {
   const int m = a.sys.m;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < a.Q; base += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t lid = base + threadIdx.x;
-    bool done = lid >= a.Q;
+    bool done = lid >= a.Q || redundant[lid];
     const uint64_t key = done ? 0ull : mix64(hash[lid]);
     for (int pass = 0;; ++pass) {
       if (!done) done = resolve_lane<VEC>(a, rows + lid * m, key, (uint32_t)lid);
@@ -429,12 +474,13 @@ __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t
 
 }  // namespace
 
-void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, cudaStream_t st, int nsm) {
+void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, const uint8_t* redundant,
+                         cudaStream_t st, int nsm) {
   const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)a.Q + 255) / 256, (uint64_t)nsm * 8));
   if (a.sys.m % 4 == 0)
-    k_resolve_rows<true><<<blocks, 256, 0, st>>>(a, rows, hash);
+    k_resolve_rows<true><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
   else
-    k_resolve_rows<false><<<blocks, 256, 0, st>>>(a, rows, hash);
+    k_resolve_rows<false><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
 }
 
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {

@@ -131,9 +131,10 @@ struct snp_system {
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey;
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask;
+  std::vector<uint32_t> eqmask;
   // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
-  DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash;
+  DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash, d_red;
   int32_t Rp = 0, mp = 0, mt_rows = 0;
   uint64_t tc_cap = 0;  // candidates the tensor-core chunk buffers hold
   std::vector<unsigned long long> colkey, rowkey;
@@ -169,6 +170,7 @@ struct snp_system {
     s.gain = d_gain.as<int32_t>();
     s.colkey = d_colkey.as<unsigned long long>();
     s.rowkey = d_rowkey.as<unsigned long long>();
+    s.eqmask = d_eqmask.as<uint32_t>();
     return s;
   }
   snp::DevTable table() const { return snp::DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }

@@ -104,10 +104,12 @@ int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uin
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
 // Step (d) for candidate rows already in global memory (rows[lid * m], hash[lid]).
-void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, cudaStream_t st, int nsm);
+// Candidates with redundant[lid] set repeat an earlier candidate and are skipped.
+void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, const uint8_t* redundant,
+                         cudaStream_t st, int nsm);
 // Tensor-core form of step (c) (snp_tc.cu).
 void launch_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P, uint64_t g0, uint32_t Q,
-                      uint8_t* loc, int mp, uint32_t* pidx, cudaStream_t st, int nsm);
+                      uint8_t* loc, int mp, uint32_t* pidx, uint8_t* redundant, cudaStream_t st, int nsm);
 void launch_tc_rows(DevSys s, const int32_t* parents, const uint8_t* loc, int mp, const uint32_t* pidx, uint32_t Q,
                     const int8_t* MT, int Rp, const int16_t* rn, const uint8_t* rk, int32_t* rows,
                     unsigned long long* hash, cudaStream_t st);

@@ -37,7 +37,8 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], uint32_t a0, uint32_t a1, ui
 // Step (b) for the chunk: per candidate its parent (frontier index) and, per
 // neuron, the position of the chosen rule among the neuron's rules.
 __global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P,
-                                                   uint64_t g0, uint32_t Q, uint8_t* loc, int mp, uint32_t* pidx) {
+                                                   uint64_t g0, uint32_t Q, uint8_t* loc, int mp, uint32_t* pidx,
+                                                   uint8_t* redundant) {
   extern __shared__ int32_t smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int m = s.m;
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* pare
       const int n0 = lane * s.K, n1 = min(n0 + s.K, m);
       uint64_t q = (w.after > t) ? 0ull : t / w.after;
       uint8_t* dst = loc + (size_t)l * mp;
+      bool red = false;
       for (int n = n1 - 1; n >= n0; --n) {
         const uint32_t mask = w.msk[n];
         if (!mask) {
@@ -83,9 +85,15 @@ __global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* pare
           d = (uint32_t)(q % radix);
           q /= radix;
         }
-        dst[n] = (uint8_t)nth_set_bit(mask, (int)d);
+        const int k = nth_set_bit(mask, (int)d);
+        dst[n] = (uint8_t)k;
+        red |= redundant_choice(s, mask, __ldg(s.first_rule + n) + k);
       }
-      if (lane == 0) pidx[l] = (uint32_t)p;
+      red = __any_sync(0xffffffffu, red);
+      if (lane == 0) {
+        pidx[l] = (uint32_t)p;
+        redundant[l] = red ? 1 : 0;
+      }
       __syncwarp();
     }
   }
@@ -199,11 +207,11 @@ __global__ void __launch_bounds__(128) k_tc_peak(int iters, int* out) {
 }
 
 void launch_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P, uint64_t g0, uint32_t Q,
-                      uint8_t* loc, int mp, uint32_t* pidx, cudaStream_t st, int nsm) {
+                      uint8_t* loc, int mp, uint32_t* pidx, uint8_t* redundant, cudaStream_t st, int nsm) {
   const size_t smem = (size_t)4 * 2 * s.m * sizeof(int32_t);
   const uint64_t ntasks = ((uint64_t)Q + 31) / 32;
   const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((ntasks + 3) / 4, (uint64_t)nsm * 16));
-  k_tc_digits<<<blocks, 128, smem, st>>>(s, parents, off, P, g0, Q, loc, mp, pidx);
+  k_tc_digits<<<blocks, 128, smem, st>>>(s, parents, off, P, g0, Q, loc, mp, pidx, redundant);
 }
 
 size_t tc_rows_smem(int mp) { return (size_t)kTcBM * mp + kTcBM * kTcAStride + kTcBM * sizeof(int32_t); }

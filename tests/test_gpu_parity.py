@@ -331,3 +331,30 @@ def test_tc_refuses_entries_beyond_int8(gpu):
 def test_tc_peak_probe(gpu):
     tops = gpu.snp_tc_peak_tops(2000)
     assert tops > 1.0
+
+
+def test_rules_with_identical_rows(gpu):
+    """Neurons whose rules share a row of M_Pi but differ in their regexes: the
+    candidates that choose a later rule repeat earlier ones, and the result must
+    not depend on how the simulator exploits that."""
+    rng = np.random.default_rng(77)
+    for _ in range(20):
+        m = int(rng.integers(2, 7))
+        rn, ri, rj, rc, rp = [], [], [], [], []
+        for n in range(m):
+            k = int(rng.integers(1, 5))
+            c, p = int(rng.integers(1, 3)), int(rng.integers(0, 3))
+            for _ in range(k):
+                rn.append(n)
+                ri.append(int(rng.integers(1, 4)))
+                rj.append(int(rng.integers(0, 3)))
+                same = rng.random() < 0.7
+                rc.append(c if same else int(rng.integers(1, 3)))
+                rp.append(p if same else int(rng.integers(0, 3)))
+        targets = [sorted(rng.choice([t for t in range(m) if t != n], size=min(2, m - 1), replace=False).tolist())
+                   for n in range(m)]
+        system = snp_synth.make_system(m, rn, ri, rj, rc, rp, targets, rng.integers(0, 6, size=m))
+        for transition in (gpu.SNP_T_SPARSE_I32, gpu.SNP_T_TC_I8):
+            s = gpu.System(system)
+            s.explore(6, cap=40, budget=400, transition=transition)
+            assert_same(s, oracle.Oracle(system).explore(6, cap=40, budget=400))
