@@ -239,7 +239,7 @@ def bench_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    per_depth = [{"depth": d, "new": x.new, "examined": x.examined, "ms": round(x.ms, 4),
+    per_depth = [{"depth": d, "new": x.new, "examined": x.examined, "chunks": x.chunks, "ms": round(x.ms, 4),
                   "new_per_s": round(x.new / (x.ms * 1e-3)) if x.ms > 0 else None} for d, x in enumerate(st) if d > 0]
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -228,6 +229,32 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     for (int q = r0; q < r; ++q)
       if (std::equal(&h->M[(size_t)q * m], &h->M[(size_t)q * m] + m, &h->M[(size_t)r * m])) h->eqmask[r] |= 1u << (q - r0);
   }
+  // Applicable rules by spike count.  Above T = 1 + the largest i or c of a
+  // neuron's rules, a^x in L(a^i (a^j)*) reduces to (x - i) mod j == 0 for the
+  // rules with j >= 1, so the masks repeat with period L = lcm of those j:
+  // the table holds x = 0 .. T + L - 1 (bits 0-31 the mask, bits 32-63 the
+  // mask without rules that repeat an earlier applicable rule's row).
+  h->amet.assign(m, make_int2(-1, 0));
+  h->atab.clear();
+  for (int n = 0; n < m; ++n) {
+    const int r0 = h->first_rule[n], r1 = h->first_rule[n + 1];
+    int64_t T = 1, L = 1;
+    for (int r = r0; r < r1 && L <= 64; ++r) {
+      T = std::max<int64_t>(T, 1 + std::max<int64_t>(h->rule[r].x, h->rule[r].z));
+      if (h->rule[r].y >= 1) L = std::lcm<int64_t>(L, h->rule[r].y);
+    }
+    if (L > 64 || T + L > 256) continue;  // evaluated from the rules on the device
+    h->amet[n] = make_int2((int)h->atab.size(), (int)(T | (L << 16)));
+    for (int32_t x = 0; x < T + L; ++x) {
+      uint32_t mask = 0;
+      for (int r = r0; r < r1; ++r)
+        if (rule_applies(x, h->rule[r])) mask |= 1u << (r - r0);
+      uint32_t keep = mask;
+      for (int k = 0; k < r1 - r0; ++k)
+        if (((mask >> k) & 1u) && (h->eqmask[r0 + k] & mask)) keep &= ~(1u << k);
+      h->atab.push_back((unsigned long long)mask | ((unsigned long long)keep << 32));
+    }
+  }
   h->rowkey.assign(R + 1, 0ull);
   for (int r = 0; r < R; ++r)
     for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e)
@@ -245,6 +272,8 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_colkey, h->colkey.data(), sizeof(unsigned long long) * m)) ||
       (rc = up(h->d_rowkey, h->rowkey.data(), sizeof(unsigned long long) * (R + 1))) ||
       (rc = up(h->d_eqmask, h->eqmask.data(), sizeof(uint32_t) * (R + 1))) ||
+      (rc = up(h->d_amet, h->amet.data(), sizeof(int2) * m)) ||
+      (rc = up(h->d_atab, h->atab.data(), sizeof(unsigned long long) * std::max<size_t>(h->atab.size(), 1))) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;
     return rc;
@@ -288,7 +317,7 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
   uint64_t* dpsi = reinterpret_cast<uint64_t*>(h->d_tmp.as<char>() + ((sizeof(int32_t) * m + 15) / 16) * 16);
   CK(cudaMemcpy(dC, c.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
   CK(cudaMemset(h->d_st.p, 0, sizeof(ChunkState)));
-  launch_psi(h->dev(), dC, 1, -1, dpsi, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
+  launch_psi(h->dev(), dC, 1, -1, dpsi, nullptr, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
   CK(cudaGetLastError());
   uint64_t ps = 0;
   CK(cudaMemcpy(&ps, dpsi, sizeof ps, cudaMemcpyDeviceToHost));
@@ -396,12 +425,14 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
       TRY(h->d_psi.reserve(sizeof(uint64_t) * (P + 1)));
       TRY(h->d_off.reserve(sizeof(uint64_t) * (P + 1)));
       TRY(h->d_scan_tmp.reserve(scan_temp_bytes(P + 1, 8)));
+      TRY(h->d_prec.reserve(sizeof(ParentRec) * (P + 1)));
       h->psi_cap = P + 1;
     }
     const int32_t* parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
     CK(cudaMemsetAsync(h->d_psi.as<uint64_t>() + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, P, o->max_expand_value, h->d_psi.as<uint64_t>(), h->d_st.as<ChunkState>(), st, nsm);
+    launch_psi(h->dev(), parents, P, o->max_expand_value, h->d_psi.as<uint64_t>(), h->d_prec.as<ParentRec>(),
+               h->d_st.as<ChunkState>(), st, nsm);
     CK(cudaGetLastError());
     sd.launches += 1 + scan_u64_sat(h->d_psi.as<uint64_t>(), h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
     CK(cudaGetLastError());
@@ -460,6 +491,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         a.gmin = h->d_gmin.as<uint32_t>();
         a.slot_of = h->d_slot_of.as<uint32_t>();
         a.ownbits = h->d_own.as<uint32_t>();
+        a.prec = h->d_prec.as<ParentRec>();
         a.st = h->d_st.as<ChunkState>();
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
         if (tc) {
@@ -738,7 +770,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
     const int32_t* parents = out + (size_t)level_lo * m;
     CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
     CK(cudaMemsetAsync(L.psi + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, P, o->max_expand_value, L.psi, L.st, st, nsm);
+    launch_psi(h->dev(), parents, P, o->max_expand_value, L.psi, nullptr, L.st, st, nsm);
     CK(cudaGetLastError());
     scan_u64_sat(L.psi, L.off, P + 1, L.scan_tmp, st);
     CK(cudaMemcpyAsync(h->pin.u64, L.off + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -782,6 +814,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       a.gmin = L.gmin;
       a.slot_of = L.slot_of;
       a.ownbits = L.own;
+      a.prec = nullptr;
       a.st = L.st;
       launch_expand(a, st, nsm);
       CK(cudaGetLastError());

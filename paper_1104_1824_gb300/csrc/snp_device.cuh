@@ -37,6 +37,8 @@ struct DevSys {
   const unsigned long long* colkey;  // [m] random odd multiplier R[j] of column j
   const unsigned long long* rowkey;  // [R] H[r] = sum over row r of M_Pi of M[r][j] * R[j] (mod 2^64)
   const uint32_t* eqmask;     // [R] positions of earlier rules of the same neuron with the same row of M_Pi
+  const int2* amet;           // [m] {offset into atab or -1, T | L << 16}: see appl()
+  const unsigned long long* atab;  // applicable-rule masks of each neuron by spike count
 };
 
 // Rule r, chosen for a neuron whose applicable rules are `mask`, gives the
@@ -45,6 +47,20 @@ struct DevSys {
 __device__ __forceinline__ bool redundant_choice(const DevSys& s, uint32_t mask, int r) {
   return (mask & __ldg(s.eqmask + r)) != 0u;
 }
+
+// Per-parent summary written with Psi (step a) for batches that cross
+// parents: the hash of the parent's base child (every neuron that can fire
+// uses its first applicable rule) and its neurons with two or more
+// applicable rules, in neuron order, as (neuron << 16) | mask.  nnt =
+// kRecFull when there are more than kRecNt of them or one does not fit 16
+// bits: such a parent is decoded from its row.
+constexpr int kRecNt = 9;
+constexpr uint32_t kRecFull = 0xFFFFFFFFu;
+struct __align__(16) ParentRec {
+  unsigned long long hbase;
+  uint32_t nnt;
+  uint32_t nt[kRecNt];
+};
 
 struct DevTable {
   unsigned long long* slots;  // [nbuckets * kBucket]: (fp32 << 32) | row
@@ -89,11 +105,43 @@ __device__ __forceinline__ uint64_t col_hash(const DevSys& s, int j, int32_t v) 
 }
 
 // a^x in L(a^i (a^j)*) and x >= c (Section 2.1, rule (b-1)).
-__device__ __forceinline__ bool rule_applies(int32_t x, int4 rp) {
+__host__ __device__ __forceinline__ bool rule_applies(int32_t x, int4 rp) {
   if (x < rp.x || x < rp.z) return false;
   if (rp.y == 0) return x == rp.x;
   if (rp.y == 1) return true;
   return ((x - rp.x) % rp.y) == 0;
+}
+
+// Applicable rules of neuron n holding x spikes, from the rules themselves:
+// bits 0-31 the mask (bit k = rule first_rule[n] + k), bits 32-63 the same
+// mask without the rules that repeat an earlier applicable rule's row.
+__device__ __forceinline__ uint64_t appl_rules(const DevSys& s, int n, int32_t x) {
+  const int r0 = __ldg(s.first_rule + n), r1 = __ldg(s.first_rule + n + 1);
+  uint32_t mask = 0;
+  for (int r = r0; r < r1; ++r)
+    if (rule_applies(x, __ldg(s.rule + r))) mask |= 1u << (r - r0);
+  uint32_t keep = mask;
+  for (uint32_t b = mask; b; b &= b - 1) {
+    const int k = __ffs(b) - 1;
+    if (__ldg(s.eqmask + r0 + k) & mask) keep &= ~(1u << k);
+  }
+  return (uint64_t)mask | ((uint64_t)keep << 32);
+}
+
+// appl_rules(s, n, x) by table.  Above T = 1 + the largest i or c of the
+// neuron's rules every threshold holds and a^i alone never matches, so the
+// masks repeat with period L = lcm of the rules' j >= 1: the table holds
+// x = 0 .. T + L - 1 and larger x fold onto T + (x - T) mod L.  Neurons whose
+// T + L is too large for a table (offset -1) evaluate their rules.
+__device__ __forceinline__ uint64_t appl(const DevSys& s, int n, int32_t x) {
+  const int2 mt = __ldg(s.amet + n);
+  if (mt.x >= 0 && x >= 0) {
+    const int T = mt.y & 0xFFFF, L = (int)((uint32_t)mt.y >> 16);
+    int k = x;
+    if (x >= T + L) k = T + ((L & (L - 1)) ? (x - T) % L : ((x - T) & (L - 1)));
+    return __ldg(s.atab + mt.x + k);
+  }
+  return appl_rules(s, n, x);
 }
 
 // Position of the d-th set bit (0-based) of mask.
@@ -153,11 +201,7 @@ __device__ __forceinline__ void load_parent(const DevSys& s, const int32_t* __re
   const int n0 = lane * s.K;
   const int n1 = min(n0 + s.K, s.m);
   for (int n = n0; n < n1; ++n) {
-    const int32_t x = w.par[n];
-    const int r0 = __ldg(s.first_rule + n), r1 = __ldg(s.first_rule + n + 1);
-    uint32_t mask = 0;
-    for (int r = r0; r < r1; ++r)
-      if (rule_applies(x, __ldg(s.rule + r))) mask |= 1u << (r - r0);
+    const uint32_t mask = (uint32_t)appl(s, n, w.par[n]);
     w.msk[n] = mask;
     prod = sat_mul(prod, mask ? (uint64_t)__popc(mask) : 1ull);
   }

@@ -1,48 +1,61 @@
 // The expand kernel: steps (b), (c) and (d) for one chunk of candidates.
 //
-// A warp takes a run of consecutive candidates of one parent (spiking-vector
-// indices t0, t0 + 1, ...).  It keeps a base: the digits of t0 in the mixed
-// radix of the per-neuron choice counts (Eq. psi; last neuron least
-// significant), the child C' = C + S . M_Pi of t0 (Eq. next-config) and its
-// linear hash.  A batch of up to 32 candidates is then built lane-parallel:
-// lane k adds k to the base's digits (only the few least significant
-// non-trivial neurons change), copies the base row into its own tile row and
-// swaps the changed neurons' rows of M_Pi (hash: swaps their H[r]).  Lane k
-// then resolves its row: it probes the hash table, compares full keys, and
-// either finds the key (seen before, or staged earlier in this chunk: then it
-// lowers that key's first-occurrence index) or claims an empty slot, stages
-// its row and publishes the slot.  The base then moves on by the batch size.
+// Candidates are spiking-vector indices in the mixed radix of the per-neuron
+// choice counts (Eq. psi; last neuron least significant).  A warp walks a run
+// of consecutive candidates in one of two ways:
+//
+// * block mode, while the current parent has 32 or more candidates left.  The
+//   least significant neurons with two or more applicable rules, as many as
+//   keep the product RL of their choice counts <= B, form a block: candidates
+//   b * RL .. b * RL + RL - 1 share every other digit.  Lane k owns candidate
+//   k of each block: once per parent it builds its row C' = C + S . M_Pi
+//   (Eq. next-config) from the block base plus its own low digits, with the
+//   linear hash of that row.  Moving to the next block changes the high
+//   digits like an odometer (usually one neuron): lane 0 lists the swapped
+//   rules and every lane swaps the same rows of M_Pi in its own row and their
+//   H[r] in its hash.
+// * crossing batches, once the parent has fewer than 32 candidates left: one
+//   candidate per lane, possibly of different parents, decoded from the
+//   parent's record (its multi-choice neurons and base hash) written with Psi.
+//   Surviving candidates are queued in the tile and their rows built all at
+//   once before they are resolved.
+//
+// Resolving a row (step d): probe the hash table, compare full keys, and
+// either find the key (seen before, or staged earlier in this chunk: then
+// lower that key's first-occurrence index) or claim an empty slot, stage the
+// row and publish the slot.
 #include "snp_kernels.cuh"
 
 namespace snp {
 
 namespace {
 
-constexpr int kLowDigits = 16;  // least significant non-trivial neurons tracked per parent
-
 struct ExpandSmem {
-  int32_t* tile;              // [B][ts] rows of candidates waiting for a lookup
-  unsigned long long* keys;   // [B] their table keys
-  uint32_t* lids;             // [B] their chunk-local indices
+  int32_t* tile;              // [B][ts] block mode: row k = lane k's candidate; crossing batches: queued rows
+  unsigned long long* keys;   // [B] crossing batches: table keys of the queued rows
+  long long* dpc;             // [B] parent of a queued row still to be built, else -1
+  unsigned long long* dt;     // [B] its index among the parent's candidates
+  uint32_t* lids;             // [B] chunk-local indices of the queued rows
   int32_t* par;               // [m4] parent
-  int32_t* buf;               // [m4] base child
+  int32_t* buf;               // [m4] block base child
   uint32_t* msk;              // [m4] applicable-rule masks
-  uint8_t* dig;               // [m4] base digits
-  int32_t* low;               // [kLowDigits] least significant non-trivial neurons, least first
-  int* nlow;                  // [1] entries of low
-  uint32_t* plow;             // [1] product of their choice counts (capped at 2^31)
-  uint32_t* vlow;             // [1] value of the base's digits on them (< plow)
-  unsigned long long* hbase;  // [1] linear hash of the base child
-  int* nred;                  // [1] neurons of the base that use a redundant rule (a later duplicate)
+  int32_t* ntl;               // [m4] neurons with two or more applicable rules, least significant first
+  int2* chg;                  // [m4] (old rule, new rule) pairs of the last block step
+  int* hdr;                   // [8] kNnt, kNlow, kRL, kNchg, kNred; hbase at hdr + 6
+  uint8_t* dig;               // [m4] digits of the block base
 };
+enum { kNnt = 0, kNlow = 1, kRL = 2, kNchg = 3, kNred = 4 };
+__device__ __forceinline__ unsigned long long& hbase_of(const ExpandSmem& w) {
+  return *reinterpret_cast<unsigned long long*>(w.hdr + 6);
+}
 
 __host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
 
-__host__ __device__ inline size_t expand_keys_bytes(int B) { return ((size_t)B * 12 + 15) & ~size_t(15); }
+__host__ __device__ inline size_t expand_keys_bytes(int B) { return ((size_t)B * 28 + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
   const int m4 = round4(m);
-  size_t b = (size_t)B * ts * 4 + expand_keys_bytes(B) + (size_t)m4 * 12 + 96 + (size_t)m4;
+  size_t b = (size_t)B * ts * 4 + expand_keys_bytes(B) + (size_t)m4 * 16 + (size_t)m4 * 8 + 32 + (size_t)m4;
   return (b + 15) & ~size_t(15);
 }
 
@@ -71,22 +84,19 @@ __device__ __forceinline__ void add_row_shared(const DevSys& s, int32_t* row, in
   }
 }
 
-// Step (a) for the parent row: masks, the list of the least significant
-// non-trivial neurons, and the mixed-radix place value of the neurons owned by
-// later lanes (neuron 0 most significant).
+// Step (a) for the parent row: masks, the multi-choice neurons (least
+// significant first), the block (the least significant of them whose choice
+// counts multiply to RL <= B) and, per lane, the mixed-radix place value of
+// the neurons owned by later lanes (neuron 0 most significant).
 __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const int32_t* __restrict__ row, ExpandSmem& w,
-                                                 int lane) {
+                                                 int B, int lane) {
   __syncwarp();
   for (int n = lane; n < s.m; n += 32) w.par[n] = row[n];
   __syncwarp();
   uint64_t prod = 1;
   const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
   for (int n = n0; n < n1; ++n) {
-    const int32_t x = w.par[n];
-    const int r0 = __ldg(s.first_rule + n), r1 = __ldg(s.first_rule + n + 1);
-    uint32_t mask = 0;
-    for (int r = r0; r < r1; ++r)
-      if (rule_applies(x, __ldg(s.rule + r))) mask |= 1u << (r - r0);
+    const uint32_t mask = (uint32_t)appl(s, n, w.par[n]);
     w.msk[n] = mask;
     prod = sat_mul(prod, mask ? (uint64_t)__popc(mask) : 1ull);
   }
@@ -98,31 +108,29 @@ __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const int32_t*
   }
   const uint64_t a = __shfl_down_sync(0xffffffffu, v, 1);
   __syncwarp();
-  // least significant non-trivial neurons, scanning 32 neurons at a time from the end
   int count = 0;
-  for (int top = s.m - 1; top >= 0 && count < kLowDigits; top -= 32) {
+  for (int top = s.m - 1; top >= 0; top -= 32) {
     const int n = top - lane;
     const bool nt = n >= 0 && __popc(w.msk[n]) > 1;
     const uint32_t b = __ballot_sync(0xffffffffu, nt);
-    const int rank = __popc(b & ((1u << lane) - 1u));
-    if (nt && count + rank < kLowDigits) w.low[count + rank] = n;
+    if (nt) w.ntl[count + __popc(b & ((1u << lane) - 1u))] = n;
     count += __popc(b);
   }
+  __syncwarp();
   if (lane == 0) {
-    const int nl = min(count, kLowDigits);
-    uint64_t pl = 1;
-    for (int i = 0; i < nl; ++i) {
-      pl *= (uint64_t)__popc(w.msk[w.low[i]]);
-      if (pl > (1ull << 31)) pl = 1ull << 31;
-    }
-    *w.nlow = nl;
-    *w.plow = (uint32_t)pl;
+    int nl = 0, rl = 1;
+    while (nl < count && rl * __popc(w.msk[w.ntl[nl]]) <= B) rl *= __popc(w.msk[w.ntl[nl++]]);
+    w.hdr[kNnt] = count;
+    w.hdr[kNlow] = nl;
+    w.hdr[kRL] = rl;
   }
   __syncwarp();
   return lane == 31 ? 1ull : a;
 }
 
-// The base becomes candidate t of the loaded parent: digits, child, hash.
+// The block base becomes candidate t of the loaded parent: digits, child in
+// buf, hash, and the count of neurons whose digit picks a rule that repeats an
+// earlier applicable rule's row.
 __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint64_t t, uint64_t after, int lane) {
   for (int n = lane; n < s.m; n += 32) w.buf[n] = w.par[n];
   uint64_t hp = 0;
@@ -158,34 +166,10 @@ __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint
   for (int o = 16; o > 0; o >>= 1) red += __shfl_xor_sync(0xffffffffu, red, o);
   __syncwarp();
   if (lane == 0) {
-    *w.hbase = hp;
-    *w.nred = red;
-    uint64_t v = 0, place = 1;
-    for (int i = 0; i < *w.nlow && place < (1ull << 31); ++i) {
-      const int n = w.low[i];
-      v += place * w.dig[n];
-      place *= __popc(w.msk[n]);
-    }
-    const uint64_t cap = (uint64_t)*w.plow - 1;
-    *w.vlow = (uint32_t)(v < cap ? v : cap);
+    hbase_of(w) = hp;
+    w.hdr[kNred] = red;
   }
   __syncwarp();
-}
-
-// Adds k to the base digits of the low neurons (k < the product of their
-// radices); calls f(neuron, old digit, new digit) for each changed one.
-template <typename F>
-__device__ __forceinline__ void add_to_digits(const ExpandSmem& w, uint32_t k, F&& f) {
-  const int nl = *w.nlow;
-  for (int i = 0; i < nl && k; ++i) {
-    const int n = w.low[i];
-    const uint32_t r = __popc(w.msk[n]);
-    const uint32_t d = w.dig[n];
-    const uint32_t sum = d + k;
-    const uint32_t nd = sum % r;
-    k = sum / r;
-    if (nd != d) f(n, (int)d, (int)nd);
-  }
 }
 
 template <bool VEC>
@@ -305,14 +289,14 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
   return true;
 }
 
-// Step (d) for the fill (<= 32) rows waiting in the tile, one per lane:
-// passes until every row is resolved; a lane never waits inside a pass, so
-// owners in this warp publish before anyone looks again.
+// Step (d) for one row per lane (lanes with todo set): passes until every
+// row is resolved; a lane never waits inside a pass, so owners in this warp
+// publish before anyone looks again.
 template <bool VEC>
-__device__ __forceinline__ void flush_tile(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
-  bool todo = lane < fill;
+__device__ __noinline__ void resolve_warp(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
+                                             bool todo) {
   for (int pass = 0;; ++pass) {
-    if (todo && resolve_lane<VEC>(a, w.tile + lane * ts, w.keys[lane], w.lids[lane])) todo = false;
+    if (todo && resolve_lane<VEC>(a, row, key, lid)) todo = false;
     if (__all_sync(0xffffffffu, !todo)) break;
     if (pass >= kSpinLimit) {
       if (todo) atomicOr(&a.st->error, kErrTimeout);
@@ -323,33 +307,239 @@ __device__ __forceinline__ void flush_tile(const ClaimArgs& a, ExpandSmem& w, in
   __syncwarp();
 }
 
+// Mixed-radix digit of a neuron with `radix` choices; q moves to the next
+// more significant neuron.
+__device__ __forceinline__ uint32_t next_digit(uint64_t& q, uint32_t radix) {
+  if (radix <= 1) return 0;
+  if ((q >> 32) == 0) {
+    const uint32_t q32 = (uint32_t)q;
+    q = q32 / radix;
+    return q32 % radix;
+  }
+  const uint32_t d = (uint32_t)(q % radix);
+  q /= radix;
+  return d;
+}
+
+// Calls f(n, x) for n = m - 1 down to 0 with x = row[n].
+template <bool VEC, typename F>
+__device__ __forceinline__ void for_each_neuron_desc(const int32_t* row, int m, F&& f) {
+  if (VEC) {
+    const int4* r4 = reinterpret_cast<const int4*>(row);
+    for (int n4 = (m >> 2) - 1; n4 >= 0; --n4) {
+      const int4 v = r4[n4];
+      f(4 * n4 + 3, v.w);
+      f(4 * n4 + 2, v.z);
+      f(4 * n4 + 1, v.y);
+      f(4 * n4, v.x);
+    }
+    return;
+  }
+  for (int n = m - 1; n >= 0; --n) f(n, row[n]);
+}
+
+// One lane's candidate in a batch that crosses parents.
+struct FlatLane {
+  uint64_t o;    // end of parent p + lane (off[p + 1 + lane])
+  uint64_t t;    // index of the lane's candidate among its parent's
+  uint64_t h;    // linear hash of the candidate's child
+  int64_t pc;    // the lane's parent
+};
+
+// Steps (b)-(c), decision half, for candidates g .. g + nf - 1 (nf <= B) of a
+// batch that may cross parents: each lane finds its parent among the next 32
+// (off is sorted) and decodes its spiking vector (last neuron least
+// significant).  From the parent's record only the multi-choice neurons are
+// visited: hash = record hash + H[chosen] - H[first applicable] for each
+// neuron whose digit is not 0; a parent without a record is decoded from its
+// row and the applicability table.  keep = the candidate picks no rule that
+// repeats an earlier applicable rule's row.  Returns nf, which shrinks when
+// parents without candidates push a parent beyond the 32 examined.
+template <bool VEC>
+__device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int nf, int64_t p, uint64_t p_lo,
+                                           int lane, FlatLane& f, bool& keep) {
+  const DevSys& s = a.sys;
+  const int64_t pj = p + 1 + lane;
+  f.o = pj <= a.P ? __ldcg(a.off + pj) : ~0ull;
+  const uint64_t o31 = __shfl_sync(0xffffffffu, f.o, 31);
+  if (o31 - g < (uint64_t)nf) nf = (int)(o31 - g);  // o31 > g: parent p holds g
+  const uint64_t c = g + lane;
+  int k = 0;  // parents p .. p + k - 1 end at or before c
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    const uint64_t v = __shfl_sync(0xffffffffu, f.o, k + step - 1);
+    if (v <= c) k += step;
+  }
+  const uint64_t prev = __shfl_sync(0xffffffffu, f.o, k > 0 ? k - 1 : 0);
+  f.pc = lane < nf ? p + k : p;
+  f.t = c - (k > 0 ? prev : p_lo);
+  f.h = 0;
+  keep = false;
+  if (lane >= nf) return nf;
+  uint64_t q = f.t;
+  bool red = false;
+  uint32_t nnt = kRecFull;
+  const ParentRec* rec = a.prec ? a.prec + f.pc : nullptr;
+  if (rec) {
+    const uint4 head = __ldcg(reinterpret_cast<const uint4*>(rec));
+    f.h = ((unsigned long long)head.y << 32) | head.x;
+    nnt = head.z;
+  }
+  if (nnt != kRecFull) {
+    uint64_t h = f.h;
+    for (int i = (int)nnt - 1; i >= 0; --i) {
+      const uint32_t e = __ldcg(rec->nt + i);
+      const uint32_t mask = e & 0xFFFFu;
+      const uint32_t d = next_digit(q, __popc(mask));
+      if (d == 0) continue;
+      const int r0 = __ldg(s.first_rule + (e >> 16));
+      const int rb = r0 + nth_set_bit(mask, (int)d);
+      h += __ldg(s.rowkey + rb) - __ldg(s.rowkey + r0 + __ffs(mask) - 1);
+      red |= (__ldg(s.eqmask + rb) & mask) != 0u;
+    }
+    f.h = h;
+  } else {
+    uint64_t h = 0;
+    for_each_neuron_desc<VEC>(a.parents + (size_t)f.pc * s.m, s.m, [&](int n, int32_t x) {
+      h += col_hash(s, n, x);
+      const uint64_t am = appl(s, n, x);
+      const uint32_t mask = (uint32_t)am;
+      if (!mask) return;
+      const int kb = nth_set_bit(mask, (int)next_digit(q, __popc(mask)));
+      h += __ldg(s.rowkey + __ldg(s.first_rule + n) + kb);
+      red |= ((am >> (32 + kb)) & 1ull) == 0;
+    });
+    f.h = h;
+  }
+  keep = !red;
+  return nf;
+}
+
+// Step (c) for a candidate of a crossing batch: C' = C + the chosen rules'
+// rows, built in a tile row (one lane).
+template <bool VEC>
+__device__ __forceinline__ void flat_build(const ClaimArgs& a, int64_t pc, uint64_t t, int32_t* trow) {
+  const DevSys& s = a.sys;
+  const int32_t* prow = a.parents + (size_t)pc * s.m;
+  copy_row<VEC>(prow, trow, s.m);
+  uint64_t q = t;
+  for_each_neuron_desc<VEC>(prow, s.m, [&](int n, int32_t x) {
+    const uint32_t mask = (uint32_t)appl(s, n, x);
+    if (!mask) return;
+    const int kb = nth_set_bit(mask, (int)next_digit(q, __popc(mask)));
+    add_row_private(s, trow, __ldg(s.first_rule + n) + kb, 1);
+  });
+}
+
 // Per-warp shared memory of the expand loop.
 __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, int B, int ts) {
   const int m4 = round4(m);
   ExpandSmem w;
   w.tile = reinterpret_cast<int32_t*>(base);
   w.keys = reinterpret_cast<unsigned long long*>(w.tile + (size_t)B * ts);
-  w.lids = reinterpret_cast<uint32_t*>(w.keys + B);
+  w.dpc = reinterpret_cast<long long*>(w.keys + B);
+  w.dt = reinterpret_cast<unsigned long long*>(w.dpc + B);
+  w.lids = reinterpret_cast<uint32_t*>(w.dt + B);
   w.par = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(w.keys) + expand_keys_bytes(B));
   w.buf = w.par + m4;
   w.msk = reinterpret_cast<uint32_t*>(w.buf + m4);
-  w.low = reinterpret_cast<int32_t*>(w.msk + m4);               // 64 bytes
-  w.nlow = w.low + kLowDigits;                                    // +64
-  w.plow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 1);   // +68
-  w.vlow = reinterpret_cast<uint32_t*>(w.low + kLowDigits + 2);   // +72
-  w.hbase = reinterpret_cast<unsigned long long*>(w.low + kLowDigits + 4);  // +80
-  w.nred = w.low + kLowDigits + 6;                                // +88
-  w.dig = reinterpret_cast<uint8_t*>(w.low) + 96;
+  w.ntl = reinterpret_cast<int32_t*>(w.msk + m4);
+  w.chg = reinterpret_cast<int2*>(w.ntl + m4);
+  w.hdr = reinterpret_cast<int*>(w.chg + m4);
+  w.dig = reinterpret_cast<uint8_t*>(w.hdr + 8);
   return w;
 }
 
+// Resolves the queued rows of crossing batches (building them first).
+template <bool VEC>
+__device__ __forceinline__ void flush_queue(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
+  const bool mine = lane < fill;
+  if (mine && w.dpc[lane] >= 0) flat_build<VEC>(a, w.dpc[lane], w.dt[lane], w.tile + lane * ts);
+  __syncwarp();
+  resolve_warp<VEC>(a, w.tile + lane * ts, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine);
+}
+
+// Block mode for parent p from candidate a.g0 + l to the end of the parent or
+// of the task; returns the new l.
+template <bool VEC>
+__device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w, int B, int ts, int64_t p,
+                                              uint64_t p_lo, uint64_t p_hi, uint64_t l, uint64_t lb, int lane) {
+  const DevSys& s = a.sys;
+  const int m = s.m;
+  const uint64_t g = a.g0 + l;
+  const uint64_t gend = min(p_hi, a.g0 + lb);
+  const uint64_t after = parent_state(s, a.parents + (size_t)p * m, w, B, lane);
+  const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
+  uint64_t b = (g - p_lo) / (uint64_t)RL;
+  decode_full(s, w, b * (uint64_t)RL, after, lane);
+  // lane k < RL: candidate k of the block = base + its low digits
+  int32_t* row = w.tile + lane * ts;
+  uint64_t hk = 0;
+  bool redk = true;
+  if (lane < RL) {
+    copy_row<VEC>(w.buf, row, m);
+    redk = false;
+    uint32_t q = (uint32_t)lane;
+    for (int i = 0; i < nlow; ++i) {
+      const int n = w.ntl[i];
+      const uint32_t mask = w.msk[n];
+      const uint32_t radix = __popc(mask);
+      const uint32_t d = q % radix;
+      q /= radix;
+      if (d == 0) continue;
+      const int r0 = rule_of(s, w, n, 0), rd = rule_of(s, w, n, (int)d);
+      add_row_private(s, row, r0, -1);
+      add_row_private(s, row, rd, 1);
+      hk += __ldg(s.rowkey + rd) - __ldg(s.rowkey + r0);
+      redk |= redundant_choice(s, mask, rd);
+    }
+  }
+  uint64_t gb = p_lo + b * (uint64_t)RL;
+  for (;;) {
+    const uint64_t c = gb + lane;
+    const bool todo = lane < RL && c >= g && c < gend && !redk && w.hdr[kNred] == 0;
+    resolve_warp<VEC>(a, row, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo);
+    gb += (uint64_t)RL;
+    if (gb >= gend) break;
+    // next block: the high digits move on by one (odometer, least significant first)
+    if (lane == 0) {
+      uint64_t h = hbase_of(w);
+      int red = w.hdr[kNred], nc = 0;
+      for (int i = nlow; i < nnt; ++i) {
+        const int n = w.ntl[i];
+        const uint32_t mask = w.msk[n];
+        const int d = w.dig[n];
+        const int nd = (d + 1 == __popc(mask)) ? 0 : d + 1;
+        const int ro = rule_of(s, w, n, d), rn = rule_of(s, w, n, nd);
+        w.chg[nc++] = make_int2(ro, rn);
+        h += __ldg(s.rowkey + rn) - __ldg(s.rowkey + ro);
+        red += (redundant_choice(s, mask, rn) ? 1 : 0) - (redundant_choice(s, mask, ro) ? 1 : 0);
+        w.dig[n] = (uint8_t)nd;
+        if (nd != 0) break;
+      }
+      hbase_of(w) = h;
+      w.hdr[kNred] = red;
+      w.hdr[kNchg] = nc;
+    }
+    __syncwarp();
+    if (lane < RL) {
+      const int nc = w.hdr[kNchg];
+      for (int j = 0; j < nc; ++j) {
+        const int2 rr = w.chg[j];
+        add_row_private(s, row, rr.x, -1);
+        add_row_private(s, row, rr.y, 1);
+      }
+    }
+  }
+  return gend - a.g0;
+}
+
 // Steps (b)-(d) for the tasks task0, task0 + tstride, ... of chunk a (a task
-// is a run of a.run consecutive candidates), by one warp.
+// is a run of a.run consecutive candidates), by one warp: block mode while
+// the parent has 32 or more candidates left, else crossing batches.
 template <bool VEC>
 __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, ExpandSmem& w, uint64_t task0,
                                             uint64_t tstride, int lane) {
-  const DevSys& s = a.sys;
-  const int m = s.m;
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
   for (uint64_t task = task0; task < ntasks; task += tstride) {
     const uint64_t la = task * a.run;
@@ -357,85 +547,62 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
     int64_t p = warp_find_parent(a.off, a.P, a.g0 + la, lane);
     uint64_t p_lo = __ldcg(a.off + p), p_hi = __ldcg(a.off + p + 1);
     if (task == 0 && lane == 0) a.st->p_first = (unsigned long long)p;
-    uint64_t after = parent_state(s, a.parents + (size_t)p * m, w, lane);
-    decode_full(s, w, a.g0 + la - p_lo, after, lane);
     uint64_t l = la;
-    int fill = 0;  // rows waiting in the tile
-    while (l < lb) {
+    int fill = 0;  // rows queued by crossing batches
+    for (;;) {
+      const bool done = l >= lb;
       const uint64_t g = a.g0 + l;
-      // a batch never crosses a parent, nor a rollover of the tracked low digits
-      const uint32_t room = *w.plow - *w.vlow;
-      const int nb = (int)min(min(min((uint64_t)B, lb - l), p_hi - g), (uint64_t)room);
-      if (nb <= 0) {  // cannot happen: every bound above is positive
-        if (lane == 0) atomicOr(&a.st->error, kErrInternal);
-        break;
+      if (done || p_hi - g >= 32) {
+        if (fill > 0) {  // the tile is about to be reused, or the task ends
+          flush_queue<VEC>(a, w, ts, fill, lane);
+          fill = 0;
+        }
+        if (done) break;
+        l = block_run<VEC>(a, w, B, ts, p, p_lo, p_hi, l, lb, lane);
+        const uint64_t gn = a.g0 + l;
+        if (l < lb) {
+          do {
+            ++p;
+            p_lo = p_hi;
+            p_hi = __ldcg(a.off + p + 1);
+          } while (gn >= p_hi);
+        }
+        continue;
       }
-      // a candidate using a redundant rule repeats an earlier one: no lookup needed
+      // crossing batch
+      FlatLane f;
       bool keep = false;
-      if (lane < nb) {
-        int red = *w.nred;
-        add_to_digits(w, (uint32_t)lane, [&](int n, int d, int nd) {
-          const uint32_t mask = w.msk[n];
-          red += (redundant_choice(s, mask, rule_of(s, w, n, nd)) ? 1 : 0) -
-                 (redundant_choice(s, mask, rule_of(s, w, n, d)) ? 1 : 0);
-        });
-        keep = red == 0;
-      }
+      const int nb = flat_decode<VEC>(a, g, (int)min((uint64_t)B, lb - l), p, p_lo, lane, f, keep);
       const uint32_t kept = __ballot_sync(0xffffffffu, keep);
-      if (fill + __popc(kept) > B) {  // no room for this batch's rows: resolve what waits
-        flush_tile<VEC>(a, w, ts, fill, lane);
+      if (fill + __popc(kept) > B) {
+        flush_queue<VEC>(a, w, ts, fill, lane);
         fill = 0;
       }
-      if (keep) {  // build the row in the next free tile slot
+      if (keep) {
         const int slot = fill + __popc(kept & ((1u << lane) - 1u));
-        int32_t* trow = w.tile + slot * ts;
-        copy_row<VEC>(w.buf, trow, m);
-        uint64_t h = *w.hbase;
-        add_to_digits(w, (uint32_t)lane, [&](int n, int d, int nd) {
-          const int r_old = rule_of(s, w, n, d), r_new = rule_of(s, w, n, nd);
-          add_row_private(s, trow, r_old, -1);
-          add_row_private(s, trow, r_new, 1);
-          h += __ldg(s.rowkey + r_new) - __ldg(s.rowkey + r_old);
-        });
-        w.keys[slot] = mix64(h);
+        w.dpc[slot] = f.pc;
+        w.dt[slot] = f.t;
+        w.keys[slot] = mix64(f.h);
         w.lids[slot] = (uint32_t)(l + lane);
       }
       fill += __popc(kept);
       __syncwarp();
-      if (fill >= B || l + nb >= lb) {
-        flush_tile<VEC>(a, w, ts, fill, lane);
-        fill = 0;
+      l += (uint64_t)nb;
+      if (l >= lb) {  // keep the parent of the task's last candidate
+        p = __shfl_sync(0xffffffffu, f.pc, nb - 1);
+        continue;
       }
-      l += nb;
-      if (l >= lb) break;
       const uint64_t gn = a.g0 + l;
-      if (gn >= p_hi) {  // next parent
-        do {
-          ++p;
-          p_lo = p_hi;
-          p_hi = __ldcg(a.off + p + 1);
-        } while (gn >= p_hi);
-        after = parent_state(s, a.parents + (size_t)p * m, w, lane);
-        decode_full(s, w, gn - p_lo, after, lane);
-      } else if ((uint32_t)nb == room) {  // the low digits roll over: decode in full
-        decode_full(s, w, gn - p_lo, after, lane);
-      } else {  // same parent: the base moves on by nb
-        if (lane == 0) {
-          uint64_t h = *w.hbase;
-          int red = *w.nred;
-          add_to_digits(w, (uint32_t)nb, [&](int n, int d, int nd) {
-            const int r_old = rule_of(s, w, n, d), r_new = rule_of(s, w, n, nd);
-            add_row_private(s, w.buf, r_old, -1);
-            add_row_private(s, w.buf, r_new, 1);
-            h += __ldg(s.rowkey + r_new) - __ldg(s.rowkey + r_old);
-            red += (redundant_choice(s, w.msk[n], r_new) ? 1 : 0) - (redundant_choice(s, w.msk[n], r_old) ? 1 : 0);
-            w.dig[n] = (uint8_t)nd;
-          });
-          *w.hbase = h;
-          *w.nred = red;
-          *w.vlow += (uint32_t)nb;
-        }
-        __syncwarp();
+      const int kn = __popc(__ballot_sync(0xffffffffu, f.o <= gn));  // parents ending at or before gn
+      if (kn < 32) {
+        const uint64_t lo = __shfl_sync(0xffffffffu, f.o, kn > 0 ? kn - 1 : 0);
+        p_hi = __shfl_sync(0xffffffffu, f.o, kn);
+        if (kn > 0) p_lo = lo;
+        p += kn;
+      } else {
+        p = warp_find_parent(a.off, a.P, gn, lane);
+        p_lo = __ldcg(a.off + p);
+        p_hi = __ldcg(a.off + p + 1);
       }
     }
     if (task + 1 == ntasks && lane == 0) a.st->p_last = (unsigned long long)p;
@@ -632,12 +799,9 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       const int32_t* row = parents + (size_t)p * m;
       uint64_t prod = 1;
       bool skip = false, ov = false;
-      int r = __ldg(S.first_rule);
       for (int n = 0; n < m; ++n) {
         const int32_t x = row[n];
-        const int r1 = __ldg(S.first_rule + n + 1);
-        uint32_t cnt = 0;
-        for (; r < r1; ++r) cnt += rule_applies(x, __ldg(S.rule + r)) ? 1u : 0u;
+        const uint32_t cnt = __popc((uint32_t)appl(S, n, x));
         if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
         ov |= x > INT32_MAX - __ldg(S.gain + n);
         skip |= max_expand >= 0 && x > max_expand;
@@ -678,6 +842,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       a.gmin = sc.gmin;
       a.slot_of = sc.slot_of;
       a.ownbits = sc.own;
+      a.prec = nullptr;
       a.st = sc.st;
       if ((m & 3) == 0)
         expand_warp<true>(a, ba.B, ba.ts, w, warp, nwarps, lane);

@@ -29,29 +29,17 @@ __device__ __forceinline__ void set_error(ChunkState* st, uint32_t bits) { atomi
 // Step (a) and Eq. psi for every frontier row, one lane per row: counts each
 // neuron's applicable rules, Psi = prod max(1, omega) (saturating); flags rows
 // whose children could leave int32 and gives Psi = 0 to rows not to be
-// expanded (max_expand).  The rule table sits in shared memory when it fits.
-template <bool SMEM, bool VEC>
+// expanded (max_expand).  With REC it also writes the row's ParentRec.
+template <bool VEC, bool REC>
 __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand,
-                                             uint64_t* psi, ChunkState* st) {
-  extern __shared__ __align__(16) unsigned char psi_smem[];
+                                             uint64_t* psi, ParentRec* rec, ChunkState* st) {
   const int m = s.m;
-  const int4* rule = s.rule;
-  const int32_t* fr = s.first_rule;
-  if (SMEM) {
-    int4* r4 = reinterpret_cast<int4*>(psi_smem);
-    int32_t* f4 = reinterpret_cast<int32_t*>(r4 + s.R);
-    for (int i = threadIdx.x; i < s.R; i += blockDim.x) r4[i] = s.rule[i];
-    for (int i = threadIdx.x; i <= m; i += blockDim.x) f4[i] = s.first_rule[i];
-    __syncthreads();
-    rule = r4;
-    fr = f4;
-  }
   bool over = false;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t* row = rows + (size_t)p * m;
-    uint64_t prod = 1;
+    uint64_t prod = 1, hb = 0;
+    uint32_t nnt = 0;
     bool skip = false, ov = false;
-    int r = fr[0];
     for (int n0 = 0; n0 < m; n0 += 4) {
       int x4[4];
       if (VEC) {
@@ -66,32 +54,39 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int6
         const int n = n0 + u;
         if (n >= m) break;
         const int32_t x = x4[u];
-        const int r1 = fr[n + 1];
-        uint32_t cnt = 0;
-        for (; r < r1; ++r) cnt += rule_applies(x, rule[r]) ? 1u : 0u;
+        const uint32_t mask = (uint32_t)appl(s, n, x);
+        const uint32_t cnt = __popc(mask);
         if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
         ov |= x > INT32_MAX - __ldg(s.gain + n);
         skip |= max_expand >= 0 && x > max_expand;
+        if (REC) {
+          hb += col_hash(s, n, x);
+          if (mask) hb += __ldg(s.rowkey + __ldg(s.first_rule + n) + __ffs(mask) - 1);
+          if (cnt > 1) {
+            if (nnt < (uint32_t)kRecNt && n < 65536 && mask < 65536u) rec[p].nt[nnt] = ((uint32_t)n << 16) | mask;
+            nnt = (nnt < (uint32_t)kRecNt && n < 65536 && mask < 65536u) ? nnt + 1 : kRecFull;
+          }
+        }
       }
     }
     psi[p] = skip ? 0ull : prod;
+    if (REC) {
+      rec[p].hbase = hb;
+      rec[p].nnt = nnt;
+    }
     over |= ov && !skip;
   }
   if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
 }
 
-int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ChunkState* st,
-               cudaStream_t stream, int nsm) {
-  const size_t table = (size_t)s.R * sizeof(int4) + (size_t)(s.m + 1) * sizeof(int32_t);
-  const bool smem = table <= (96u << 10);
-  const bool vec = (s.m % 4) == 0;
+int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ParentRec* rec,
+               ChunkState* st, cudaStream_t stream, int nsm) {
   const int threads = 256;
   const int64_t want = (P + threads - 1) / threads;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
-  auto fn = smem ? (vec ? k_psi<true, true> : k_psi<true, false>) : (vec ? k_psi<false, true> : k_psi<false, false>);
-  const size_t bytes = smem ? table : 0;
-  if (bytes > (48u << 10)) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  fn<<<blocks, threads, bytes, stream>>>(s, rows, P, max_expand, psi, st);
+  const bool vec = (s.m % 4) == 0;
+  auto fn = rec ? (vec ? k_psi<true, true> : k_psi<false, true>) : (vec ? k_psi<true, false> : k_psi<false, false>);
+  fn<<<blocks, threads, 0, stream>>>(s, rows, P, max_expand, psi, rec, st);
   return 1;
 }
 

@@ -20,6 +20,7 @@ struct ClaimArgs {
   uint32_t* gmin;             // [Q] per claiming lid: smallest chunk-local candidate holding its key
   uint32_t* slot_of;          // [Q] per claiming lid: its table slot
   uint32_t* ownbits;          // [Q / 32 + 1] bit lid set iff candidate lid claimed a new key
+  const ParentRec* prec;      // [P] parent summaries, or nullptr (decode from the rows)
   ChunkState* st;
 };
 
@@ -99,7 +100,7 @@ void launch_batch_depth(const BatchArgs& a, int blocks, int warps, cudaStream_t 
 __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n);
 
 // Step (a) and Psi for P frontier rows; returns the launches made.
-int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ChunkState* st,
+int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ParentRec* rec, ChunkState* st,
                cudaStream_t stream, int nsm);
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
