@@ -237,55 +237,63 @@ __device__ __forceinline__ void stage_row_lane(const int32_t* row, int32_t* dst,
 // reserved but not yet published; the caller then tries again in a later pass.
 template <bool VEC>
 __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid) {
+  // A bucket fills as a prefix (a slot is claimed only when every earlier
+  // slot was seen taken, and slots never become empty again), so the slots
+  // holding our fingerprint all precede the first empty one.  Each bucket is
+  // classified branch-free; the compare, the claim and the owner's work then
+  // run once per lane, which keeps lanes that hit different slots together.
   const int m = a.sys.m;
   const uint32_t fp = fp32_of(key);
+  const unsigned long long mine = ((unsigned long long)fp << 32) | kRowReserved;
   uint64_t bucket = key & a.table.bmask;
-  for (uint64_t probes = 0; probes <= a.table.bmask; ++probes, bucket = (bucket + 1) & a.table.bmask) {
+  unsigned long long* owned = nullptr;
+  for (uint64_t probes = 0; probes <= a.table.bmask && !owned;) {
     unsigned long long* bs = a.table.slots + bucket * kBucket;
-    unsigned long long v[kBucket];
     const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(bs);
+    uint32_t match = 0, empty = 0;
 #pragma unroll
     for (int q = 0; q < kBucket / 2; ++q) {
       const ulonglong2 x = __ldcg(b2 + q);
-      v[2 * q] = x.x;
-      v[2 * q + 1] = x.y;
+      empty |= (x.x == kEmpty ? 1u : 0u) << (2 * q);
+      empty |= (x.y == kEmpty ? 1u : 0u) << (2 * q + 1);
+      match |= ((uint32_t)(x.x >> 32) == fp && (uint32_t)x.x != kRowTomb && x.x != kEmpty ? 1u : 0u) << (2 * q);
+      match |= ((uint32_t)(x.y >> 32) == fp && (uint32_t)x.y != kRowTomb && x.y != kEmpty ? 1u : 0u) << (2 * q + 1);
     }
-#pragma unroll
-    for (int j = 0; j < kBucket; ++j) {
-      unsigned long long x = v[j];
-      for (;;) {  // until slot j holds a key that is not ours, or we are done
-        if (x == kEmpty) {
-          const unsigned long long old = atomicCAS(bs + j, kEmpty, ((unsigned long long)fp << 32) | kRowReserved);
-          if (old == kEmpty) {  // owner: stage, record, publish
-            stage_row_lane<VEC>(row, a.staging + (size_t)lid * m, m);
-            a.gmin[lid] = lid;
-            a.slot_of[lid] = (uint32_t)(bucket * kBucket + j);
-            atomicOr(a.ownbits + (lid >> 5), 1u << (lid & 31));
-            st_release(bs + j, ((unsigned long long)fp << 32) | (kPending | lid));
-            return true;
-          }
-          x = old;  // someone else took the slot: look at what is there now
-          continue;
-        }
-        const uint32_t rf = (uint32_t)x;
-        if ((uint32_t)(x >> 32) != fp || rf == kRowTomb) break;
-        if (rf == kRowReserved) return false;  // published soon: try again later
-        const int32_t* other;
-        if (rf & kPending) {
-          (void)ld_acquire(bs + j);  // orders the staged row's reads after the publish
-          other = a.staging + (size_t)(rf & ~kPending) * m;
-        } else {
-          other = a.pool + (size_t)rf * m;
-        }
-        if (row_equal_lane<VEC>(row, other, m)) {
-          if (rf & kPending) atomicMin(a.gmin + (rf & ~kPending), lid);
-          return true;
-        }
-        break;
+    for (; match; match &= match - 1) {
+      const int j = __ffs(match) - 1;
+      const unsigned long long x = __ldcg(bs + j);
+      const uint32_t rf = (uint32_t)x;
+      if (rf == kRowReserved) return false;  // published soon: try again later
+      const int32_t* other;
+      if (rf & kPending) {
+        (void)ld_acquire(bs + j);  // orders the staged row's reads after the publish
+        other = a.staging + (size_t)(rf & ~kPending) * m;
+      } else {
+        other = a.pool + (size_t)rf * m;
+      }
+      if (row_equal_lane<VEC>(row, other, m)) {
+        if (rf & kPending) atomicMin(a.gmin + (rf & ~kPending), lid);
+        return true;
       }
     }
+    if (empty) {
+      const int j = __ffs(empty) - 1;
+      if (atomicCAS(bs + j, kEmpty, mine) == kEmpty) owned = bs + j;
+      continue;  // owner, or look at this bucket again
+    }
+    ++probes;
+    bucket = (bucket + 1) & a.table.bmask;
   }
-  atomicOr(&a.st->error, kErrTableFull);
+  if (!owned) {
+    atomicOr(&a.st->error, kErrTableFull);
+    return true;
+  }
+  // owner: stage, record, publish
+  stage_row_lane<VEC>(row, a.staging + (size_t)lid * m, m);
+  a.gmin[lid] = lid;
+  a.slot_of[lid] = (uint32_t)(owned - a.table.slots);
+  atomicOr(a.ownbits + (lid >> 5), 1u << (lid & 31));
+  st_release(owned, ((unsigned long long)fp << 32) | (kPending | lid));
   return true;
 }
 
