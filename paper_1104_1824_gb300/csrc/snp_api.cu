@@ -229,14 +229,24 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     for (int q = r0; q < r; ++q)
       if (std::equal(&h->M[(size_t)q * m], &h->M[(size_t)q * m] + m, &h->M[(size_t)r * m])) h->eqmask[r] |= 1u << (q - r0);
   }
+  h->rowkey.assign(R + 1, 0ull);
+  for (int r = 0; r < R; ++r)
+    for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e)
+      h->rowkey[r] += (uint64_t)(int64_t)h->csr[e].y * h->colkey[h->csr[e].x];
   // Applicable rules by spike count.  Above T = 1 + the largest i or c of a
   // neuron's rules, a^x in L(a^i (a^j)*) reduces to (x - i) mod j == 0 for the
-  // rules with j >= 1, so the masks repeat with period L = lcm of those j:
-  // the table holds x = 0 .. T + L - 1 (bits 0-31 the mask, bits 32-63 the
-  // mask without rules that repeat an earlier applicable rule's row).
-  h->amet.assign(m, make_int2(-1, 0));
+  // rules with j >= 1, so the entries repeat with period L = lcm of those j:
+  // the table holds x = 0 .. T + L - 1.  Larger x fold onto T + (x - T) mod L
+  // on the device, dividing by L as (v * magic) >> shift with
+  // shift = 32 + ceil(log2 L) and magic = ceil(2^shift / L), exact for v < 2^31
+  // (Granlund and Montgomery, PLDI 1994).
+  h->ninfo.assign(m, snp::NeuronInfo{});
   h->atab.clear();
   for (int n = 0; n < m; ++n) {
+    snp::NeuronInfo& ni = h->ninfo[n];
+    ni.off = -1;
+    ni.gain = h->gain[n];
+    ni.colkey = h->colkey[n];
     const int r0 = h->first_rule[n], r1 = h->first_rule[n + 1];
     int64_t T = 1, L = 1;
     for (int r = r0; r < r1 && L <= 64; ++r) {
@@ -244,7 +254,12 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       if (h->rule[r].y >= 1) L = std::lcm<int64_t>(L, h->rule[r].y);
     }
     if (L > 64 || T + L > 256) continue;  // evaluated from the rules on the device
-    h->amet[n] = make_int2((int)h->atab.size(), (int)(T | (L << 16)));
+    uint32_t lg = 0;
+    while ((1ll << lg) < L) ++lg;
+    ni.off = (int32_t)h->atab.size();
+    ni.tl = (uint32_t)(T | (L << 16));
+    ni.shift = 32 + lg;
+    ni.magic = (((unsigned long long)1 << ni.shift) + (unsigned long long)L - 1) / (unsigned long long)L;
     for (int32_t x = 0; x < T + L; ++x) {
       uint32_t mask = 0;
       for (int r = r0; r < r1; ++r)
@@ -252,13 +267,13 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       uint32_t keep = mask;
       for (int k = 0; k < r1 - r0; ++k)
         if (((mask >> k) & 1u) && (h->eqmask[r0 + k] & mask)) keep &= ~(1u << k);
-      h->atab.push_back((unsigned long long)mask | ((unsigned long long)keep << 32));
+      snp::ApplEntry ae;
+      ae.mask = mask;
+      ae.keep = keep;
+      ae.hfirst = mask ? h->rowkey[r0 + __builtin_ctz(mask)] : 0ull;
+      h->atab.push_back(ae);
     }
   }
-  h->rowkey.assign(R + 1, 0ull);
-  for (int r = 0; r < R; ++r)
-    for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e)
-      h->rowkey[r] += (uint64_t)(int64_t)h->csr[e].y * h->colkey[h->csr[e].x];
   int rc = SNP_OK;
   auto up = [&](DevBuf& b, const void* src, size_t bytes) -> int {
     if ((rc = b.reserve(std::max<size_t>(bytes, 16))) != SNP_OK) return rc;
@@ -272,8 +287,8 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_colkey, h->colkey.data(), sizeof(unsigned long long) * m)) ||
       (rc = up(h->d_rowkey, h->rowkey.data(), sizeof(unsigned long long) * (R + 1))) ||
       (rc = up(h->d_eqmask, h->eqmask.data(), sizeof(uint32_t) * (R + 1))) ||
-      (rc = up(h->d_amet, h->amet.data(), sizeof(int2) * m)) ||
-      (rc = up(h->d_atab, h->atab.data(), sizeof(unsigned long long) * std::max<size_t>(h->atab.size(), 1))) ||
+      (rc = up(h->d_ninfo, h->ninfo.data(), sizeof(snp::NeuronInfo) * m)) ||
+      (rc = up(h->d_atab, h->atab.data(), sizeof(snp::ApplEntry) * std::max<size_t>(h->atab.size(), 1))) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;
     return rc;
@@ -384,6 +399,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * rows_plan));
     h->pool_rows = rows_plan;
   }
+
   if (o->record_parents) {
     TRY(h->d_rec_parent.reserve(sizeof(int64_t) * h->pool_rows));
     TRY(h->d_rec_index.reserve(sizeof(uint64_t) * h->pool_rows));
@@ -423,18 +439,19 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     CK(cudaEventRecord(h->ev[0], st));
     if (h->psi_cap < P + 1) {
       TRY(h->d_psi.reserve(sizeof(uint64_t) * (P + 1)));
+      TRY(h->d_prec.reserve(sizeof(ParentRec) * (P + 1)));
       TRY(h->d_off.reserve(sizeof(uint64_t) * (P + 1)));
       TRY(h->d_scan_tmp.reserve(scan_temp_bytes(P + 1, 8)));
-      TRY(h->d_prec.reserve(sizeof(ParentRec) * (P + 1)));
       h->psi_cap = P + 1;
     }
     const int32_t* parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
-    CK(cudaMemsetAsync(h->d_psi.as<uint64_t>() + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, P, o->max_expand_value, h->d_psi.as<uint64_t>(), h->d_prec.as<ParentRec>(),
-               h->d_st.as<ChunkState>(), st, nsm);
+    uint64_t* psi = h->d_psi.as<uint64_t>();
+    CK(cudaMemsetAsync(psi + P, 0, sizeof(uint64_t), st));
+    launch_psi(h->dev(), parents, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(), h->d_st.as<ChunkState>(),
+               st, nsm);
     CK(cudaGetLastError());
-    sd.launches += 1 + scan_u64_sat(h->d_psi.as<uint64_t>(), h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
+    sd.launches += 1 + scan_u64_sat(psi, h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
     CK(cudaGetLastError());
     uint64_t total = 0;
     CK(cudaMemcpyAsync(h->pin.u64, h->d_off.as<uint64_t>() + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));

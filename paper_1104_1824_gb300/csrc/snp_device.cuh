@@ -27,6 +27,9 @@ constexpr uint32_t kErrInternal = 16u;
 // Bound on the wait for a reserved slot to be published.
 constexpr int kSpinLimit = 1 << 22;
 
+struct NeuronInfo;
+struct ApplEntry;
+
 // The system as the kernels see it.
 struct DevSys {
   int32_t m, R, K;            // K = neurons owned by one lane = ceil(m / 32)
@@ -37,8 +40,25 @@ struct DevSys {
   const unsigned long long* colkey;  // [m] random odd multiplier R[j] of column j
   const unsigned long long* rowkey;  // [R] H[r] = sum over row r of M_Pi of M[r][j] * R[j] (mod 2^64)
   const uint32_t* eqmask;     // [R] positions of earlier rules of the same neuron with the same row of M_Pi
-  const int2* amet;           // [m] {offset into atab or -1, T | L << 16}: see appl()
-  const unsigned long long* atab;  // applicable-rule masks of each neuron by spike count
+  const NeuronInfo* ninfo;    // [m] per-neuron constants: see appl()
+  const ApplEntry* atab;      // applicable rules of each neuron by spike count
+};
+
+// Per-neuron constants read together by the applicability scan.
+struct __align__(16) NeuronInfo {
+  int32_t off;                // first entry of the neuron in atab, or -1 (evaluate the rules)
+  uint32_t tl;                // T | L << 16 (see appl)
+  unsigned long long magic;   // ceil(2^shift / L): floor(v / L) = (v * magic) >> shift for v < 2^31
+  int32_t gain;               // largest increase of the neuron's column in one step
+  uint32_t shift;             // 32 + ceil(log2 L)
+  unsigned long long colkey;  // R[n]
+};
+
+// Applicable rules of a neuron for one spike count.
+struct __align__(16) ApplEntry {
+  uint32_t mask;              // bit k: rule first_rule[n] + k applies
+  uint32_t keep;              // mask without the rules that repeat an earlier applicable rule's row
+  unsigned long long hfirst;  // H[first applicable rule], 0 if none
 };
 
 // Rule r, chosen for a neuron whose applicable rules are `mask`, gives the
@@ -112,10 +132,8 @@ __host__ __device__ __forceinline__ bool rule_applies(int32_t x, int4 rp) {
   return ((x - rp.x) % rp.y) == 0;
 }
 
-// Applicable rules of neuron n holding x spikes, from the rules themselves:
-// bits 0-31 the mask (bit k = rule first_rule[n] + k), bits 32-63 the same
-// mask without the rules that repeat an earlier applicable rule's row.
-__device__ __forceinline__ uint64_t appl_rules(const DevSys& s, int n, int32_t x) {
+// Applicable rules of neuron n holding x spikes, from the rules themselves.
+static __device__ __noinline__ ApplEntry appl_rules(const DevSys& s, int n, int32_t x) {
   const int r0 = __ldg(s.first_rule + n), r1 = __ldg(s.first_rule + n + 1);
   uint32_t mask = 0;
   for (int r = r0; r < r1; ++r)
@@ -125,23 +143,57 @@ __device__ __forceinline__ uint64_t appl_rules(const DevSys& s, int n, int32_t x
     const int k = __ffs(b) - 1;
     if (__ldg(s.eqmask + r0 + k) & mask) keep &= ~(1u << k);
   }
-  return (uint64_t)mask | ((uint64_t)keep << 32);
+  ApplEntry e;
+  e.mask = mask;
+  e.keep = keep;
+  e.hfirst = mask ? __ldg(s.rowkey + r0 + __ffs(mask) - 1) : 0ull;
+  return e;
 }
 
 // appl_rules(s, n, x) by table.  Above T = 1 + the largest i or c of the
 // neuron's rules every threshold holds and a^i alone never matches, so the
-// masks repeat with period L = lcm of the rules' j >= 1: the table holds
-// x = 0 .. T + L - 1 and larger x fold onto T + (x - T) mod L.  Neurons whose
-// T + L is too large for a table (offset -1) evaluate their rules.
-__device__ __forceinline__ uint64_t appl(const DevSys& s, int n, int32_t x) {
-  const int2 mt = __ldg(s.amet + n);
-  if (mt.x >= 0 && x >= 0) {
-    const int T = mt.y & 0xFFFF, L = (int)((uint32_t)mt.y >> 16);
-    int k = x;
-    if (x >= T + L) k = T + ((L & (L - 1)) ? (x - T) % L : ((x - T) & (L - 1)));
-    return __ldg(s.atab + mt.x + k);
+// entries repeat with period L = lcm of the rules' j >= 1: the table holds
+// x = 0 .. T + L - 1 and larger x fold onto T + (x - T) mod L, the quotient
+// by multiply and shift (Granlund and Montgomery, PLDI 1994; exact here since
+// x - T < 2^31).  Neurons whose T + L is too large for a table evaluate
+// their rules.
+__device__ __forceinline__ ApplEntry appl_entry(const DevSys& s, const NeuronInfo& ni, int n, int32_t x) {
+  if (ni.off >= 0 && x >= 0) {
+    const uint32_t T = ni.tl & 0xFFFFu, L = ni.tl >> 16;
+    uint32_t k = (uint32_t)x;
+    if (k >= T + L) {
+      const uint32_t v = k - T;
+      const uint32_t q = (uint32_t)(((unsigned long long)v * ni.magic) >> ni.shift);
+      k = T + v - q * L;
+    }
+    const uint4 e = __ldg(reinterpret_cast<const uint4*>(s.atab + ni.off + k));
+    ApplEntry r;
+    r.mask = e.x;
+    r.keep = e.y;
+    r.hfirst = ((unsigned long long)e.w << 32) | e.z;
+    return r;
   }
   return appl_rules(s, n, x);
+}
+
+__device__ __forceinline__ NeuronInfo neuron_info(const DevSys& s, int n) {
+  const int4* p = reinterpret_cast<const int4*>(s.ninfo + n);
+  const int4 a = __ldg(p), b = __ldg(p + 1);
+  NeuronInfo ni;
+  ni.off = a.x;
+  ni.tl = (uint32_t)a.y;
+  ni.magic = ((unsigned long long)(uint32_t)a.w << 32) | (uint32_t)a.z;
+  ni.gain = b.x;
+  ni.shift = (uint32_t)b.y;
+  ni.colkey = ((unsigned long long)(uint32_t)b.w << 32) | (uint32_t)b.z;
+  return ni;
+}
+
+// Bits 0-31: applicable rules of neuron n with x spikes; bits 32-63: the same
+// without rules that repeat an earlier applicable rule's row.
+__device__ __forceinline__ uint64_t appl(const DevSys& s, int n, int32_t x) {
+  const ApplEntry e = appl_entry(s, neuron_info(s, n), n, x);
+  return (uint64_t)e.mask | ((uint64_t)e.keep << 32);
 }
 
 // Position of the d-th set bit (0-based) of mask.
@@ -257,6 +309,36 @@ __device__ __forceinline__ uint64_t fingerprint(const DevSys& s, const int32_t* 
   uint64_t h = 0;
   for (int n = lane; n < s.m; n += 32) h += col_hash(s, n, buf[n]);
   return mix64(warp_sum_u64(h));
+}
+
+// dst[0, m) = src[0, m), read through L2, the loads issued in groups of 8 so
+// that a group is in flight together (16-byte words when m % 4 == 0; both
+// rows then start 16-byte aligned).
+__device__ __forceinline__ void copy_row_cg(const int32_t* src, int32_t* dst, int m) {
+  if ((m & 3) == 0) {
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(dst);
+    const int n4 = m >> 2;
+    for (int j0 = 0; j0 < n4; j0 += 8) {
+      int4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < n4) v[u] = __ldcg(s4 + j0 + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < n4) d4[j0 + u] = v[u];
+    }
+    return;
+  }
+  for (int j0 = 0; j0 < m; j0 += 8) {
+    int32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (j0 + u < m) v[u] = __ldcg(src + j0 + u);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (j0 + u < m) dst[j0 + u] = v[u];
+  }
 }
 
 __device__ __forceinline__ uint32_t fp32_of(uint64_t h) {

@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
           const int64_t row = n_rows + (int64_t)rank;
           const int32_t* src = sc.staging + (size_t)o * m;
           int32_t* dst = bs->pool + (size_t)row * m;
-          for (int j = 0; j < m; ++j) dst[j] = __ldcg(src + j);
+          copy_row_cg(src, dst, m);
           *slot = hi | (uint32_t)row;
           if (rank + 1 == accept) {
             sc.st->capped = 1;

@@ -131,18 +131,19 @@ struct snp_system {
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_amet, d_atab;
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_ninfo, d_atab;
   std::vector<uint32_t> eqmask;
-  std::vector<int2> amet;                   // per neuron {offset into atab or -1, T | L << 16}
-  std::vector<unsigned long long> atab;     // applicable-rule masks by spike count
+  std::vector<snp::NeuronInfo> ninfo;       // per-neuron constants of the applicability scan
+  std::vector<snp::ApplEntry> atab;         // applicable rules by spike count
   // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
   DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash, d_red;
   int32_t Rp = 0, mp = 0, mt_rows = 0;
   uint64_t tc_cap = 0;  // candidates the tensor-core chunk buffers hold
   std::vector<unsigned long long> colkey, rowkey;
   // exploration state
-  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_psi, d_off, d_scan_tmp, d_st,
-      d_rec_parent, d_rec_index, d_tmp, d_prec;
+  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_off, d_scan_tmp, d_st,
+      d_rec_parent, d_rec_index, d_tmp,
+      d_psi, d_prec;
   int64_t pool_rows = 0;  // capacity in rows
   uint64_t nbuckets = 0;
   uint64_t q_cap = 0;     // staging capacity in rows
@@ -173,8 +174,8 @@ struct snp_system {
     s.colkey = d_colkey.as<unsigned long long>();
     s.rowkey = d_rowkey.as<unsigned long long>();
     s.eqmask = d_eqmask.as<uint32_t>();
-    s.amet = d_amet.as<int2>();
-    s.atab = d_atab.as<unsigned long long>();
+    s.ninfo = d_ninfo.as<snp::NeuronInfo>();
+    s.atab = d_atab.as<snp::ApplEntry>();
     return s;
   }
   snp::DevTable table() const { return snp::DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }

@@ -26,10 +26,44 @@ __device__ __forceinline__ void set_error(ChunkState* st, uint32_t bits) { atomi
 
 }  // namespace
 
-// Step (a) and Eq. psi for every frontier row, one lane per row: counts each
-// neuron's applicable rules, Psi = prod max(1, omega) (saturating); flags rows
-// whose children could leave int32 and gives Psi = 0 to rows not to be
-// expanded (max_expand).  With REC it also writes the row's ParentRec.
+// Step (a) for one configuration, neuron by neuron: Psi = prod max(1, omega)
+// (saturating; omega <= 32, so below 2^58 a product cannot overflow), whether
+// a child could leave int32, whether the row is past max_expand, and its
+// ParentRec (base-child hash, multi-choice neurons in neuron order).
+struct PsiAcc {
+  uint64_t prod = 1, hb = 0;
+  uint32_t nnt = 0;
+  bool ov = false, skip = false;
+
+  template <bool REC>
+  __device__ __forceinline__ void visit(const DevSys& s, int n, int32_t x, int32_t max_expand, ParentRec* rec) {
+    const NeuronInfo ni = neuron_info(s, n);
+    const ApplEntry e = appl_entry(s, ni, n, x);
+    const uint32_t cnt = __popc(e.mask);
+    if (cnt > 1) {
+      if (prod >> 58)
+        prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
+      else
+        prod *= cnt;
+    }
+    ov |= x > INT32_MAX - ni.gain;
+    skip |= max_expand >= 0 && x > max_expand;
+    if (REC) {
+      hb += (uint64_t)(uint32_t)x * ni.colkey + e.hfirst;
+      if (cnt > 1) {
+        const bool fits = nnt < (uint32_t)kRecNt && n < 65536 && e.mask < 65536u;
+        if (fits) rec->nt[nnt] = ((uint32_t)n << 16) | e.mask;
+        nnt = fits ? nnt + 1 : kRecFull;
+      }
+    }
+  }
+  __device__ __forceinline__ uint64_t psi() const { return skip ? 0ull : prod; }
+  __device__ __forceinline__ bool overflow() const { return ov && !skip; }
+};
+
+// Step (a) and Eq. psi for every frontier row, one lane per row, with the
+// rows' ParentRecs when rec is given; rows not to be expanded (max_expand)
+// get Psi = 0, rows whose children could leave int32 raise kErrOverflow.
 template <bool VEC, bool REC>
 __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand,
                                              uint64_t* psi, ParentRec* rec, ChunkState* st) {
@@ -37,9 +71,7 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int6
   bool over = false;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t* row = rows + (size_t)p * m;
-    uint64_t prod = 1, hb = 0;
-    uint32_t nnt = 0;
-    bool skip = false, ov = false;
+    PsiAcc acc;
     for (int n0 = 0; n0 < m; n0 += 4) {
       int x4[4];
       if (VEC) {
@@ -50,31 +82,15 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int6
         for (int u = 0; u < 4; ++u) x4[u] = (n0 + u < m) ? __ldg(row + n0 + u) : 0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int n = n0 + u;
-        if (n >= m) break;
-        const int32_t x = x4[u];
-        const uint32_t mask = (uint32_t)appl(s, n, x);
-        const uint32_t cnt = __popc(mask);
-        if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
-        ov |= x > INT32_MAX - __ldg(s.gain + n);
-        skip |= max_expand >= 0 && x > max_expand;
-        if (REC) {
-          hb += col_hash(s, n, x);
-          if (mask) hb += __ldg(s.rowkey + __ldg(s.first_rule + n) + __ffs(mask) - 1);
-          if (cnt > 1) {
-            if (nnt < (uint32_t)kRecNt && n < 65536 && mask < 65536u) rec[p].nt[nnt] = ((uint32_t)n << 16) | mask;
-            nnt = (nnt < (uint32_t)kRecNt && n < 65536 && mask < 65536u) ? nnt + 1 : kRecFull;
-          }
-        }
-      }
+      for (int u = 0; u < 4; ++u)
+        if (n0 + u < m) acc.visit<REC>(s, n0 + u, x4[u], max_expand, REC ? rec + p : nullptr);
     }
-    psi[p] = skip ? 0ull : prod;
+    psi[p] = acc.psi();
     if (REC) {
-      rec[p].hbase = hb;
-      rec[p].nnt = nnt;
+      rec[p].hbase = acc.hb;
+      rec[p].nnt = acc.nnt;
     }
-    over |= ov && !skip;
+    over |= acc.overflow();
   }
   if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
 }
@@ -134,45 +150,78 @@ __device__ __forceinline__ int64_t find_parent(const uint64_t* off, int64_t P, u
   return lo;
 }
 
-// Accepts first occurrences of rank < remaining (discovery order), rejects the
-// rest.  One warp per bitmap word, one lane per set bit.
+// One first occurrence: accepted (rank < remaining: copied to its pool row in
+// rank order, its slot pointed at the row) or rejected (its slot becomes a
+// tombstone).
+__device__ __forceinline__ void commit_one(const CommitArgs& a, uint32_t lid, uint64_t rank) {
+  const int m = a.sys.m;
+  const uint32_t s = a.srow[lid];
+  unsigned long long* slot = a.table.slots + a.slot_of[s];
+  const unsigned long long hi = (*slot) & 0xFFFFFFFF00000000ull;
+  if (rank >= a.remaining) {
+    *slot = hi | kRowTomb;
+    return;
+  }
+  const int64_t row = a.row_base + (int64_t)rank;
+  const int32_t* src = a.staging + (size_t)s * m;
+  int32_t* dst = a.pool + (size_t)row * m;
+  copy_row_cg(src, dst, m);
+  *slot = hi | (uint32_t)row;
+  if (rank + 1 == a.remaining) {
+    a.st->capped = 1;
+    a.st->last_lid = lid;
+  }
+  if (a.rec_parent) {
+    const uint64_t g = a.g0 + lid;
+    const int64_t p = find_parent(a.off, a.P, g);
+    a.rec_parent[row] = a.parent_base + p;
+    a.rec_index[row] = g - __ldg(a.off + p);
+  }
+}
+
+// Commits every first occurrence of the chunk, one lane per rank: a warp
+// takes ranks r0 .. r0 + 31 (st->n_alloc of them in all), finds the bitmap
+// word holding r0 in the exclusive prefix sums wbase, and each lane then
+// finds its own word among the next 32 and its set bit within the word.
 __global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
   const int lane = threadIdx.x & 31;
-  const int m = a.sys.m;
-  const bool vec = (m % 4) == 0;
-  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
-  for (uint64_t wd = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); wd < a.nwords; wd += nw) {
-    const uint32_t word = a.bits[wd];
-    if (!((word >> lane) & 1u)) continue;
-    const uint32_t lid = (uint32_t)wd * 32u + (uint32_t)lane;
-    const uint64_t rank = (uint64_t)a.wbase[wd] + __popc(word & ((1u << lane) - 1u));
-    const uint32_t s = a.srow[lid];
-    unsigned long long* slot = a.table.slots + a.slot_of[s];
-    const unsigned long long hi = (*slot) & 0xFFFFFFFF00000000ull;
-    if (rank < a.remaining) {
-      const int64_t row = a.row_base + (int64_t)rank;
-      const int32_t* src = a.staging + (size_t)s * m;
-      int32_t* dst = a.pool + (size_t)row * m;
-      if (vec) {
-        const int4* s4 = reinterpret_cast<const int4*>(src);
-        int4* d4 = reinterpret_cast<int4*>(dst);
-        for (int j = 0; j < (m >> 2); ++j) d4[j] = __ldcg(s4 + j);
-      } else {
-        for (int j = 0; j < m; ++j) dst[j] = __ldcg(src + j);
+  const uint32_t total = *reinterpret_cast<volatile const unsigned int*>(&a.st->n_alloc);
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t r0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < total;
+       r0 += nwarps * 32) {
+    // largest w with wbase[w] <= r0 (the word holding rank r0)
+    int64_t lo = 0, hi = a.nwords;
+    while (hi - lo > 1) {
+      const int64_t step = (hi - lo + 31) / 32;
+      const int64_t idx = lo + (int64_t)lane * step;
+      const bool ok = idx < hi && a.wbase[idx] <= r0;
+      const uint32_t bal = __ballot_sync(0xffffffffu, ok);
+      lo += (int64_t)(31 - __clz(bal)) * step;
+      hi = min(lo + step, hi);
+    }
+    const uint64_t r = r0 + lane;
+    const int64_t wj = lo + 1 + lane;
+    const uint64_t nb = wj < (int64_t)a.nwords ? a.wbase[wj] : ~0ull;  // first rank after word lo + lane
+    int k = 0;  // words lo .. lo + k - 1 end at or before r
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const uint64_t v = __shfl_sync(0xffffffffu, nb, k + step - 1);
+      if (v <= r) k += step;
+    }
+    const uint64_t nb31 = __shfl_sync(0xffffffffu, nb, 31);
+    if (r < total) {
+      uint64_t w = (uint64_t)lo + k;
+      if (nb31 <= r) {  // beyond the window: a run of empty words
+        int64_t l2 = lo + 32, h2 = a.nwords;
+        while (h2 - l2 > 1) {
+          const int64_t mid = l2 + (h2 - l2) / 2;
+          if (a.wbase[mid] <= r) l2 = mid; else h2 = mid;
+        }
+        w = (uint64_t)l2;
       }
-      *slot = hi | (uint32_t)row;
-      if (rank + 1 == a.remaining) {
-        a.st->capped = 1;
-        a.st->last_lid = lid;
-      }
-      if (a.rec_parent) {
-        const uint64_t g = a.g0 + lid;
-        const int64_t p = find_parent(a.off, a.P, g);
-        a.rec_parent[row] = a.parent_base + p;
-        a.rec_index[row] = g - __ldg(a.off + p);
-      }
-    } else {
-      *slot = hi | kRowTomb;
+      const uint32_t word = a.bits[w];
+      const uint32_t q = (uint32_t)(r - a.wbase[w]);
+      commit_one(a, (uint32_t)w * 32u + __fns(word, 0, (int)q + 1), r);
     }
   }
 }

@@ -249,6 +249,18 @@ def test_overflow_is_reported(gpu):
     with pytest.raises(gpu.SnpError) as ei:
         s.step(system.c0)
     assert ei.value.code == gpu.SNP_E_OVERFLOW
+    # Counts grow by 4 a step (gain 5): the frontier of depth 3 holds 2^31 - 5,
+    # whose children could pass 2^31 - 1; depth 2 is still fine.
+    m = 2 ** 31 - 1
+    system = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 5], [[1], [0]], [m - 12, 1])
+    s = gpu.System(system)
+    s.explore(2)
+    assert s.reachable().tolist() == [[m - 12, 1], [m - 8, 5], [m - 4, 9]]
+    with pytest.raises(gpu.SnpError) as ei:
+        s.explore(3)
+    assert ei.value.code == gpu.SNP_E_OVERFLOW
+    s.explore(2, cap=1)
+    assert s.count() == 3
 
 
 def test_state_and_buffer_errors(gpu):
@@ -358,3 +370,51 @@ def test_rules_with_identical_rows(gpu):
             s = gpu.System(system)
             s.explore(6, cap=40, budget=400, transition=transition)
             assert_same(s, oracle.Oracle(system).explore(6, cap=40, budget=400))
+
+
+def large_count_system():
+    """Neurons whose rule sets give every kind of applicability lookup: period
+    L = 6 (folded by multiply and shift), L = 8, L = lcm(5, 7, 3) = 105 and a
+    threshold of 300 (both evaluated from the rules), a threshold of 200 with
+    L = 3, and two rules with identical rows."""
+    rules = [  # (neuron, i, j, c, p)
+        (0, 1, 2, 1, 1), (0, 2, 3, 2, 1),
+        (1, 3, 4, 1, 2), (1, 1, 0, 1, 1), (1, 5, 8, 3, 1),
+        (2, 2, 5, 1, 1), (2, 3, 7, 2, 2), (2, 1, 3, 1, 1),
+        (3, 200, 1, 200, 1), (3, 1, 3, 1, 1),
+        (4, 300, 2, 1, 1),
+        (5, 1, 1, 1, 1), (5, 1, 1, 1, 1),
+    ]
+    rn, ri, rj, rc, rp = (list(x) for x in zip(*rules))
+    targets = [[1, 2], [2, 3], [3, 4], [4, 5], [5, 0], [0, 1]]
+    return snp_synth.make_system(6, rn, ri, rj, rc, rp, targets, [0] * 6, name="large-count")
+
+
+def test_applicability_at_large_spike_counts(gpu):
+    system = large_count_system()
+    s = gpu.System(system)
+    o = oracle.Oracle(system)
+    rng = np.random.default_rng(11)
+    for k in range(300):
+        band = rng.integers(0, 3, size=6)
+        C = np.where(band == 0, rng.integers(0, 20, size=6),
+                     np.where(band == 1, rng.integers(180, 330, size=6), rng.integers(10**6, 10**7, size=6)))
+        C = C.astype(np.int32)
+        kids, psi = s.step(C)
+        assert psi == o.psi(C), C
+        assert (kids == o.step(C)).all(), C
+
+
+def test_explore_from_large_spike_counts(gpu):
+    system = large_count_system()
+    rng = np.random.default_rng(12)
+    for k in range(4):
+        system.c0[:] = rng.integers(10**5, 10**6, size=6).astype(np.int32)
+        if k == 1:
+            system.c0[3] = 250
+            system.c0[4] = 301
+        s = gpu.System(system)
+        s.explore(4, cap=3000, budget=40000)
+        e = oracle.Oracle(system).explore(4, cap=3000, budget=40000)
+        assert (s.reachable() == e.configs).all()
+        assert [x.examined for x in s.depth_stats()] == [x.examined for x in e.depths]
