@@ -101,8 +101,9 @@ typedef struct {
  *  stream            cudaStream_t to run on, or NULL for the default stream.
  *  kernel_timing     1: time the expand kernel of every pass with CUDA events
  *                    on `stream` (snp_depth_info.expand_ms).
- *  tile              candidates a warp builds together (batch engine); <= 0:
- *                    automatic.
+ *  tile              rows of a warp's candidate tile (batch engine): the most
+ *                    candidates a warp builds together; <= 0: the largest
+ *                    that shared memory holds.
  *  warps             warps per CTA of the batch engine (4 or 8); <= 0: automatic.
  * Candidate order ("canonical order"): parents in discovery order; for each,
  * its valid spiking vectors in mixed-radix order with neuron 0's choice most

@@ -71,7 +71,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   const uint64_t nslots = std::max<uint64_t>(pow2_at_least(want_slots), kBucket);
   // tile rows and warps
   int ts = 0;
-  int B = plan.tile > 0 ? plan.tile : (int)std::min<size_t>(32, std::max<size_t>(2, (8u << 10) / (4u * (((m_max + 3) & ~3) + 4))));
+  int B = plan.tile > 0 ? plan.tile : 32;  // shrunk below to what the shared memory holds
   const int warps = plan.warps == 4 ? 4 : 8;
   size_t warp_smem = expand_smem_bytes(m_max, B, &ts);
   while (B > 1 && warp_smem * warps > (200u << 10)) warp_smem = expand_smem_bytes(m_max, --B, &ts);

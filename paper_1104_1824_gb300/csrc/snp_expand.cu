@@ -299,10 +299,12 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
 
 // Step (d) for one row per lane (lanes with todo set): passes until every
 // row is resolved; a lane never waits inside a pass, so owners in this warp
-// publish before anyone looks again.
+// publish before anyone looks again.  KIND separates the out-of-line copies
+// of the single-system kernel (0) and the batch kernel (1), whose register
+// budgets differ.
 template <bool VEC>
-__device__ __noinline__ void resolve_warp(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
-                                             bool todo) {
+__device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
+                                                  bool todo) {
   for (int pass = 0;; ++pass) {
     if (todo && resolve_lane<VEC>(a, row, key, lid)) todo = false;
     if (__all_sync(0xffffffffu, !todo)) break;
@@ -313,6 +315,21 @@ __device__ __noinline__ void resolve_warp(const ClaimArgs& a, const int32_t* row
     __nanosleep(32);
   }
   __syncwarp();
+}
+
+template <bool VEC>
+__device__ __noinline__ void resolve_warp_call(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
+                                               bool todo) {
+  resolve_warp_body<VEC>(a, row, key, lid, todo);
+}
+
+template <bool VEC, int KIND>
+__device__ __forceinline__ void resolve_warp(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
+                                             bool todo) {
+  if constexpr (KIND == 0)
+    resolve_warp_call<VEC>(a, row, key, lid, todo);
+  else
+    resolve_warp_body<VEC>(a, row, key, lid, todo);
 }
 
 // Mixed-radix digit of a neuron with `radix` choices; q moves to the next
@@ -459,17 +476,17 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
 }
 
 // Resolves the queued rows of crossing batches (building them first).
-template <bool VEC>
+template <bool VEC, int KIND>
 __device__ __forceinline__ void flush_queue(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
   const bool mine = lane < fill;
   if (mine && w.dpc[lane] >= 0) flat_build<VEC>(a, w.dpc[lane], w.dt[lane], w.tile + lane * ts);
   __syncwarp();
-  resolve_warp<VEC>(a, w.tile + lane * ts, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine);
+  resolve_warp<VEC, KIND>(a, w.tile + lane * ts, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine);
 }
 
 // Block mode for parent p from candidate a.g0 + l to the end of the parent or
 // of the task; returns the new l.
-template <bool VEC>
+template <bool VEC, int KIND>
 __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w, int B, int ts, int64_t p,
                                               uint64_t p_lo, uint64_t p_hi, uint64_t l, uint64_t lb, int lane) {
   const DevSys& s = a.sys;
@@ -506,7 +523,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   for (;;) {
     const uint64_t c = gb + lane;
     const bool todo = lane < RL && c >= g && c < gend && !redk && w.hdr[kNred] == 0;
-    resolve_warp<VEC>(a, row, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo);
+    resolve_warp<VEC, KIND>(a, row, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo);
     gb += (uint64_t)RL;
     if (gb >= gend) break;
     // next block: the high digits move on by one (odometer, least significant first)
@@ -545,7 +562,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
 // Steps (b)-(d) for the tasks task0, task0 + tstride, ... of chunk a (a task
 // is a run of a.run consecutive candidates), by one warp: block mode while
 // the parent has 32 or more candidates left, else crossing batches.
-template <bool VEC>
+template <bool VEC, int KIND>
 __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, ExpandSmem& w, uint64_t task0,
                                             uint64_t tstride, int lane) {
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
@@ -562,11 +579,11 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       const uint64_t g = a.g0 + l;
       if (done || p_hi - g >= 32) {
         if (fill > 0) {  // the tile is about to be reused, or the task ends
-          flush_queue<VEC>(a, w, ts, fill, lane);
+          flush_queue<VEC, KIND>(a, w, ts, fill, lane);
           fill = 0;
         }
         if (done) break;
-        l = block_run<VEC>(a, w, B, ts, p, p_lo, p_hi, l, lb, lane);
+        l = block_run<VEC, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, lane);
         const uint64_t gn = a.g0 + l;
         if (l < lb) {
           do {
@@ -583,7 +600,7 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       const int nb = flat_decode<VEC>(a, g, (int)min((uint64_t)B, lb - l), p, p_lo, lane, f, keep);
       const uint32_t kept = __ballot_sync(0xffffffffu, keep);
       if (fill + __popc(kept) > B) {
-        flush_queue<VEC>(a, w, ts, fill, lane);
+        flush_queue<VEC, KIND>(a, w, ts, fill, lane);
         fill = 0;
       }
       if (keep) {
@@ -622,7 +639,7 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   ExpandSmem w = expand_smem(smem_raw + (size_t)wib * expand_warp_bytes(a.sys.m, B, ts), a.sys.m, B, ts);
-  expand_warp<VEC>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
+  expand_warp<VEC, 0>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
 }
 
 // Step (d) for rows already built in global memory (the tensor-core form):
@@ -853,9 +870,9 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       a.prec = nullptr;
       a.st = sc.st;
       if ((m & 3) == 0)
-        expand_warp<true>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+        expand_warp<true, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
       else
-        expand_warp<false>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+        expand_warp<false, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
       __threadfence();
       __syncthreads();
       // first-occurrence marks

@@ -225,7 +225,7 @@ int tick(snp_server* S) {
   const int nsm = sm_count(S->device);
   const int warps = 8;
   int ts = 0;
-  int B = (int)std::min<size_t>(16, std::max<size_t>(2, (8u << 10) / (4u * (((m_max + 3) & ~3) + 4))));
+  int B = 32;  // shrunk below to what the shared memory holds
   size_t warp_smem = expand_smem_bytes(m_max, B, &ts);
   while (B > 1 && warp_smem * warps > (200u << 10)) warp_smem = expand_smem_bytes(m_max, --B, &ts);
   const int blocks = std::max(1, std::min(nsm, n));
