@@ -274,6 +274,21 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       h->atab.push_back(ae);
     }
   }
+  // Direct table of small spike counts (see DevSys::dmask).
+  h->dmask.assign((size_t)m * snp::kDirect, 0u);
+  h->dhx.assign((size_t)m * snp::kDirect, 0ull);
+  h->gain_small = 1;
+  for (int n = 0; n < m; ++n) {
+    if (h->gain[n] > INT32_MAX - snp::kDirect) h->gain_small = 0;
+    for (int32_t x = 0; x < snp::kDirect; ++x) {
+      uint32_t mask = 0;
+      for (int r = h->first_rule[n]; r < h->first_rule[n + 1]; ++r)
+        if (rule_applies(x, h->rule[r])) mask |= 1u << (r - h->first_rule[n]);
+      h->dmask[(size_t)n * snp::kDirect + x] = mask;
+      h->dhx[(size_t)n * snp::kDirect + x] = (unsigned long long)x * h->colkey[n] +
+                                             (mask ? h->rowkey[h->first_rule[n] + __builtin_ctz(mask)] : 0ull);
+    }
+  }
   int rc = SNP_OK;
   auto up = [&](DevBuf& b, const void* src, size_t bytes) -> int {
     if ((rc = b.reserve(std::max<size_t>(bytes, 16))) != SNP_OK) return rc;
@@ -289,6 +304,8 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_eqmask, h->eqmask.data(), sizeof(uint32_t) * (R + 1))) ||
       (rc = up(h->d_ninfo, h->ninfo.data(), sizeof(snp::NeuronInfo) * m)) ||
       (rc = up(h->d_atab, h->atab.data(), sizeof(snp::ApplEntry) * std::max<size_t>(h->atab.size(), 1))) ||
+      (rc = up(h->d_dmask, h->dmask.data(), sizeof(uint32_t) * h->dmask.size())) ||
+      (rc = up(h->d_dhx, h->dhx.data(), sizeof(unsigned long long) * h->dhx.size())) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;
     return rc;

@@ -42,7 +42,15 @@ struct DevSys {
   const uint32_t* eqmask;     // [R] positions of earlier rules of the same neuron with the same row of M_Pi
   const NeuronInfo* ninfo;    // [m] per-neuron constants: see appl()
   const ApplEntry* atab;      // applicable rules of each neuron by spike count
+  // Direct table for spike counts below kDirect, [m][kDirect]: the applicable
+  // mask, and x * R[n] + H[first applicable rule] (the neuron's share of the
+  // hash of the base child).  gain_small: every column's gain is at most
+  // INT32_MAX - kDirect, so counts below kDirect cannot overflow a child.
+  const uint32_t* dmask;
+  const unsigned long long* dhx;
+  int32_t gain_small;
 };
+constexpr int kDirect = 64;
 
 // Per-neuron constants read together by the applicability scan.
 struct __align__(16) NeuronInfo {

@@ -826,9 +826,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       bool skip = false, ov = false;
       for (int n = 0; n < m; ++n) {
         const int32_t x = row[n];
-        const uint32_t cnt = __popc((uint32_t)appl(S, n, x));
+        const bool small = (uint32_t)x < (uint32_t)kDirect;
+        const uint32_t cnt = __popc(small ? __ldg(S.dmask + (size_t)n * kDirect + x) : (uint32_t)appl(S, n, x));
         if (cnt > 1) prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
-        ov |= x > INT32_MAX - __ldg(S.gain + n);
+        if (!small || !S.gain_small) ov |= x > INT32_MAX - __ldg(S.gain + n);
         skip |= max_expand >= 0 && x > max_expand;
       }
       sc.off[p] = skip ? 0ull : prod;

@@ -131,10 +131,13 @@ struct snp_system {
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_ninfo, d_atab;
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_ninfo, d_atab, d_dmask, d_dhx;
   std::vector<uint32_t> eqmask;
   std::vector<snp::NeuronInfo> ninfo;       // per-neuron constants of the applicability scan
   std::vector<snp::ApplEntry> atab;         // applicable rules by spike count
+  std::vector<uint32_t> dmask;              // [m][kDirect] applicable masks of small counts
+  std::vector<unsigned long long> dhx;      // [m][kDirect] x * R[n] + H[first applicable rule]
+  int32_t gain_small = 0;
   // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
   DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash, d_red;
   int32_t Rp = 0, mp = 0, mt_rows = 0;
@@ -176,6 +179,9 @@ struct snp_system {
     s.eqmask = d_eqmask.as<uint32_t>();
     s.ninfo = d_ninfo.as<snp::NeuronInfo>();
     s.atab = d_atab.as<snp::ApplEntry>();
+    s.dmask = d_dmask.as<uint32_t>();
+    s.dhx = d_dhx.as<unsigned long long>();
+    s.gain_small = gain_small;
     return s;
   }
   snp::DevTable table() const { return snp::DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }

@@ -37,22 +37,33 @@ struct PsiAcc {
 
   template <bool REC>
   __device__ __forceinline__ void visit(const DevSys& s, int n, int32_t x, int32_t max_expand, ParentRec* rec) {
-    const NeuronInfo ni = neuron_info(s, n);
-    const ApplEntry e = appl_entry(s, ni, n, x);
-    const uint32_t cnt = __popc(e.mask);
+    uint32_t mask;
+    uint64_t hx = 0;
+    if ((uint32_t)x < (uint32_t)kDirect) {  // small count: one entry of the direct table
+      const size_t k = (size_t)n * kDirect + (uint32_t)x;
+      mask = __ldg(s.dmask + k);
+      if (REC) hx = __ldg(s.dhx + k);
+      if (!s.gain_small) ov |= x > INT32_MAX - __ldg(s.gain + n);
+    } else {
+      const NeuronInfo ni = neuron_info(s, n);
+      const ApplEntry e = appl_entry(s, ni, n, x);
+      mask = e.mask;
+      if (REC) hx = (uint64_t)(uint32_t)x * ni.colkey + e.hfirst;
+      ov |= x > INT32_MAX - ni.gain;
+    }
+    const uint32_t cnt = __popc(mask);
     if (cnt > 1) {
       if (prod >> 58)
         prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
       else
         prod *= cnt;
     }
-    ov |= x > INT32_MAX - ni.gain;
     skip |= max_expand >= 0 && x > max_expand;
     if (REC) {
-      hb += (uint64_t)(uint32_t)x * ni.colkey + e.hfirst;
+      hb += hx;
       if (cnt > 1) {
-        const bool fits = nnt < (uint32_t)kRecNt && n < 65536 && e.mask < 65536u;
-        if (fits) rec->nt[nnt] = ((uint32_t)n << 16) | e.mask;
+        const bool fits = nnt < (uint32_t)kRecNt && n < 65536 && mask < 65536u;
+        if (fits) rec->nt[nnt] = ((uint32_t)n << 16) | mask;
         nnt = fits ? nnt + 1 : kRecFull;
       }
     }
