@@ -274,6 +274,25 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       h->atab.push_back(ae);
     }
   }
+  // Rows of M_Pi on their neuron's support (see DevSys::rdesc): rules of one
+  // neuron differ only there, so swapping one for another is one pass.
+  h->rdesc.assign(R, make_int4(0, 0, 0, 0));
+  h->scol.clear();
+  h->rval.clear();
+  for (int n = 0; n < m; ++n) {
+    const int r0 = h->first_rule[n], r1 = h->first_rule[n + 1];
+    std::vector<int32_t> sup;
+    for (int r = r0; r < r1; ++r)
+      for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e) sup.push_back(h->csr[e].x);
+    std::sort(sup.begin(), sup.end());
+    sup.erase(std::unique(sup.begin(), sup.end()), sup.end());
+    const int off = (int)h->scol.size(), len = (int)sup.size();
+    h->scol.insert(h->scol.end(), sup.begin(), sup.end());
+    for (int r = r0; r < r1; ++r) {
+      h->rdesc[r] = make_int4(off, len, (int)h->rval.size(), n);
+      for (int i = 0; i < len; ++i) h->rval.push_back(h->M[(size_t)r * m + sup[i]]);
+    }
+  }
   // Direct table of small spike counts (see DevSys::dmask).
   h->dmask.assign((size_t)m * snp::kDirect, 0u);
   h->dhx.assign((size_t)m * snp::kDirect, 0ull);
@@ -305,6 +324,9 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_ninfo, h->ninfo.data(), sizeof(snp::NeuronInfo) * m)) ||
       (rc = up(h->d_atab, h->atab.data(), sizeof(snp::ApplEntry) * std::max<size_t>(h->atab.size(), 1))) ||
       (rc = up(h->d_dmask, h->dmask.data(), sizeof(uint32_t) * h->dmask.size())) ||
+      (rc = up(h->d_rdesc, h->rdesc.data(), sizeof(int4) * std::max(R, 1))) ||
+      (rc = up(h->d_scol, h->scol.data(), sizeof(int32_t) * std::max<size_t>(h->scol.size(), 1))) ||
+      (rc = up(h->d_rval, h->rval.data(), sizeof(int32_t) * std::max<size_t>(h->rval.size(), 1))) ||
       (rc = up(h->d_dhx, h->dhx.data(), sizeof(unsigned long long) * h->dhx.size())) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;

@@ -49,6 +49,12 @@ struct DevSys {
   const uint32_t* dmask;
   const unsigned long long* dhx;
   int32_t gain_small;
+  // Rows of M_Pi on their neuron's support: the columns any rule of the neuron
+  // touches (its own and its synapse targets).  Rule r: {offset of the support
+  // in scol, its length, offset of r's values in rval, neuron}.
+  const int4* rdesc;
+  const int32_t* scol;
+  const int32_t* rval;
 };
 constexpr int kDirect = 64;
 
@@ -140,21 +146,25 @@ __host__ __device__ __forceinline__ bool rule_applies(int32_t x, int4 rp) {
   return ((x - rp.x) % rp.y) == 0;
 }
 
-// Applicable rules of neuron n holding x spikes, from the rules themselves.
-static __device__ __noinline__ ApplEntry appl_rules(const DevSys& s, int n, int32_t x) {
-  const int r0 = __ldg(s.first_rule + n), r1 = __ldg(s.first_rule + n + 1);
+// Applicable rules of neuron n holding x spikes, from the rules themselves
+// (out of line, it is the rare path: it takes the four arrays it reads rather
+// than the whole system).
+static __device__ __noinline__ ApplEntry appl_rules(const int32_t* first_rule, const int4* rule,
+                                                   const uint32_t* eqmask, const unsigned long long* rowkey, int n,
+                                                   int32_t x) {
+  const int r0 = __ldg(first_rule + n), r1 = __ldg(first_rule + n + 1);
   uint32_t mask = 0;
   for (int r = r0; r < r1; ++r)
-    if (rule_applies(x, __ldg(s.rule + r))) mask |= 1u << (r - r0);
+    if (rule_applies(x, __ldg(rule + r))) mask |= 1u << (r - r0);
   uint32_t keep = mask;
   for (uint32_t b = mask; b; b &= b - 1) {
     const int k = __ffs(b) - 1;
-    if (__ldg(s.eqmask + r0 + k) & mask) keep &= ~(1u << k);
+    if (__ldg(eqmask + r0 + k) & mask) keep &= ~(1u << k);
   }
   ApplEntry e;
   e.mask = mask;
   e.keep = keep;
-  e.hfirst = mask ? __ldg(s.rowkey + r0 + __ffs(mask) - 1) : 0ull;
+  e.hfirst = mask ? __ldg(rowkey + r0 + __ffs(mask) - 1) : 0ull;
   return e;
 }
 
@@ -181,7 +191,7 @@ __device__ __forceinline__ ApplEntry appl_entry(const DevSys& s, const NeuronInf
     r.hfirst = ((unsigned long long)e.w << 32) | e.z;
     return r;
   }
-  return appl_rules(s, n, x);
+  return appl_rules(s.first_rule, s.rule, s.eqmask, s.rowkey, n, x);
 }
 
 __device__ __forceinline__ NeuronInfo neuron_info(const DevSys& s, int n) {

@@ -76,6 +76,44 @@ __device__ __forceinline__ void add_row_private(const DevSys& s, int32_t* row, i
   }
 }
 
+// row += M[rn] - M[ro] for two rules of one neuron (the row is private to
+// the calling lane): one pass over the neuron's support.
+__device__ __forceinline__ void swap_rule_private(const DevSys& s, int32_t* row, int ro, int rn) {
+  const int4 dn = __ldg(s.rdesc + rn);
+  const int32_t* vn = s.rval + dn.z;
+  const int32_t* vo = s.rval + __ldg(&s.rdesc[ro].z);
+  const int32_t* col = s.scol + dn.x;
+  for (int i = 0; i < dn.y; ++i) row[__ldg(col + i)] += __ldg(vn + i) - __ldg(vo + i);
+}
+
+// row += M[r] (the row is private to the calling lane).
+__device__ __forceinline__ void add_rule_private(const DevSys& s, int32_t* row, int r) {
+  const int4 dr = __ldg(s.rdesc + r);
+  const int32_t* v = s.rval + dr.z;
+  const int32_t* col = s.scol + dr.x;
+  for (int i = 0; i < dr.y; ++i) row[__ldg(col + i)] += __ldg(v + i);
+}
+
+// The batch kernel runs at its register limit: it keeps the CSR walk, which
+// needs fewer live values.
+template <int KIND>
+__device__ __forceinline__ void swap_rule(const DevSys& s, int32_t* row, int ro, int rn) {
+  if constexpr (KIND == 0) {
+    swap_rule_private(s, row, ro, rn);
+  } else {
+    add_row_private(s, row, ro, -1);
+    add_row_private(s, row, rn, 1);
+  }
+}
+
+template <int KIND>
+__device__ __forceinline__ void add_rule(const DevSys& s, int32_t* row, int r) {
+  if constexpr (KIND == 0)
+    add_rule_private(s, row, r);
+  else
+    add_row_private(s, row, r, 1);
+}
+
 __device__ __forceinline__ void add_row_shared(const DevSys& s, int32_t* row, int r, int sign) {
   const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
   for (int e = e0; e < e1; ++e) {
@@ -442,7 +480,7 @@ __device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int n
 
 // Step (c) for a candidate of a crossing batch: C' = C + the chosen rules'
 // rows, built in a tile row (one lane).
-template <bool VEC>
+template <bool VEC, int KIND>
 __device__ __forceinline__ void flat_build(const ClaimArgs& a, int64_t pc, uint64_t t, int32_t* trow) {
   const DevSys& s = a.sys;
   const int32_t* prow = a.parents + (size_t)pc * s.m;
@@ -452,7 +490,7 @@ __device__ __forceinline__ void flat_build(const ClaimArgs& a, int64_t pc, uint6
     const uint32_t mask = (uint32_t)appl(s, n, x);
     if (!mask) return;
     const int kb = nth_set_bit(mask, (int)next_digit(q, __popc(mask)));
-    add_row_private(s, trow, __ldg(s.first_rule + n) + kb, 1);
+    add_rule<KIND>(s, trow, __ldg(s.first_rule + n) + kb);
   });
 }
 
@@ -479,7 +517,7 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
 template <bool VEC, int KIND>
 __device__ __forceinline__ void flush_queue(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
   const bool mine = lane < fill;
-  if (mine && w.dpc[lane] >= 0) flat_build<VEC>(a, w.dpc[lane], w.dt[lane], w.tile + lane * ts);
+  if (mine && w.dpc[lane] >= 0) flat_build<VEC, KIND>(a, w.dpc[lane], w.dt[lane], w.tile + lane * ts);
   __syncwarp();
   resolve_warp<VEC, KIND>(a, w.tile + lane * ts, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine);
 }
@@ -513,8 +551,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
       q /= radix;
       if (d == 0) continue;
       const int r0 = rule_of(s, w, n, 0), rd = rule_of(s, w, n, (int)d);
-      add_row_private(s, row, r0, -1);
-      add_row_private(s, row, rd, 1);
+      swap_rule<KIND>(s, row, r0, rd);
       hk += __ldg(s.rowkey + rd) - __ldg(s.rowkey + r0);
       redk |= redundant_choice(s, mask, rd);
     }
@@ -551,8 +588,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
       const int nc = w.hdr[kNchg];
       for (int j = 0; j < nc; ++j) {
         const int2 rr = w.chg[j];
-        add_row_private(s, row, rr.x, -1);
-        add_row_private(s, row, rr.y, 1);
+        swap_rule<KIND>(s, row, rr.x, rr.y);
       }
     }
   }

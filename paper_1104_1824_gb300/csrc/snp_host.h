@@ -131,13 +131,16 @@ struct snp_system {
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
-  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_ninfo, d_atab, d_dmask, d_dhx;
+  DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_ninfo, d_atab, d_dmask, d_dhx, d_rdesc,
+      d_scol, d_rval;
   std::vector<uint32_t> eqmask;
   std::vector<snp::NeuronInfo> ninfo;       // per-neuron constants of the applicability scan
   std::vector<snp::ApplEntry> atab;         // applicable rules by spike count
   std::vector<uint32_t> dmask;              // [m][kDirect] applicable masks of small counts
   std::vector<unsigned long long> dhx;      // [m][kDirect] x * R[n] + H[first applicable rule]
   int32_t gain_small = 0;
+  std::vector<int4> rdesc;                  // per rule: support offset, length, value offset, neuron
+  std::vector<int32_t> scol, rval;          // neuron supports; rule values on them
   // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
   DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash, d_red;
   int32_t Rp = 0, mp = 0, mt_rows = 0;
@@ -182,6 +185,9 @@ struct snp_system {
     s.dmask = d_dmask.as<uint32_t>();
     s.dhx = d_dhx.as<unsigned long long>();
     s.gain_small = gain_small;
+    s.rdesc = d_rdesc.as<int4>();
+    s.scol = d_scol.as<int32_t>();
+    s.rval = d_rval.as<int32_t>();
     return s;
   }
   snp::DevTable table() const { return snp::DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }
