@@ -526,12 +526,16 @@ __device__ __forceinline__ void flush_queue(const ClaimArgs& a, ExpandSmem& w, i
 // of the task; returns the new l.
 template <bool VEC, int KIND>
 __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w, int B, int ts, int64_t p,
-                                              uint64_t p_lo, uint64_t p_hi, uint64_t l, uint64_t lb, int lane) {
+                                              uint64_t p_lo, uint64_t p_hi, uint64_t l, uint64_t lb,
+                                              int64_t& cached_p, uint64_t& after, int lane) {
   const DevSys& s = a.sys;
   const int m = s.m;
   const uint64_t g = a.g0 + l;
   const uint64_t gend = min(p_hi, a.g0 + lb);
-  const uint64_t after = parent_state(s, a.parents + (size_t)p * m, w, B, lane);
+  if (p != cached_p) {  // the warp's shared memory still holds the state of cached_p
+    after = parent_state(s, a.parents + (size_t)p * m, w, B, lane);
+    cached_p = p;
+  }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
   uint64_t b = (g - p_lo) / (uint64_t)RL;
   decode_full(s, w, b * (uint64_t)RL, after, lane);
@@ -602,10 +606,23 @@ template <bool VEC, int KIND>
 __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, ExpandSmem& w, uint64_t task0,
                                             uint64_t tstride, int lane) {
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
+  int64_t p = -1;         // parent of the previous task's last candidate
+  int64_t cached_p = -1;  // parent whose state the warp's shared memory holds
+  uint64_t after = 0;     // its per-lane place values
   for (uint64_t task = task0; task < ntasks; task += tstride) {
     const uint64_t la = task * a.run;
     const uint64_t lb = min(la + a.run, (uint64_t)a.Q);
-    int64_t p = warp_find_parent(a.off, a.P, a.g0 + la, lane);
+    {
+      // tasks come in increasing order: look among the 32 parents from the
+      // previous one first (off is sorted), else search all of them
+      const uint64_t g = a.g0 + la;
+      int k = 32;
+      if (p >= 0) {
+        const int64_t pj = p + 1 + lane;
+        k = __popc(__ballot_sync(0xffffffffu, pj <= a.P && __ldcg(a.off + pj) <= g));
+      }
+      p = k < 32 ? p + k : warp_find_parent(a.off, a.P, g, lane);
+    }
     uint64_t p_lo = __ldcg(a.off + p), p_hi = __ldcg(a.off + p + 1);
     if (task == 0 && lane == 0) a.st->p_first = (unsigned long long)p;
     uint64_t l = la;
@@ -619,7 +636,7 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
           fill = 0;
         }
         if (done) break;
-        l = block_run<VEC, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, lane);
+        l = block_run<VEC, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, cached_p, after, lane);
         const uint64_t gn = a.g0 + l;
         if (l < lb) {
           do {
