@@ -487,8 +487,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
     uint64_t* psi = h->d_psi.as<uint64_t>();
     CK(cudaMemsetAsync(psi + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(), h->d_st.as<ChunkState>(),
-               st, nsm);
+    launch_psi(h->dev(), parents, P, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
     CK(cudaGetLastError());
     sd.launches += 1 + scan_u64_sat(psi, h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
     CK(cudaGetLastError());
@@ -497,6 +496,15 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     TRY(check_device_errors(h, st, "applicability scan"));
     total = *h->pin.u64;
     sd.candidates = total;
+    // Parent records serve the batches that cross parents; with few
+    // candidates per parent they are worth a second pass over the frontier.
+    const bool with_records = !tc && P > 0 && total <= 256ull * (uint64_t)P;
+    if (with_records) {
+      launch_psi(h->dev(), parents, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(), h->d_st.as<ChunkState>(),
+                 st, nsm);
+      CK(cudaGetLastError());
+      sd.launches += 1;
+    }
     const uint64_t T = budget > 0 ? std::min<uint64_t>(total, (uint64_t)budget) : total;
     uint64_t remaining = cap > 0 ? (uint64_t)cap : ~0ull;
     uint64_t g0 = 0, examined = 0;
@@ -547,7 +555,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         a.gmin = h->d_gmin.as<uint32_t>();
         a.slot_of = h->d_slot_of.as<uint32_t>();
         a.ownbits = h->d_own.as<uint32_t>();
-        a.prec = h->d_prec.as<ParentRec>();
+        a.prec = with_records ? h->d_prec.as<ParentRec>() : nullptr;
         a.st = h->d_st.as<ChunkState>();
         if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
         if (tc) {

@@ -27,13 +27,22 @@ __device__ __forceinline__ void set_error(ChunkState* st, uint32_t bits) { atomi
 }  // namespace
 
 // Step (a) for one configuration, neuron by neuron: Psi = prod max(1, omega)
-// (saturating; omega <= 32, so below 2^58 a product cannot overflow), whether
+// (saturating; four counts are multiplied in 32 bits, at most 2^20, and a
+// product below 2^43 cannot overflow by such a factor), whether
 // a child could leave int32, whether the row is past max_expand, and its
 // ParentRec (base-child hash, multi-choice neurons in neuron order).
 struct PsiAcc {
   uint64_t prod = 1, hb = 0;
-  uint32_t nnt = 0;
+  uint32_t nnt = 0, part = 1;
+  int parts = 0;
   bool ov = false, skip = false;
+
+  // prod *= part (saturating; part <= 2^20)
+  __device__ __forceinline__ void flush() {
+    if (part > 1) prod = (prod >> 43) ? (__umul64hi(prod, part) ? kSat : prod * part) : prod * part;
+    part = 1;
+    parts = 0;
+  }
 
   template <bool REC>
   __device__ __forceinline__ void visit(const DevSys& s, int n, int32_t x, int32_t max_expand, ParentRec* rec) {
@@ -52,12 +61,8 @@ struct PsiAcc {
       ov |= x > INT32_MAX - ni.gain;
     }
     const uint32_t cnt = __popc(mask);
-    if (cnt > 1) {
-      if (prod >> 58)
-        prod = __umul64hi(prod, cnt) ? kSat : prod * cnt;
-      else
-        prod *= cnt;
-    }
+    part *= cnt > 1 ? cnt : 1u;  // four counts of at most 32 fit 32 bits
+    if (++parts == 4) flush();
     skip |= max_expand >= 0 && x > max_expand;
     if (REC) {
       hb += hx;
@@ -68,7 +73,10 @@ struct PsiAcc {
       }
     }
   }
-  __device__ __forceinline__ uint64_t psi() const { return skip ? 0ull : prod; }
+  __device__ __forceinline__ uint64_t psi() {
+    flush();
+    return skip ? 0ull : prod;
+  }
   __device__ __forceinline__ bool overflow() const { return ov && !skip; }
 };
 
