@@ -338,8 +338,9 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
   }
   CK(cudaEventCreate(&h->ev[0]));
   CK(cudaEventCreate(&h->ev[1]));
-  CK(cudaEventCreate(&h->evk[0]));
-  CK(cudaEventCreate(&h->evk[1]));
+  for (auto& pair : h->evk)
+    for (auto& e : pair) CK(cudaEventCreate(&e));
+  for (auto& e : h->evs) CK(cudaEventCreate(&e, cudaEventDisableTiming));
   *out = h;
   return SNP_OK;
 }
@@ -349,7 +350,10 @@ int snp_free(snp_handle h) {
   cudaSetDevice(h->device);
   for (auto& e : h->ev)
     if (e) cudaEventDestroy(e);
-  for (auto& e : h->evk)
+  for (auto& pair : h->evk)
+    for (auto& e : pair)
+      if (e) cudaEventDestroy(e);
+  for (auto& e : h->evs)
     if (e) cudaEventDestroy(e);
   delete h;
   return SNP_OK;
@@ -445,6 +449,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     h->rec_rows = h->pool_rows;
   }
   TRY(ensure_chunk_buffers(h, std::min<uint64_t>(qmax, 1 << 16), st));
+  TRY(h->d_ctr.reserve(2 * sizeof(unsigned long long)));
 
   // Root level: C0.
   h->n_rows = 1;
@@ -506,118 +511,51 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
       sd.launches += 1;
     }
     const uint64_t T = budget > 0 ? std::min<uint64_t>(total, (uint64_t)budget) : total;
-    uint64_t remaining = cap > 0 ? (uint64_t)cap : ~0ull;
-    uint64_t g0 = 0, examined = 0;
+    uint64_t remaining = cap > 0 ? (uint64_t)cap : ~0ull;  // as of the passes read back so far
+    uint64_t g0 = 0, examined = 0;                         // g0: first candidate of the next pass
     int64_t nnew = 0;
     bool capped = false;
-    while (g0 < T && !capped) {
-      uint64_t Q = std::min<uint64_t>(T - g0, qmax);
-      if (o->chunk <= 0 && cap > 0) {
-        const double want = (double)remaining / std::max(rate, 1.0 / 1024.0) * 1.25 + 4096.0;
-        if (want < (double)Q) Q = std::max<uint64_t>((uint64_t)want, std::min<uint64_t>(T - g0, 1 << 16));
+    // Device counters {rows, still acceptable}: the commit of a pass takes its
+    // row base and limit from them, so the next pass can be enqueued before
+    // this one is read back (at most two in flight; a pass that starts after
+    // the depth is full does nothing).
+    h->pin.ctr[0] = (unsigned long long)h->n_rows;
+    h->pin.ctr[1] = remaining;
+    CK(cudaMemcpyAsync(h->d_ctr.p, h->pin.ctr, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    struct Flight {
+      uint64_t g0, Q, may_add;
+      int slot;
+    };
+    Flight fl[2];
+    int nfl = 0, next_slot = 0;
+    uint64_t pend_add = 0, pend_q = 0;  // rows the passes in flight may add; their candidates
+    auto retire = [&]() -> int {        // reads back the oldest pass in flight
+      const Flight f = fl[0];
+      fl[0] = fl[1];
+      --nfl;
+      CK(cudaEventSynchronize(h->evs[f.slot]));
+      const ChunkState cs = *h->pin.slot[f.slot];
+      *h->pin.h = cs;
+      pend_add -= f.may_add;
+      pend_q -= f.Q;
+      if (cs.error) {
+        const uint32_t e = cs.error;
+        if (e & kErrOverflow) return fail(SNP_E_OVERFLOW, "expand/claim/commit: a spike count could leave the int32 range");
+        if (e & kErrTimeout) return fail(SNP_E_TIMEOUT, "expand/claim/commit: bounded wait for a hash slot ran out");
+        return fail(SNP_E_INTERNAL, "expand/claim/commit: device consistency check failed (bits 0x%x)", e);
       }
-      // Room for every candidate of the chunk being new.
-      const uint64_t may_add = std::min<uint64_t>(Q, remaining);
-      if ((uint64_t)h->n_rows + may_add > (uint64_t)h->pool_rows) {
-        if ((uint64_t)h->n_rows + may_add > 0x7FFFFFF0ull) return fail(SNP_E_NOMEM, "more than 2^31 configurations");
-        const int64_t want = std::max<int64_t>(h->pool_rows * 2, h->n_rows + (int64_t)may_add);
-        TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
-        h->pool_rows = want;
-        parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
-        if (o->record_parents) {
-          TRY(h->d_rec_parent.reserve(sizeof(int64_t) * want, st, true));
-          TRY(h->d_rec_index.reserve(sizeof(uint64_t) * want, st, true));
-          h->rec_rows = want;
-        }
-      }
-      const uint64_t nslots = h->nbuckets * kBucket;
-      if ((long double)(h->n_rows + tombs) + (long double)Q > 0.75L * (long double)nslots) {
-        uint64_t nb = h->nbuckets;
-        while ((long double)(h->n_rows + Q) > 0.5L * (long double)(nb * kBucket)) nb *= 2;
-        TRY(rebuild_table(h, nb, st));
-        sd.launches += 2;
-        tombs = 0;
-      }
-      TRY(ensure_chunk_buffers(h, Q, st));
-      CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
-      {
-        ClaimArgs a;
-        a.sys = h->dev();
-        a.parents = parents;
-        a.off = h->d_off.as<uint64_t>();
-        a.P = P;
-        a.g0 = g0;
-        a.Q = (uint32_t)Q;
-        a.run = 0;
-        a.table = h->table();
-        a.pool = h->d_pool.as<int32_t>();
-        a.staging = h->d_staging.as<int32_t>();
-        a.gmin = h->d_gmin.as<uint32_t>();
-        a.slot_of = h->d_slot_of.as<uint32_t>();
-        a.ownbits = h->d_own.as<uint32_t>();
-        a.prec = with_records ? h->d_prec.as<ParentRec>() : nullptr;
-        a.st = h->d_st.as<ChunkState>();
-        if (o->kernel_timing) CK(cudaEventRecord(h->evk[0], st));
-        if (tc) {
-          launch_tc_digits(a.sys, parents, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
-                           h->d_pidx.as<uint32_t>(), h->d_red.as<uint8_t>(), st, nsm);
-          CK(cudaMemsetAsync(h->d_hash.p, 0, sizeof(unsigned long long) * Q, st));
-          launch_tc_rows(a.sys, parents, h->d_loc.as<uint8_t>(), h->mp, h->d_pidx.as<uint32_t>(), (uint32_t)Q,
-                         h->d_MT.as<int8_t>(), h->Rp, h->d_rn.as<int16_t>(), h->d_rk.as<uint8_t>(),
-                         h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), st);
-          launch_resolve_rows(a, h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), h->d_red.as<uint8_t>(),
-                              st, nsm);
-          sd.launches += 3;
-        } else {
-          launch_expand(a, st, nsm);
-          sd.launches += 1;
-        }
-        CK(cudaGetLastError());
-        if (o->kernel_timing) CK(cudaEventRecord(h->evk[1], st));
-      }
-      const uint32_t nwords = (uint32_t)((Q + 31) / 32);
-      k_mark<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_own.as<uint32_t>(), h->d_gmin.as<uint32_t>(),
-                                                               h->d_bits.as<uint32_t>(), h->d_srow.as<uint32_t>(),
-                                                               nwords, h->d_st.as<ChunkState>());
-      launch_popc(h->d_bits.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, st);
-      sd.launches += 2 + scan_u32(h->d_wbase.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, h->d_scan_tmp.p, st);
-      CommitArgs c;
-      c.sys = h->dev();
-      c.nwords = nwords;
-      c.bits = h->d_bits.as<uint32_t>();
-      c.wbase = h->d_wbase.as<uint32_t>();
-      c.srow = h->d_srow.as<uint32_t>();
-      c.slot_of = h->d_slot_of.as<uint32_t>();
-      c.staging = h->d_staging.as<int32_t>();
-      c.table = h->table();
-      c.pool = h->d_pool.as<int32_t>();
-      c.row_base = h->n_rows;
-      c.remaining = remaining;
-      c.rec_parent = o->record_parents ? h->d_rec_parent.as<int64_t>() : nullptr;
-      c.rec_index = o->record_parents ? h->d_rec_index.as<uint64_t>() : nullptr;
-      c.off = h->d_off.as<uint64_t>();
-      c.P = P;
-      c.parent_base = level_lo;
-      c.g0 = g0;
-      c.st = h->d_st.as<ChunkState>();
-      k_commit<<<grid_for(nwords, 8, nsm * 16), 256, 0, st>>>(c);
-      CK(cudaGetLastError());
-      k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_bits.as<uint32_t>(), nwords);
-      CK(cudaGetLastError());
-      sd.launches += 2;
-      TRY(check_device_errors(h, st, "expand/claim/commit"));
-      const ChunkState cs = *h->pin.h;
+      if (capped) return SNP_OK;  // enqueued before the cap was known: did nothing
       if (o->kernel_timing) {
         float kms = 0.f;
-        CK(cudaEventElapsedTime(&kms, h->evk[0], h->evk[1]));
+        CK(cudaEventElapsedTime(&kms, h->evk[f.slot][0], h->evk[f.slot][1]));
         sd.expand_ms += kms;
       }
       {
         // algorithmic bytes of the expand kernel (include/snp.h, snp_depth_info)
         const int64_t row = 4ll * m;
-        const int64_t dups = (int64_t)Q - (int64_t)cs.n_alloc;
+        const int64_t dups = (int64_t)f.Q - (int64_t)cs.n_alloc;
         const int64_t nparents = (int64_t)(cs.p_last - cs.p_first + 1);
-        sd.expand_bytes += (int64_t)Q * 8 + dups * row + (int64_t)cs.n_alloc * (row + 8) + nparents * row;
+        sd.expand_bytes += (int64_t)f.Q * 8 + dups * row + (int64_t)cs.n_alloc * (row + 8) + nparents * row;
       }
       const uint64_t acc = std::min<uint64_t>(cs.n_alloc, remaining);
       tombs += (int64_t)(cs.n_alloc - acc);
@@ -625,14 +563,140 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
       h->n_rows += (int64_t)acc;
       if (remaining != ~0ull) remaining -= acc;
       if (cs.capped) {
-        examined = g0 + cs.last_lid + 1;
+        examined = f.g0 + cs.last_lid + 1;
         capped = true;
       } else {
-        examined = g0 + Q;
+        examined = f.g0 + f.Q;
       }
-      rate = std::max(1e-6, (double)cs.n_alloc / (double)Q);
-      g0 += Q;
+      rate = std::max(1e-6, (double)cs.n_alloc / (double)f.Q);
       sd.chunks += 1;
+      return SNP_OK;
+    };
+    for (;;) {
+      // what the depth may still accept once the passes in flight are done, as expected from the last rate
+      const double left = cap > 0 ? (double)remaining - rate * (double)pend_q : 1.0;
+      if (nfl < 2 && g0 < T && !capped && remaining > 0 && (nfl == 0 || o->chunk > 0 || left > 0)) {
+        uint64_t Q = std::min<uint64_t>(T - g0, qmax);
+        if (o->chunk <= 0 && cap > 0) {
+          const double want = std::max(left, 0.0) / std::max(rate, 1.0 / 1024.0) * 1.25 + 4096.0;
+          if (want < (double)Q) Q = std::max<uint64_t>((uint64_t)want, std::min<uint64_t>(T - g0, 1 << 16));
+        }
+        // Room for every candidate of the pass being new, after those in flight.
+        const uint64_t may_add = std::min<uint64_t>(Q, remaining);
+        const uint64_t rows_hi = (uint64_t)h->n_rows + pend_add + may_add;
+        if (rows_hi > (uint64_t)h->pool_rows) {
+          if (rows_hi > 0x7FFFFFF0ull) {
+            if (nfl > 0) {  // the passes in flight may settle it
+              TRY(retire());
+              continue;
+            }
+            return fail(SNP_E_NOMEM, "more than 2^31 configurations");
+          }
+          const int64_t want = std::max<int64_t>(h->pool_rows * 2, (int64_t)rows_hi);
+          TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
+          h->pool_rows = want;
+          parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
+          if (o->record_parents) {
+            TRY(h->d_rec_parent.reserve(sizeof(int64_t) * want, st, true));
+            TRY(h->d_rec_index.reserve(sizeof(uint64_t) * want, st, true));
+            h->rec_rows = want;
+          }
+        }
+        const uint64_t nslots = h->nbuckets * kBucket;
+        if ((long double)(h->n_rows + tombs) + (long double)(pend_q + Q) > 0.75L * (long double)nslots) {
+          if (nfl > 0) {  // a rebuild needs exact counts
+            TRY(retire());
+            continue;
+          }
+          uint64_t nb = h->nbuckets;
+          while ((long double)(h->n_rows + Q) > 0.5L * (long double)(nb * kBucket)) nb *= 2;
+          TRY(rebuild_table(h, nb, st));
+          sd.launches += 2;
+          tombs = 0;
+        }
+        TRY(ensure_chunk_buffers(h, Q, st));
+        const int slot = next_slot;
+        next_slot ^= 1;
+        CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
+        {
+          ClaimArgs a;
+          a.sys = h->dev();
+          a.parents = parents;
+          a.off = h->d_off.as<uint64_t>();
+          a.P = P;
+          a.g0 = g0;
+          a.Q = (uint32_t)Q;
+          a.run = 0;
+          a.table = h->table();
+          a.pool = h->d_pool.as<int32_t>();
+          a.staging = h->d_staging.as<int32_t>();
+          a.gmin = h->d_gmin.as<uint32_t>();
+          a.slot_of = h->d_slot_of.as<uint32_t>();
+          a.ownbits = h->d_own.as<uint32_t>();
+          a.prec = with_records ? h->d_prec.as<ParentRec>() : nullptr;
+          a.ctr = h->d_ctr.as<unsigned long long>();
+          a.st = h->d_st.as<ChunkState>();
+          if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][0], st));
+          if (tc) {
+            launch_tc_digits(a.sys, parents, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
+                             h->d_pidx.as<uint32_t>(), h->d_red.as<uint8_t>(), st, nsm);
+            CK(cudaMemsetAsync(h->d_hash.p, 0, sizeof(unsigned long long) * Q, st));
+            launch_tc_rows(a.sys, parents, h->d_loc.as<uint8_t>(), h->mp, h->d_pidx.as<uint32_t>(), (uint32_t)Q,
+                           h->d_MT.as<int8_t>(), h->Rp, h->d_rn.as<int16_t>(), h->d_rk.as<uint8_t>(),
+                           h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(), st);
+            launch_resolve_rows(a, h->d_rows.as<int32_t>(), h->d_hash.as<unsigned long long>(),
+                                h->d_red.as<uint8_t>(), st, nsm);
+            sd.launches += 3;
+          } else {
+            launch_expand(a, st, nsm);
+            sd.launches += 1;
+          }
+          CK(cudaGetLastError());
+          if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][1], st));
+        }
+        const uint32_t nwords = (uint32_t)((Q + 31) / 32);
+        k_mark<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_own.as<uint32_t>(), h->d_gmin.as<uint32_t>(),
+                                                                 h->d_bits.as<uint32_t>(), h->d_srow.as<uint32_t>(),
+                                                                 nwords, h->d_st.as<ChunkState>());
+        launch_popc(h->d_bits.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, st);
+        sd.launches += 2 + scan_u32(h->d_wbase.as<uint32_t>(), h->d_wbase.as<uint32_t>(), nwords, h->d_scan_tmp.p, st);
+        CommitArgs c;
+        c.sys = h->dev();
+        c.nwords = nwords;
+        c.bits = h->d_bits.as<uint32_t>();
+        c.wbase = h->d_wbase.as<uint32_t>();
+        c.srow = h->d_srow.as<uint32_t>();
+        c.slot_of = h->d_slot_of.as<uint32_t>();
+        c.staging = h->d_staging.as<int32_t>();
+        c.table = h->table();
+        c.pool = h->d_pool.as<int32_t>();
+        c.row_base = 0;
+        c.remaining = 0;
+        c.ctr = h->d_ctr.as<unsigned long long>();
+        c.rec_parent = o->record_parents ? h->d_rec_parent.as<int64_t>() : nullptr;
+        c.rec_index = o->record_parents ? h->d_rec_index.as<uint64_t>() : nullptr;
+        c.off = h->d_off.as<uint64_t>();
+        c.P = P;
+        c.parent_base = level_lo;
+        c.g0 = g0;
+        c.st = h->d_st.as<ChunkState>();
+        k_commit<<<grid_for(nwords, 8, nsm * 16), 256, 0, st>>>(c);
+        CK(cudaGetLastError());
+        k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(h->d_bits.as<uint32_t>(), nwords,
+                                                                       h->d_ctr.as<unsigned long long>(),
+                                                                       h->d_st.as<ChunkState>());
+        CK(cudaGetLastError());
+        sd.launches += 2;
+        CK(cudaMemcpyAsync(h->pin.slot[slot], h->d_st.p, sizeof(ChunkState), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(h->evs[slot], st));
+        fl[nfl++] = Flight{g0, Q, may_add, slot};
+        pend_add += may_add;
+        pend_q += Q;
+        g0 += Q;
+        continue;
+      }
+      if (nfl == 0) break;
+      TRY(retire());
     }
     CK(cudaEventRecord(h->ev[1], st));
     CK(cudaEventSynchronize(h->ev[1]));
@@ -879,6 +943,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       a.slot_of = L.slot_of;
       a.ownbits = L.own;
       a.prec = nullptr;
+      a.ctr = nullptr;
       a.st = L.st;
       launch_expand(a, st, nsm);
       CK(cudaGetLastError());
@@ -904,10 +969,11 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       c.P = P;
       c.parent_base = level_lo;
       c.g0 = g0;
+      c.ctr = nullptr;
       c.st = L.st;
       k_commit<<<grid_for(nwords, 8, nsm * 16), 256, 0, st>>>(c);
       CK(cudaGetLastError());
-      k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(L.bits, nwords);
+      k_clear_bits<<<grid_for(nwords, 256, nsm * 8), 256, 0, st>>>(L.bits, nwords, nullptr, nullptr);
       CK(cudaGetLastError());
       CK(cudaMemcpyAsync(hst, L.st, sizeof(ChunkState), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));

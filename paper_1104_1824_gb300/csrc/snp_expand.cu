@@ -690,6 +690,7 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
 template <bool VEC>
 __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.ctr && __ldcg(a.ctr + 1) == 0) return;  // the depth is full: a chunk enqueued ahead has nothing to do
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   ExpandSmem w = expand_smem(smem_raw + (size_t)wib * expand_warp_bytes(a.sys.m, B, ts), a.sys.m, B, ts);
   expand_warp<VEC, 0>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
@@ -701,6 +702,7 @@ template <bool VEC>
 __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t* rows,
                                                       const unsigned long long* hash, const uint8_t* redundant) {
   const int m = a.sys.m;
+  if (a.ctr && __ldcg(a.ctr + 1) == 0) return;
   for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < a.Q; base += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t lid = base + threadIdx.x;
     bool done = lid >= a.Q || redundant[lid];
@@ -922,6 +924,7 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       a.slot_of = sc.slot_of;
       a.ownbits = sc.own;
       a.prec = nullptr;
+      a.ctr = nullptr;
       a.st = sc.st;
       if ((m & 3) == 0)
         expand_warp<true, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);

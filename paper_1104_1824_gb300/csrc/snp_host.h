@@ -80,13 +80,19 @@ struct DevBuf {
 
 // Pinned host words the depth loop reads back: chunk counters and one u64.
 struct PinnedState {
-  ChunkState* h = nullptr;
+  ChunkState* h = nullptr;      // counters of the last pass read back
+  ChunkState* slot[2] = {nullptr, nullptr};  // counters of passes in flight
   uint64_t* u64 = nullptr;
+  unsigned long long* ctr = nullptr;         // source of the device counters {rows, still acceptable}
   PinnedState() {
     void* p = nullptr;
-    if (cudaMallocHost(&p, 256) == cudaSuccess) {
-      h = static_cast<ChunkState*>(p);
-      u64 = reinterpret_cast<uint64_t*>(static_cast<char*>(p) + 128);
+    if (cudaMallocHost(&p, 512) == cudaSuccess) {
+      char* c = static_cast<char*>(p);
+      h = reinterpret_cast<ChunkState*>(c);
+      u64 = reinterpret_cast<uint64_t*>(c + 128);
+      slot[0] = reinterpret_cast<ChunkState*>(c + 192);
+      slot[1] = reinterpret_cast<ChunkState*>(c + 256);
+      ctr = reinterpret_cast<unsigned long long*>(c + 320);
     }
   }
   ~PinnedState() {
@@ -149,7 +155,7 @@ struct snp_system {
   // exploration state
   DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_off, d_scan_tmp, d_st,
       d_rec_parent, d_rec_index, d_tmp,
-      d_psi, d_prec;
+      d_psi, d_prec, d_ctr;
   int64_t pool_rows = 0;  // capacity in rows
   uint64_t nbuckets = 0;
   uint64_t q_cap = 0;     // staging capacity in rows
@@ -157,7 +163,8 @@ struct snp_system {
   int64_t rec_rows = 0;
   PinnedState pin;
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaEvent_t evk[2] = {nullptr, nullptr};  // around the expand kernel
+  cudaEvent_t evk[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // around the expand kernel, per pass slot
+  cudaEvent_t evs[2] = {nullptr, nullptr};   // end of a pass in flight, per slot
   // results
   bool explored = false;
   bool have_parents = false;

@@ -172,21 +172,22 @@ __device__ __forceinline__ int64_t find_parent(const uint64_t* off, int64_t P, u
 // One first occurrence: accepted (rank < remaining: copied to its pool row in
 // rank order, its slot pointed at the row) or rejected (its slot becomes a
 // tombstone).
-__device__ __forceinline__ void commit_one(const CommitArgs& a, uint32_t lid, uint64_t rank) {
+__device__ __forceinline__ void commit_one(const CommitArgs& a, uint32_t lid, uint64_t rank, int64_t row_base,
+                                           uint64_t remaining) {
   const int m = a.sys.m;
   const uint32_t s = a.srow[lid];
   unsigned long long* slot = a.table.slots + a.slot_of[s];
   const unsigned long long hi = (*slot) & 0xFFFFFFFF00000000ull;
-  if (rank >= a.remaining) {
+  if (rank >= remaining) {
     *slot = hi | kRowTomb;
     return;
   }
-  const int64_t row = a.row_base + (int64_t)rank;
+  const int64_t row = row_base + (int64_t)rank;
   const int32_t* src = a.staging + (size_t)s * m;
   int32_t* dst = a.pool + (size_t)row * m;
   copy_row_cg(src, dst, m);
   *slot = hi | (uint32_t)row;
-  if (rank + 1 == a.remaining) {
+  if (rank + 1 == remaining) {
     a.st->capped = 1;
     a.st->last_lid = lid;
   }
@@ -205,6 +206,8 @@ __device__ __forceinline__ void commit_one(const CommitArgs& a, uint32_t lid, ui
 __global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
   const int lane = threadIdx.x & 31;
   const uint32_t total = *reinterpret_cast<volatile const unsigned int*>(&a.st->n_alloc);
+  const int64_t row_base = a.ctr ? (int64_t)__ldcg(a.ctr) : a.row_base;
+  const uint64_t remaining = a.ctr ? __ldcg(a.ctr + 1) : a.remaining;
   const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   for (uint64_t r0 = ((uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; r0 < total;
        r0 += nwarps * 32) {
@@ -240,13 +243,21 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
       }
       const uint32_t word = a.bits[w];
       const uint32_t q = (uint32_t)(r - a.wbase[w]);
-      commit_one(a, (uint32_t)w * 32u + __fns(word, 0, (int)q + 1), r);
+      commit_one(a, (uint32_t)w * 32u + __fns(word, 0, (int)q + 1), r, row_base, remaining);
     }
   }
 }
 
-__global__ void k_clear_bits(uint32_t* bits, uint32_t nwords) {
+// Clears the first-occurrence bitmap; with ctr, one thread then moves the
+// device counters past the chunk's accepted configurations.
+__global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x) bits[i] = 0;
+  if (ctr && blockIdx.x == 0 && threadIdx.x == 0) {
+    const unsigned long long left = ctr[1];
+    const unsigned long long acc = min((unsigned long long)st->n_alloc, left);
+    ctr[0] += acc;
+    if (left != ~0ull) ctr[1] = left - acc;
+  }
 }
 
 // Inserts committed rows [r0, r1) (all distinct) into an empty or partly

@@ -21,6 +21,7 @@ struct ClaimArgs {
   uint32_t* slot_of;          // [Q] per claiming lid: its table slot
   uint32_t* ownbits;          // [Q / 32 + 1] bit lid set iff candidate lid claimed a new key
   const ParentRec* prec;      // [P] parent summaries, or nullptr (decode from the rows)
+  const unsigned long long* ctr;  // device counters {rows, still acceptable} or nullptr; none left: no work
   ChunkState* st;
 };
 
@@ -36,6 +37,7 @@ struct CommitArgs {
   int32_t* pool;
   int64_t row_base;           // pool row of rank 0
   uint64_t remaining;         // how many more configurations the depth may accept
+  const unsigned long long* ctr;  // or, when set, both from device counters {rows, still acceptable}
   // parent records (optional)
   int64_t* rec_parent;        // [rows] or nullptr
   uint64_t* rec_index;
@@ -118,7 +120,7 @@ size_t tc_rows_smem(int mp);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);
-__global__ void k_clear_bits(uint32_t* bits, uint32_t nwords);
+__global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st);
 __global__ void k_insert_rows(DevSys s, const int32_t* pool, int64_t r0, int64_t r1, DevTable t, ChunkState* st);
 __global__ void k_step_children(DevSys s, const int32_t* C, uint64_t n, int32_t* out);
 __global__ void k_fill_u64(unsigned long long* p, uint64_t n, unsigned long long v);
