@@ -737,9 +737,14 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const size_t per_warp = expand_warp_bytes(m, B, ts);
   const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (100u << 10) / per_warp));
   const size_t smem = per_warp * wpb;
-  a.run = (uint32_t)(8 * B);
-  const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
   const int per_sm = (int)std::max<size_t>(1, (220u << 10) / smem);
+  // a task (run of candidates) of at least 8 tiles, and about two per warp of
+  // the grid: each task pays one decode of its first block
+  {
+    const uint64_t two_per_warp = 2ull * nsm * per_sm * wpb;
+    a.run = (uint32_t)std::max<uint64_t>(8ull * B, ((uint64_t)a.Q + two_per_warp - 1) / two_per_warp);
+  }
+  const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
   const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm * per_sm);
   const bool vec = (m % 4) == 0;
   auto fn = vec ? k_expand<true> : k_expand<false>;
