@@ -114,13 +114,65 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int6
   if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
 }
 
+// k_psi for m % 4 == 0 with coalesced loads: a block takes 256 rows at a
+// time and moves them through shared memory 32 columns at a time (each row's
+// slab is 128 contiguous bytes, read by 8 consecutive threads); thread t then
+// reads row t's slab at a stride of 33 words, so the 32 lanes of a warp hit 32
+// different banks.
+constexpr int kPsiRows = 256, kPsiSlab = 32;
+template <bool REC>
+__global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand,
+                                                        uint64_t* psi, ParentRec* rec, ChunkState* st) {
+  __shared__ int32_t slab[kPsiRows][kPsiSlab + 1];
+  const int m = s.m;
+  const int t = threadIdx.x;
+  bool over = false;
+  for (int64_t p0 = (int64_t)blockIdx.x * kPsiRows; p0 < P; p0 += (int64_t)gridDim.x * kPsiRows) {
+    const int nrows = (int)min((int64_t)kPsiRows, P - p0);
+    const int64_t p = p0 + t;
+    PsiAcc acc;
+    for (int n0 = 0; n0 < m; n0 += kPsiSlab) {
+      const int w = min(kPsiSlab, m - n0);  // columns in this slab (a multiple of 4)
+      const int q4 = w >> 2;                // 16-byte pieces per row
+      __syncthreads();
+      for (int i = t; i < nrows * q4; i += kPsiRows) {
+        const int r = i / q4, q = i - r * q4;
+        const int4 v = __ldg(reinterpret_cast<const int4*>(rows + (size_t)(p0 + r) * m + n0) + q);
+        int32_t* d = &slab[r][4 * q];
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
+      }
+      __syncthreads();
+      if (t < nrows)
+        for (int j = 0; j < w; ++j) acc.visit<REC>(s, n0 + j, slab[t][j], max_expand, REC ? rec + p : nullptr);
+    }
+    if (t < nrows) {
+      psi[p] = acc.psi();
+      if (REC) {
+        rec[p].hbase = acc.hb;
+        rec[p].nnt = acc.nnt;
+      }
+      over |= acc.overflow();
+    }
+  }
+  if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
+}
+
 int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ParentRec* rec,
                ChunkState* st, cudaStream_t stream, int nsm) {
   const int threads = 256;
   const int64_t want = (P + threads - 1) / threads;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
-  const bool vec = (s.m % 4) == 0;
-  auto fn = rec ? (vec ? k_psi<true, true> : k_psi<false, true>) : (vec ? k_psi<true, false> : k_psi<false, false>);
+  if ((s.m % 4) == 0) {
+    const int64_t tiles = (P + kPsiRows - 1) / kPsiRows;
+    const int tb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * 6));
+    auto fn = rec ? k_psi_tiled<true> : k_psi_tiled<false>;
+    fn<<<tb, kPsiRows, 0, stream>>>(s, rows, P, max_expand, psi, rec, st);
+    return 1;
+  }
+  auto fn = rec ? k_psi<false, true> : k_psi<false, false>;
   fn<<<blocks, threads, 0, stream>>>(s, rows, P, max_expand, psi, rec, st);
   return 1;
 }
