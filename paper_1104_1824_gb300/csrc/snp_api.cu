@@ -58,7 +58,7 @@ int ensure_chunk_buffers(snp_system* h, uint64_t q, cudaStream_t st) {
   if (h->q_cap >= q) return SNP_OK;
   q = std::max<uint64_t>(q, std::min<uint64_t>(h->q_cap * 2, 1ull << 30));
   const uint64_t words = q / 32 + 1;
-  TRY(h->d_staging.reserve(sizeof(int32_t) * (size_t)h->m * q));
+  TRY(h->d_sidx.reserve(sizeof(uint32_t) * q));
   TRY(h->d_gmin.reserve(sizeof(uint32_t) * q));
   TRY(h->d_slot_of.reserve(sizeof(uint32_t) * q));
   TRY(h->d_srow.reserve(sizeof(uint32_t) * q));
@@ -107,7 +107,8 @@ int tc_prepare(snp_system* h, uint64_t q, cudaStream_t st) {
   return SNP_OK;
 }
 
-// Clears the table and inserts rows [0, n) of the pool (2 launches).
+// Clears the table and inserts the configurations found so far (2 launches);
+// row k lives in store row perm[k].
 int rebuild_table(snp_system* h, uint64_t nbuckets, cudaStream_t st) {
   TRY(h->d_slots.reserve(nbuckets * kBucket * sizeof(unsigned long long)));
   h->nbuckets = nbuckets;
@@ -117,7 +118,7 @@ int rebuild_table(snp_system* h, uint64_t nbuckets, cudaStream_t st) {
   CK(cudaGetLastError());
   if (h->n_rows > 0) {
     k_insert_rows<<<grid_for(h->n_rows, kWarpsPerBlock, 152 * 64), kThreads, 0, st>>>(
-        h->dev(), h->d_pool.as<int32_t>(), 0, h->n_rows, h->table(), h->d_st.as<ChunkState>());
+        h->dev(), h->d_pool.as<int32_t>(), h->d_perm.as<uint32_t>(), 0, h->n_rows, h->table(), h->d_st.as<ChunkState>());
     CK(cudaGetLastError());
   }
   return SNP_OK;
@@ -375,7 +376,7 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
   uint64_t* dpsi = reinterpret_cast<uint64_t*>(h->d_tmp.as<char>() + ((sizeof(int32_t) * m + 15) / 16) * 16);
   CK(cudaMemcpy(dC, c.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
   CK(cudaMemset(h->d_st.p, 0, sizeof(ChunkState)));
-  launch_psi(h->dev(), dC, 1, -1, dpsi, nullptr, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
+  launch_psi(h->dev(), dC, nullptr, 1, -1, dpsi, nullptr, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
   CK(cudaGetLastError());
   uint64_t ps = 0;
   CK(cudaMemcpy(&ps, dpsi, sizeof ps, cudaMemcpyDeviceToHost));
@@ -413,6 +414,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
   h->depth_reached = 0;
   h->batch.reset();
   h->result_pool = nullptr;
+  h->result_perm = nullptr;
   const int m = h->m;
   const int nsm = sm_count(h->device);
   const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
@@ -438,22 +440,34 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     const long double want = 1.0L + (long double)o->depth * (long double)budget;
     if (want < 2.0e9L) rows_plan = std::max<int64_t>(rows_plan, std::min<int64_t>((int64_t)want, 1 << 20));
   }
-  if (h->pool_rows < rows_plan) {
-    TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * rows_plan));
-    h->pool_rows = rows_plan;
+  // The store keeps every claimed row where its owner wrote it (claims past
+  // the cap included, at most one pass's worth per depth); perm lists the
+  // configurations in discovery order.
+  if (h->perm_rows < rows_plan) {
+    TRY(h->d_perm.reserve(sizeof(uint32_t) * rows_plan));
+    h->perm_rows = rows_plan;
+  }
+  {
+    const int64_t store_plan = (int64_t)std::min<uint64_t>(0x7FFFFFF0ull, (uint64_t)rows_plan + qmax);
+    if (h->pool_rows < store_plan) {
+      TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * store_plan));
+      h->pool_rows = store_plan;
+    }
   }
 
   if (o->record_parents) {
-    TRY(h->d_rec_parent.reserve(sizeof(int64_t) * h->pool_rows));
-    TRY(h->d_rec_index.reserve(sizeof(uint64_t) * h->pool_rows));
-    h->rec_rows = h->pool_rows;
+    TRY(h->d_rec_parent.reserve(sizeof(int64_t) * h->perm_rows));
+    TRY(h->d_rec_index.reserve(sizeof(uint64_t) * h->perm_rows));
+    h->rec_rows = h->perm_rows;
   }
   TRY(ensure_chunk_buffers(h, std::min<uint64_t>(qmax, 1 << 16), st));
-  TRY(h->d_ctr.reserve(2 * sizeof(unsigned long long)));
+  TRY(h->d_ctr.reserve(3 * sizeof(unsigned long long)));
 
-  // Root level: C0.
+  // Root level: C0, store row 0.
   h->n_rows = 1;
+  h->n_store = 1;
   CK(cudaMemcpyAsync(h->d_pool.p, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(h->d_perm.p, 0, sizeof(uint32_t), st));
   if (o->record_parents) {
     const int64_t rp = -1;
     const uint64_t ri = 0;
@@ -488,11 +502,12 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
       TRY(h->d_scan_tmp.reserve(scan_temp_bytes(P + 1, 8)));
       h->psi_cap = P + 1;
     }
-    const int32_t* parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
+    const int32_t* parents = h->d_pool.as<int32_t>();            // the store
+    const uint32_t* pperm = h->d_perm.as<uint32_t>() + level_lo;  // its rows of this frontier
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
     uint64_t* psi = h->d_psi.as<uint64_t>();
     CK(cudaMemsetAsync(psi + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, P, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
+    launch_psi(h->dev(), parents, pperm, P, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
     CK(cudaGetLastError());
     sd.launches += 1 + scan_u64_sat(psi, h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
     CK(cudaGetLastError());
@@ -505,8 +520,8 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     // candidates per parent they are worth a second pass over the frontier.
     const bool with_records = !tc && P > 0 && total <= 256ull * (uint64_t)P;
     if (with_records) {
-      launch_psi(h->dev(), parents, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(), h->d_st.as<ChunkState>(),
-                 st, nsm);
+      launch_psi(h->dev(), parents, pperm, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(),
+                 h->d_st.as<ChunkState>(), st, nsm);
       CK(cudaGetLastError());
       sd.launches += 1;
     }
@@ -521,7 +536,8 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     // the depth is full does nothing).
     h->pin.ctr[0] = (unsigned long long)h->n_rows;
     h->pin.ctr[1] = remaining;
-    CK(cudaMemcpyAsync(h->d_ctr.p, h->pin.ctr, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
+    h->pin.ctr[2] = (unsigned long long)h->n_store;
+    CK(cudaMemcpyAsync(h->d_ctr.p, h->pin.ctr, 3 * sizeof(unsigned long long), cudaMemcpyHostToDevice, st));
     struct Flight {
       uint64_t g0, Q, may_add;
       int slot;
@@ -558,6 +574,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         sd.expand_bytes += (int64_t)f.Q * 8 + dups * row + (int64_t)cs.n_alloc * (row + 8) + nparents * row;
       }
       const uint64_t acc = std::min<uint64_t>(cs.n_alloc, remaining);
+      h->n_store += (int64_t)cs.n_alloc;  // every claim took a store row
       tombs += (int64_t)(cs.n_alloc - acc);
       nnew += (int64_t)acc;
       h->n_rows += (int64_t)acc;
@@ -583,24 +600,32 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         }
         // Room for every candidate of the pass being new, after those in flight.
         const uint64_t may_add = std::min<uint64_t>(Q, remaining);
-        const uint64_t rows_hi = (uint64_t)h->n_rows + pend_add + may_add;
-        if (rows_hi > (uint64_t)h->pool_rows) {
-          if (rows_hi > 0x7FFFFFF0ull) {
-            if (nfl > 0) {  // the passes in flight may settle it
-              TRY(retire());
-              continue;
-            }
-            return fail(SNP_E_NOMEM, "more than 2^31 configurations");
+        const uint64_t rows_hi = (uint64_t)h->n_rows + pend_add + may_add;  // discovery indices
+        const uint64_t store_hi = (uint64_t)h->n_store + pend_q + Q;      // store rows (one per claim)
+        if (rows_hi > 0x7FFFFFF0ull || store_hi > 0x7FFFFFF0ull) {
+          if (nfl > 0) {  // the passes in flight may settle it
+            TRY(retire());
+            continue;
           }
-          const int64_t want = std::max<int64_t>(h->pool_rows * 2, (int64_t)rows_hi);
-          TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
-          h->pool_rows = want;
-          parents = h->d_pool.as<int32_t>() + (size_t)level_lo * m;
+          return fail(SNP_E_NOMEM, "more than 2^31 configurations");
+        }
+        if (rows_hi > (uint64_t)h->perm_rows) {
+          const int64_t want = std::max<int64_t>(h->perm_rows * 2, (int64_t)rows_hi);
+          TRY(h->d_perm.reserve(sizeof(uint32_t) * want, st, true));
+          h->perm_rows = want;
+          pperm = h->d_perm.as<uint32_t>() + level_lo;
           if (o->record_parents) {
             TRY(h->d_rec_parent.reserve(sizeof(int64_t) * want, st, true));
             TRY(h->d_rec_index.reserve(sizeof(uint64_t) * want, st, true));
             h->rec_rows = want;
           }
+        }
+        if (store_hi > (uint64_t)h->pool_rows) {
+          const int64_t want =
+              (int64_t)std::min<uint64_t>(0x7FFFFFF0ull, std::max<uint64_t>(2ull * h->pool_rows, store_hi));
+          TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
+          h->pool_rows = want;
+          parents = h->d_pool.as<int32_t>();
         }
         const uint64_t nslots = h->nbuckets * kBucket;
         if ((long double)(h->n_rows + tombs) + (long double)(pend_q + Q) > 0.75L * (long double)nslots) {
@@ -628,8 +653,12 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
           a.Q = (uint32_t)Q;
           a.run = 0;
           a.table = h->table();
+          a.pperm = pperm;
           a.pool = h->d_pool.as<int32_t>();
-          a.staging = h->d_staging.as<int32_t>();
+          a.staging = nullptr;
+          a.store_ctr = h->d_ctr.as<unsigned long long>() + 2;
+          a.sidx_of = h->d_sidx.as<uint32_t>();
+          a.store_cap = (uint64_t)h->pool_rows;
           a.gmin = h->d_gmin.as<uint32_t>();
           a.slot_of = h->d_slot_of.as<uint32_t>();
           a.ownbits = h->d_own.as<uint32_t>();
@@ -638,7 +667,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
           a.st = h->d_st.as<ChunkState>();
           if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][0], st));
           if (tc) {
-            launch_tc_digits(a.sys, parents, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
+            launch_tc_digits(a.sys, parents, pperm, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
                              h->d_pidx.as<uint32_t>(), h->d_red.as<uint8_t>(), st, nsm);
             CK(cudaMemsetAsync(h->d_hash.p, 0, sizeof(unsigned long long) * Q, st));
             launch_tc_rows(a.sys, parents, h->d_loc.as<uint8_t>(), h->mp, h->d_pidx.as<uint32_t>(), (uint32_t)Q,
@@ -667,9 +696,11 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         c.wbase = h->d_wbase.as<uint32_t>();
         c.srow = h->d_srow.as<uint32_t>();
         c.slot_of = h->d_slot_of.as<uint32_t>();
-        c.staging = h->d_staging.as<int32_t>();
+        c.staging = nullptr;
         c.table = h->table();
         c.pool = h->d_pool.as<int32_t>();
+        c.perm = h->d_perm.as<uint32_t>();
+        c.sidx_of = h->d_sidx.as<uint32_t>();
         c.row_base = 0;
         c.remaining = 0;
         c.ctr = h->d_ctr.as<unsigned long long>();
@@ -714,6 +745,7 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
   }
   h->explored = true;
   h->result_pool = h->d_pool.as<int32_t>();
+  h->result_perm = h->d_perm.as<uint32_t>();
   h->have_parents = o->record_parents != 0;
   if (depth_reached) *depth_reached = h->depth_reached;
   if (truncated_flags)
@@ -732,7 +764,22 @@ int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int6
   if (capacity < h->n_rows) return fail(SNP_E_BUFFER, "capacity %lld < %lld rows", (long long)capacity, (long long)h->n_rows);
   if (!out) return fail(SNP_E_INVALID, "out is NULL");
   CK(cudaSetDevice(h->device));
-  CK(cudaMemcpy(out, h->result_pool, sizeof(int32_t) * (size_t)h->m * h->n_rows, cudaMemcpyDefault));
+  const size_t bytes = sizeof(int32_t) * (size_t)h->m * h->n_rows;
+  if (!h->result_perm) {
+    CK(cudaMemcpy(out, h->result_pool, bytes, cudaMemcpyDefault));
+    return SNP_OK;
+  }
+  // rows in discovery order: gather from the store (into `out` when it is
+  // device memory, else through a device buffer)
+  int32_t* dst = out;
+  if (!is_device_ptr(out)) {
+    TRY(h->d_tmp.reserve(bytes));
+    dst = h->d_tmp.as<int32_t>();
+  }
+  launch_gather_rows(h->result_pool, h->result_perm, h->n_rows, h->m, dst, nullptr);
+  CK(cudaGetLastError());
+  if (dst != out) CK(cudaMemcpy(out, dst, bytes, cudaMemcpyDeviceToHost));
+  else CK(cudaDeviceSynchronize());
   return SNP_OK;
 }
 
@@ -880,7 +927,8 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
   auto clear_and_insert = [&](int64_t rows) -> int {
     k_fill_u64<<<grid_for((int64_t)kStaticSlots, 256, nsm * 32), 256, 0, st>>>(L.slots, kStaticSlots, kEmpty);
     CK(cudaGetLastError());
-    k_insert_rows<<<grid_for(rows, kWarpsPerBlock, nsm * 64), kThreads, 0, st>>>(h->dev(), out, 0, rows, table, L.st);
+    k_insert_rows<<<grid_for(rows, kWarpsPerBlock, nsm * 64), kThreads, 0, st>>>(h->dev(), out, nullptr, 0, rows,
+                                                                                  table, L.st);
     CK(cudaGetLastError());
     return SNP_OK;
   };
@@ -898,7 +946,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
     const int32_t* parents = out + (size_t)level_lo * m;
     CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
     CK(cudaMemsetAsync(L.psi + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, P, o->max_expand_value, L.psi, nullptr, L.st, st, nsm);
+    launch_psi(h->dev(), parents, nullptr, P, o->max_expand_value, L.psi, nullptr, L.st, st, nsm);
     CK(cudaGetLastError());
     scan_u64_sat(L.psi, L.off, P + 1, L.scan_tmp, st);
     CK(cudaMemcpyAsync(h->pin.u64, L.off + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -944,6 +992,10 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       a.ownbits = L.own;
       a.prec = nullptr;
       a.ctr = nullptr;
+      a.pperm = nullptr;
+      a.store_ctr = nullptr;  // staging mode: rows are copied into `out` by the commit
+      a.sidx_of = nullptr;
+      a.store_cap = 0;
       a.st = L.st;
       launch_expand(a, st, nsm);
       CK(cudaGetLastError());
@@ -970,6 +1022,8 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       c.parent_base = level_lo;
       c.g0 = g0;
       c.ctr = nullptr;
+      c.perm = nullptr;
+      c.sidx_of = nullptr;
       c.st = L.st;
       k_commit<<<grid_for(nwords, 8, nsm * 16), 256, 0, st>>>(c);
       CK(cudaGetLastError());

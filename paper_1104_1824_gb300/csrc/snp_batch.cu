@@ -118,6 +118,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     for (int32_t i = 0; i < n; ++i) {  // release older arenas before allocating
       hs[i]->batch.reset();
       hs[i]->result_pool = nullptr;
+      hs[i]->result_perm = nullptr;
       hs[i]->explored = false;
     }
   }
@@ -249,6 +250,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     h->have_parents = false;
     h->batch = arena;
     h->result_pool = b.pool;
+    h->result_perm = nullptr;
     int code = SNP_OK;
     if (b.error & kErrOverflow) code = SNP_E_OVERFLOW;
     else if (b.error & kErrTimeout) code = SNP_E_TIMEOUT;
@@ -302,6 +304,7 @@ extern "C" int snp_batch_autotune(snp_handle* hs, int32_t n, const snp_explore_o
   for (int32_t i = 0; i < n; ++i) {
     hs[i]->batch.reset();
     hs[i]->result_pool = nullptr;
+    hs[i]->result_perm = nullptr;
     hs[i]->explored = false;
   }
   return SNP_OK;

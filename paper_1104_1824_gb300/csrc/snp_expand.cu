@@ -273,18 +273,27 @@ __device__ __forceinline__ void stage_row_lane(const int32_t* row, int32_t* dst,
 // Step (d) for one candidate, by one lane, without waiting on any other lane:
 // returns false when the key may sit in a slot that another lane or warp has
 // reserved but not yet published; the caller then tries again in a later pass.
+constexpr int kRetry = 0, kDone = 1, kOwner = 2;
+
+// Frontier row p of the chunk (through the store's row map when there is one).
+__device__ __forceinline__ const int32_t* parent_row(const ClaimArgs& a, int64_t p) {
+  return a.parents + (size_t)(a.pperm ? __ldg(a.pperm + p) : (uint64_t)p) * a.sys.m;
+}
+
 template <bool VEC>
-__device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid) {
+__device__ __forceinline__ int resolve_lane(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
+                                            unsigned long long*& owned) {
   // A bucket fills as a prefix (a slot is claimed only when every earlier
   // slot was seen taken, and slots never become empty again), so the slots
   // holding our fingerprint all precede the first empty one.  Each bucket is
-  // classified branch-free; the compare, the claim and the owner's work then
-  // run once per lane, which keeps lanes that hit different slots together.
+  // classified branch-free; the compare and the claim then run once per lane,
+  // which keeps lanes that hit different slots together.  Returns kOwner with
+  // the reserved slot in `owned`; the caller does the owner's work.
   const int m = a.sys.m;
   const uint32_t fp = fp32_of(key);
   const unsigned long long mine = ((unsigned long long)fp << 32) | kRowReserved;
   uint64_t bucket = key & a.table.bmask;
-  unsigned long long* owned = nullptr;
+  owned = nullptr;
   for (uint64_t probes = 0; probes <= a.table.bmask && !owned;) {
     unsigned long long* bs = a.table.slots + bucket * kBucket;
     const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(bs);
@@ -301,17 +310,18 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
       const int j = __ffs(match) - 1;
       const unsigned long long x = __ldcg(bs + j);
       const uint32_t rf = (uint32_t)x;
-      if (rf == kRowReserved) return false;  // published soon: try again later
+      if (rf == kRowReserved) return kRetry;  // published soon: try again later
       const int32_t* other;
       if (rf & kPending) {
-        (void)ld_acquire(bs + j);  // orders the staged row's reads after the publish
-        other = a.staging + (size_t)(rf & ~kPending) * m;
+        (void)ld_acquire(bs + j);  // orders the reads of the owner's row and records after the publish
+        const uint32_t o = rf & ~kPending;
+        other = a.store_ctr ? a.pool + (size_t)__ldcg(a.sidx_of + o) * m : a.staging + (size_t)o * m;
       } else {
         other = a.pool + (size_t)rf * m;
       }
       if (row_equal_lane<VEC>(row, other, m)) {
         if (rf & kPending) atomicMin(a.gmin + (rf & ~kPending), lid);
-        return true;
+        return kDone;
       }
     }
     if (empty) {
@@ -324,15 +334,31 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
   }
   if (!owned) {
     atomicOr(&a.st->error, kErrTableFull);
-    return true;
+    return kDone;
   }
-  // owner: stage, record, publish
-  stage_row_lane<VEC>(row, a.staging + (size_t)lid * m, m);
+  return kOwner;
+}
+
+// The owner's work: its row to staging row lid, or in store mode to store
+// row sidx (recorded in sidx_of), the claim records, then the publish.
+template <bool VEC>
+__device__ __forceinline__ void finish_owner(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
+                                             unsigned long long* owned, uint64_t sidx) {
+  const int m = a.sys.m;
+  if (a.store_ctr) {
+    if (sidx >= a.store_cap) {  // the host sizes the store for every claim of the chunk
+      atomicOr(&a.st->error, kErrStaging);
+      return;
+    }
+    stage_row_lane<VEC>(row, a.pool + (size_t)sidx * m, m);
+    a.sidx_of[lid] = (uint32_t)sidx;
+  } else {
+    stage_row_lane<VEC>(row, a.staging + (size_t)lid * m, m);
+  }
   a.gmin[lid] = lid;
   a.slot_of[lid] = (uint32_t)(owned - a.table.slots);
   atomicOr(a.ownbits + (lid >> 5), 1u << (lid & 31));
-  st_release(owned, ((unsigned long long)fp << 32) | (kPending | lid));
-  return true;
+  st_release(owned, ((unsigned long long)fp32_of(key) << 32) | (kPending | lid));
 }
 
 // Step (d) for one row per lane (lanes with todo set): passes until every
@@ -343,8 +369,22 @@ __device__ __forceinline__ bool resolve_lane(const ClaimArgs& a, const int32_t* 
 template <bool VEC>
 __device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                                   bool todo) {
+  const int lane = threadIdx.x & 31;
   for (int pass = 0;; ++pass) {
-    if (todo && resolve_lane<VEC>(a, row, key, lid)) todo = false;
+    unsigned long long* owned = nullptr;
+    const int status = todo ? resolve_lane<VEC>(a, row, key, lid, owned) : kDone;
+    uint64_t sidx = 0;
+    if (a.store_ctr) {  // the warp's owners take consecutive store rows with one atomic
+      const uint32_t ob = __ballot_sync(0xffffffffu, status == kOwner);
+      if (ob) {
+        const int leader = __ffs(ob) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.store_ctr, (unsigned long long)__popc(ob));
+        sidx = __shfl_sync(0xffffffffu, base, leader) + __popc(ob & ((1u << lane) - 1u));
+      }
+    }
+    if (status == kOwner) finish_owner<VEC>(a, row, key, lid, owned, sidx);
+    todo = status == kRetry;
     if (__all_sync(0xffffffffu, !todo)) break;
     if (pass >= kSpinLimit) {
       if (todo) atomicOr(&a.st->error, kErrTimeout);
@@ -463,7 +503,7 @@ __device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int n
     f.h = h;
   } else {
     uint64_t h = 0;
-    for_each_neuron_desc<VEC>(a.parents + (size_t)f.pc * s.m, s.m, [&](int n, int32_t x) {
+    for_each_neuron_desc<VEC>(parent_row(a, f.pc), s.m, [&](int n, int32_t x) {
       h += col_hash(s, n, x);
       const uint64_t am = appl(s, n, x);
       const uint32_t mask = (uint32_t)am;
@@ -483,7 +523,7 @@ __device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int n
 template <bool VEC, int KIND>
 __device__ __forceinline__ void flat_build(const ClaimArgs& a, int64_t pc, uint64_t t, int32_t* trow) {
   const DevSys& s = a.sys;
-  const int32_t* prow = a.parents + (size_t)pc * s.m;
+  const int32_t* prow = parent_row(a, pc);
   copy_row<VEC>(prow, trow, s.m);
   uint64_t q = t;
   for_each_neuron_desc<VEC>(prow, s.m, [&](int n, int32_t x) {
@@ -533,7 +573,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   const uint64_t g = a.g0 + l;
   const uint64_t gend = min(p_hi, a.g0 + lb);
   if (p != cached_p) {  // the warp's shared memory still holds the state of cached_p
-    after = parent_state(s, a.parents + (size_t)p * m, w, B, lane);
+    after = parent_state(s, parent_row(a, p), w, B, lane);
     cached_p = p;
   }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
@@ -708,7 +748,13 @@ __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t
     bool done = lid >= a.Q || redundant[lid];
     const uint64_t key = done ? 0ull : mix64(hash[lid]);
     for (int pass = 0;; ++pass) {
-      if (!done) done = resolve_lane<VEC>(a, rows + lid * m, key, (uint32_t)lid);
+      if (!done) {
+        unsigned long long* owned = nullptr;
+        const int status = resolve_lane<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned);
+        if (status == kOwner)
+          finish_owner<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned, a.store_ctr ? atomicAdd(a.store_ctr, 1ull) : 0ull);
+        done = status != kRetry;
+      }
       if (__all_sync(0xffffffffu, done)) break;
       if (pass >= kSpinLimit) {
         if (!done) atomicOr(&a.st->error, kErrTimeout);
@@ -930,6 +976,10 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       a.ownbits = sc.own;
       a.prec = nullptr;
       a.ctr = nullptr;
+      a.pperm = nullptr;
+      a.store_ctr = nullptr;
+      a.sidx_of = nullptr;
+      a.store_cap = 0;
       a.st = sc.st;
       if ((m & 3) == 0)
         expand_warp<true, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);

@@ -153,10 +153,12 @@ struct snp_system {
   uint64_t tc_cap = 0;  // candidates the tensor-core chunk buffers hold
   std::vector<unsigned long long> colkey, rowkey;
   // exploration state
-  DevBuf d_pool, d_slots, d_staging, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_off, d_scan_tmp, d_st,
+  DevBuf d_pool, d_slots, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_off, d_scan_tmp, d_st,
       d_rec_parent, d_rec_index, d_tmp,
-      d_psi, d_prec, d_ctr;
-  int64_t pool_rows = 0;  // capacity in rows
+      d_psi, d_prec, d_ctr, d_perm, d_sidx;
+  int64_t pool_rows = 0;  // capacity in rows (of the store: every row claimed during an exploration)
+  int64_t perm_rows = 0;  // capacity of perm (discovery index -> store row)
+  int64_t n_store = 0;    // store rows in use
   uint64_t nbuckets = 0;
   uint64_t q_cap = 0;     // staging capacity in rows
   int64_t psi_cap = 0;    // parents
@@ -174,6 +176,7 @@ struct snp_system {
   // After snp_explore_batch the configurations live in a shared batch arena.
   std::shared_ptr<snp::BatchArena> batch;
   const int32_t* result_pool = nullptr;  // rows snp_reachable reads (d_pool or the arena)
+  const uint32_t* result_perm = nullptr;  // row k of the result is result_pool row result_perm[k] (or k)
 
   snp::DevSys dev() const {
     snp::DevSys s;

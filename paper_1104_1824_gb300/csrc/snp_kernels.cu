@@ -84,12 +84,12 @@ struct PsiAcc {
 // rows' ParentRecs when rec is given; rows not to be expanded (max_expand)
 // get Psi = 0, rows whose children could leave int32 raise kErrOverflow.
 template <bool VEC, bool REC>
-__global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand,
-                                             uint64_t* psi, ParentRec* rec, ChunkState* st) {
+__global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
+                                             int32_t max_expand, uint64_t* psi, ParentRec* rec, ChunkState* st) {
   const int m = s.m;
   bool over = false;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t* row = rows + (size_t)p * m;
+    const int32_t* row = rows + (size_t)(perm ? __ldg(perm + p) : (uint64_t)p) * m;
     PsiAcc acc;
     for (int n0 = 0; n0 < m; n0 += 4) {
       int x4[4];
@@ -121,8 +121,9 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, int6
 // different banks.
 constexpr int kPsiRows = 256, kPsiSlab = 32;
 template <bool REC>
-__global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand,
-                                                        uint64_t* psi, ParentRec* rec, ChunkState* st) {
+__global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
+                                                        int32_t max_expand, uint64_t* psi, ParentRec* rec,
+                                                        ChunkState* st) {
   __shared__ int32_t slab[kPsiRows][kPsiSlab + 1];
   const int m = s.m;
   const int t = threadIdx.x;
@@ -137,7 +138,8 @@ __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t*
       __syncthreads();
       for (int i = t; i < nrows * q4; i += kPsiRows) {
         const int r = i / q4, q = i - r * q4;
-        const int4 v = __ldg(reinterpret_cast<const int4*>(rows + (size_t)(p0 + r) * m + n0) + q);
+        const uint64_t pr = perm ? __ldg(perm + p0 + r) : (uint64_t)(p0 + r);
+        const int4 v = __ldg(reinterpret_cast<const int4*>(rows + (size_t)pr * m + n0) + q);
         int32_t* d = &slab[r][4 * q];
         d[0] = v.x;
         d[1] = v.y;
@@ -160,8 +162,8 @@ __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t*
   if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
 }
 
-int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ParentRec* rec,
-               ChunkState* st, cudaStream_t stream, int nsm) {
+int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, int32_t max_expand, uint64_t* psi,
+               ParentRec* rec, ChunkState* st, cudaStream_t stream, int nsm) {
   const int threads = 256;
   const int64_t want = (P + threads - 1) / threads;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
@@ -169,11 +171,11 @@ int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uin
     const int64_t tiles = (P + kPsiRows - 1) / kPsiRows;
     const int tb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * 6));
     auto fn = rec ? k_psi_tiled<true> : k_psi_tiled<false>;
-    fn<<<tb, kPsiRows, 0, stream>>>(s, rows, P, max_expand, psi, rec, st);
+    fn<<<tb, kPsiRows, 0, stream>>>(s, rows, perm, P, max_expand, psi, rec, st);
     return 1;
   }
   auto fn = rec ? k_psi<false, true> : k_psi<false, false>;
-  fn<<<blocks, threads, 0, stream>>>(s, rows, P, max_expand, psi, rec, st);
+  fn<<<blocks, threads, 0, stream>>>(s, rows, perm, P, max_expand, psi, rec, st);
   return 1;
 }
 
@@ -235,10 +237,14 @@ __device__ __forceinline__ void commit_one(const CommitArgs& a, uint32_t lid, ui
     return;
   }
   const int64_t row = row_base + (int64_t)rank;
-  const int32_t* src = a.staging + (size_t)s * m;
-  int32_t* dst = a.pool + (size_t)row * m;
-  copy_row_cg(src, dst, m);
-  *slot = hi | (uint32_t)row;
+  if (a.perm) {  // store mode: the row stays where its owner put it
+    const uint32_t sr = a.sidx_of[s];
+    a.perm[row] = sr;
+    *slot = hi | sr;
+  } else {
+    copy_row_cg(a.staging + (size_t)s * m, a.pool + (size_t)row * m, m);
+    *slot = hi | (uint32_t)row;
+  }
   if (rank + 1 == remaining) {
     a.st->capped = 1;
     a.st->last_lid = lid;
@@ -300,6 +306,29 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
   }
 }
 
+// out[k] = pool[perm[k]] for k < n, one warp per row (16-byte pieces when
+// m % 4 == 0).
+__global__ void k_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += nw) {
+    const int32_t* src = pool + (size_t)__ldg(perm + k) * m;
+    int32_t* dst = out + (size_t)k * m;
+    if ((m & 3) == 0) {
+      const int4* s4 = reinterpret_cast<const int4*>(src);
+      int4* d4 = reinterpret_cast<int4*>(dst);
+      for (int j = lane; j < (m >> 2); j += 32) d4[j] = __ldg(s4 + j);
+    } else {
+      for (int j = lane; j < m; j += 32) dst[j] = __ldg(src + j);
+    }
+  }
+}
+
+void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 64));
+  k_gather_rows<<<blocks, 256, 0, st>>>(pool, perm, n, m, out);
+}
+
 // Clears the first-occurrence bitmap; with ctr, one thread then moves the
 // device counters past the chunk's accepted configurations.
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st) {
@@ -314,15 +343,17 @@ __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long
 
 // Inserts committed rows [r0, r1) (all distinct) into an empty or partly
 // filled table: used for C0 and to rebuild the table when it grows.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_insert_rows(DevSys s, const int32_t* pool, int64_t r0,
-                                                                     int64_t r1, DevTable t, ChunkState* st) {
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_insert_rows(DevSys s, const int32_t* pool,
+                                                                     const uint32_t* perm, int64_t r0, int64_t r1,
+                                                                     DevTable t, ChunkState* st) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t r = r0 + (int64_t)blockIdx.x * kWarpsPerBlock + wib; r < r1; r += nw) {
-    const int32_t* row = pool + (size_t)r * s.m;
+    const uint32_t sr = perm ? __ldg(perm + r) : (uint32_t)r;  // the row's place in the pool (the store)
+    const int32_t* row = pool + (size_t)sr * s.m;
     const uint64_t h = fingerprint(s, row, lane);
     if (lane == 0) {
-      const unsigned long long val = ((unsigned long long)fp32_of(h) << 32) | (uint32_t)r;
+      const unsigned long long val = ((unsigned long long)fp32_of(h) << 32) | sr;
       uint64_t b = h & t.bmask;
       bool done = false;
       for (uint64_t probes = 0; probes <= t.bmask && !done; ++probes, b = (b + 1) & t.bmask) {

@@ -8,15 +8,21 @@ namespace snp {
 
 struct ClaimArgs {
   DevSys sys;
-  const int32_t* parents;     // frontier rows, contiguous [P x m]
+  const int32_t* parents;     // frontier rows: parents + pperm[p] * m, or parents + p * m without pperm
+  const uint32_t* pperm;      // [P] store rows of the frontier, or nullptr
   const uint64_t* off;        // [P + 1] exclusive prefix sums of Psi (saturating)
   int64_t P;
   uint64_t g0;                // first candidate of the chunk
   uint32_t Q;                 // candidates in the chunk
   uint32_t run;               // consecutive candidates per warp task
   DevTable table;
-  const int32_t* pool;        // committed configurations
+  int32_t* pool;              // committed configurations (store mode: every claimed row, in claim order)
   int32_t* staging;           // [Q x m] row lid = candidate lid's configuration if lid claimed a new key
+  // Store mode (store_ctr set): an owner takes the next row of the store
+  // (pool) instead of staging row lid, and records it in sidx_of[lid].
+  unsigned long long* store_ctr;
+  uint32_t* sidx_of;          // [Q]
+  uint64_t store_cap;         // rows the store holds
   uint32_t* gmin;             // [Q] per claiming lid: smallest chunk-local candidate holding its key
   uint32_t* slot_of;          // [Q] per claiming lid: its table slot
   uint32_t* ownbits;          // [Q / 32 + 1] bit lid set iff candidate lid claimed a new key
@@ -35,6 +41,10 @@ struct CommitArgs {
   const int32_t* staging;
   DevTable table;
   int32_t* pool;
+  // Store mode (perm set): rows stay where their owners stored them;
+  // perm[row] = sidx_of[owner] records the store row of discovery index row.
+  uint32_t* perm;
+  const uint32_t* sidx_of;
   int64_t row_base;           // pool row of rank 0
   uint64_t remaining;         // how many more configurations the depth may accept
   const unsigned long long* ctr;  // or, when set, both from device counters {rows, still acceptable}
@@ -102,7 +112,8 @@ void launch_batch_depth(const BatchArgs& a, int blocks, int warps, cudaStream_t 
 __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n);
 
 // Step (a) and Psi for P frontier rows; returns the launches made.
-int launch_psi(DevSys s, const int32_t* rows, int64_t P, int32_t max_expand, uint64_t* psi, ParentRec* rec, ChunkState* st,
+int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, int32_t max_expand, uint64_t* psi,
+               ParentRec* rec, ChunkState* st,
                cudaStream_t stream, int nsm);
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
@@ -111,7 +122,8 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
 void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long long* hash, const uint8_t* redundant,
                          cudaStream_t st, int nsm);
 // Tensor-core form of step (c) (snp_tc.cu).
-void launch_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P, uint64_t g0, uint32_t Q,
+void launch_tc_digits(DevSys s, const int32_t* parents, const uint32_t* perm, const uint64_t* off, int64_t P,
+                      uint64_t g0, uint32_t Q,
                       uint8_t* loc, int mp, uint32_t* pidx, uint8_t* redundant, cudaStream_t st, int nsm);
 void launch_tc_rows(DevSys s, const int32_t* parents, const uint8_t* loc, int mp, const uint32_t* pidx, uint32_t Q,
                     const int8_t* MT, int Rp, const int16_t* rn, const uint8_t* rk, int32_t* rows,
@@ -120,8 +132,10 @@ size_t tc_rows_smem(int mp);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);
+void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out, cudaStream_t st);
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st);
-__global__ void k_insert_rows(DevSys s, const int32_t* pool, int64_t r0, int64_t r1, DevTable t, ChunkState* st);
+__global__ void k_insert_rows(DevSys s, const int32_t* pool, const uint32_t* perm, int64_t r0, int64_t r1, DevTable t,
+                              ChunkState* st);
 __global__ void k_step_children(DevSys s, const int32_t* C, uint64_t n, int32_t* out);
 __global__ void k_fill_u64(unsigned long long* p, uint64_t n, unsigned long long v);
 

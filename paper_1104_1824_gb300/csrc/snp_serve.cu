@@ -205,6 +205,7 @@ int retire(snp_server* S, Request* r) {
   h->have_parents = false;
   h->batch.reset();
   h->result_pool = h->d_pool.as<int32_t>();
+  h->result_perm = nullptr;
   r->status = (b.error & kErrOverflow) ? SNP_E_OVERFLOW
               : (b.error & kErrTimeout) ? SNP_E_TIMEOUT
               : b.error ? SNP_E_INTERNAL : SNP_OK;
@@ -410,6 +411,7 @@ int snp_server_submit(void* srv, snp_handle h, const snp_explore_opts* o, uint64
   h->explored = false;
   h->batch.reset();
   h->result_pool = nullptr;
+  h->result_perm = nullptr;
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->loop_error != SNP_OK) {

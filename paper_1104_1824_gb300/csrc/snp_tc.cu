@@ -34,9 +34,11 @@ __device__ __forceinline__ void mma_s8(int (&c)[4], uint32_t a0, uint32_t a1, ui
 
 }  // namespace
 
-// Step (b) for the chunk: per candidate its parent (frontier index) and, per
-// neuron, the position of the chosen rule among the neuron's rules.
-__global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P,
+// Step (b) for the chunk: per candidate its parent's row (perm[p] when the
+// frontier is reached through a row map, else p) and, per neuron, the
+// position of the chosen rule among the neuron's rules.
+__global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* parents, const uint32_t* perm,
+                                                   const uint64_t* off, int64_t P,
                                                    uint64_t g0, uint32_t Q, uint8_t* loc, int mp, uint32_t* pidx,
                                                    uint8_t* redundant) {
   extern __shared__ int32_t smem[];
@@ -53,7 +55,8 @@ __global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* pare
     const uint64_t la = task * run, lb = min(la + run, (uint64_t)Q);
     int64_t p = warp_find_parent(off, P, g0 + la, lane);
     uint64_t p_lo = __ldg(off + p), p_hi = __ldg(off + p + 1);
-    load_parent(s, parents + (size_t)p * m, w, lane);
+    uint32_t prow = perm ? __ldg(perm + p) : (uint32_t)p;
+    load_parent(s, parents + (size_t)prow * m, w, lane);
     for (uint64_t l = la; l < lb; ++l) {
       const uint64_t g = g0 + l;
       if (g >= p_hi) {
@@ -62,7 +65,8 @@ __global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* pare
           p_lo = p_hi;
           p_hi = __ldg(off + p + 1);
         } while (g >= p_hi);
-        load_parent(s, parents + (size_t)p * m, w, lane);
+        prow = perm ? __ldg(perm + p) : (uint32_t)p;
+        load_parent(s, parents + (size_t)prow * m, w, lane);
       }
       const uint64_t t = g - p_lo;
       const int n0 = lane * s.K, n1 = min(n0 + s.K, m);
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(128) k_tc_digits(DevSys s, const int32_t* pare
       }
       red = __any_sync(0xffffffffu, red);
       if (lane == 0) {
-        pidx[l] = (uint32_t)p;
+        pidx[l] = prow;
         redundant[l] = red ? 1 : 0;
       }
       __syncwarp();
@@ -206,12 +210,13 @@ __global__ void __launch_bounds__(128) k_tc_peak(int iters, int* out) {
   out[blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
 
-void launch_tc_digits(DevSys s, const int32_t* parents, const uint64_t* off, int64_t P, uint64_t g0, uint32_t Q,
+void launch_tc_digits(DevSys s, const int32_t* parents, const uint32_t* perm, const uint64_t* off, int64_t P,
+                      uint64_t g0, uint32_t Q,
                       uint8_t* loc, int mp, uint32_t* pidx, uint8_t* redundant, cudaStream_t st, int nsm) {
   const size_t smem = (size_t)4 * 2 * s.m * sizeof(int32_t);
   const uint64_t ntasks = ((uint64_t)Q + 31) / 32;
   const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((ntasks + 3) / 4, (uint64_t)nsm * 16));
-  k_tc_digits<<<blocks, 128, smem, st>>>(s, parents, off, P, g0, Q, loc, mp, pidx, redundant);
+  k_tc_digits<<<blocks, 128, smem, st>>>(s, parents, perm, off, P, g0, Q, loc, mp, pidx, redundant);
 }
 
 size_t tc_rows_smem(int mp) { return (size_t)kTcBM * mp + kTcBM * kTcAStride + kTcBM * sizeof(int32_t); }
