@@ -448,7 +448,9 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     h->perm_rows = rows_plan;
   }
   {
-    const int64_t store_plan = (int64_t)std::min<uint64_t>(0x7FFFFFF0ull, (uint64_t)rows_plan + qmax);
+    // claims past the cap come from the pass that reaches it: one pass per depth
+    const long double extra = (long double)qmax * (cap > 0 ? (long double)std::max(o->depth, 1) : 1.0L);
+    const int64_t store_plan = (int64_t)std::min<long double>(2147483632.0L, (long double)rows_plan + extra);
     if (h->pool_rows < store_plan) {
       TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * store_plan));
       h->pool_rows = store_plan;
@@ -621,8 +623,9 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
           }
         }
         if (store_hi > (uint64_t)h->pool_rows) {
-          const int64_t want =
-              (int64_t)std::min<uint64_t>(0x7FFFFFF0ull, std::max<uint64_t>(2ull * h->pool_rows, store_hi));
+          // uncapped: double; capped (the plan was exact up to one pass per depth): a few passes more
+          const uint64_t grow = cap > 0 ? store_hi + 2 * qmax : std::max<uint64_t>(2ull * h->pool_rows, store_hi);
+          const int64_t want = (int64_t)std::min<uint64_t>(0x7FFFFFF0ull, grow);
           TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
           h->pool_rows = want;
           parents = h->d_pool.as<int32_t>();
