@@ -83,7 +83,8 @@ struct PsiAcc {
 // Step (a) and Eq. psi for every frontier row, one lane per row, with the
 // rows' ParentRecs when rec is given; rows not to be expanded (max_expand)
 // get Psi = 0, rows whose children could leave int32 raise kErrOverflow.
-template <bool VEC, bool REC>
+// (Rows of m % 4 == 0 neurons go through k_psi_tiled instead.)
+template <bool REC>
 __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
                                              int32_t max_expand, uint64_t* psi, ParentRec* rec, ChunkState* st) {
   const int m = s.m;
@@ -91,19 +92,7 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, cons
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t* row = rows + (size_t)(perm ? __ldg(perm + p) : (uint64_t)p) * m;
     PsiAcc acc;
-    for (int n0 = 0; n0 < m; n0 += 4) {
-      int x4[4];
-      if (VEC) {
-        const int4 v = __ldg(reinterpret_cast<const int4*>(row + n0));
-        x4[0] = v.x, x4[1] = v.y, x4[2] = v.z, x4[3] = v.w;
-      } else {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) x4[u] = (n0 + u < m) ? __ldg(row + n0 + u) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (n0 + u < m) acc.visit<REC>(s, n0 + u, x4[u], max_expand, REC ? rec + p : nullptr);
-    }
+    for (int n = 0; n < m; ++n) acc.visit<REC>(s, n, __ldg(row + n), max_expand, REC ? rec + p : nullptr);
     psi[p] = acc.psi();
     if (REC) {
       rec[p].hbase = acc.hb;
@@ -174,7 +163,7 @@ int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, i
     fn<<<tb, kPsiRows, 0, stream>>>(s, rows, perm, P, max_expand, psi, rec, st);
     return 1;
   }
-  auto fn = rec ? k_psi<false, true> : k_psi<false, false>;
+  auto fn = rec ? k_psi<true> : k_psi<false>;
   fn<<<blocks, threads, 0, stream>>>(s, rows, perm, P, max_expand, psi, rec, st);
   return 1;
 }

@@ -418,3 +418,22 @@ def test_explore_from_large_spike_counts(gpu):
         e = oracle.Oracle(system).explore(4, cap=3000, budget=40000)
         assert (s.reachable() == e.configs).all()
         assert [x.examined for x in s.depth_stats()] == [x.examined for x in e.depths]
+
+
+@pytest.mark.parametrize("chunk", [0, 4096])
+def test_uncapped_growth_rebuilds_the_table(gpu, chunk):
+    """No cap and no budget: the store, the row map and the hash table all
+    grow during the run (the table is rebuilt from the rows found so far,
+    through the row map); small passes keep two in flight most of the time."""
+    system = snp_synth.random_system(8, 12, (2, 3), (2, 4), (0, 6), "sparse")
+    s = gpu.System(system)
+    s.explore(3, chunk=chunk, record_parents=True)
+    e = oracle.Oracle(system).explore(3)
+    got = s.reachable()
+    assert got.shape[0] == 159140  # well past the first table (sized for 4096 + 65536 rows)
+    assert (got == e.configs).all()
+    assert [(x.new, x.examined) for x in s.depth_stats()] == [(x.new, x.examined) for x in e.depths]
+    parent, index = s.parents()
+    o = oracle.Oracle(system)
+    for k in range(1, got.shape[0], 4999):  # each row is the index-th child of its parent
+        assert (o.child(got[parent[k]], int(index[k])) == got[k]).all()
