@@ -72,6 +72,14 @@ typedef struct snp_system* snp_handle;
  *               entry on a rule's own neuron is -c (c >= 1 spikes consumed);
  *               every other entry is >= 0 (spikes received).
  *  c0           [m] initial configuration C0, entries >= 0.
+ *  rule_terms,  optional (NULL: every rule is the single term rule_i, rule_j):
+ *  term_i,      general regular expressions, the paper's future work (Section
+ *  term_j       6), read as finite unions of terms a^i (a^j)*.  Rule r's
+ *               expression is the union of a^term_i[t] (a^term_j[t])* over
+ *               t in [rule_terms[r], rule_terms[r + 1]); rule_terms is [R + 1]
+ *               with rule_terms[0] = 0, every rule has 1 to 64 terms, and
+ *               term_i, term_j >= 0.  rule_i and rule_j are then ignored (may
+ *               be NULL).
  * A rule is applicable to a neuron holding x spikes iff a^x is in L(E) and
  * x >= c (Section 2.1, rule (b-1)). */
 typedef struct {
@@ -82,6 +90,9 @@ typedef struct {
   const int32_t* rule_j;
   const int32_t* M;
   const int32_t* c0;
+  const int32_t* rule_terms;
+  const int32_t* term_i;
+  const int32_t* term_j;
 } snp_system_desc;
 
 /* Options of snp_explore.  Fill with snp_explore_opts_init first.

@@ -45,6 +45,8 @@ def _load(path: Optional[str] = None):
     lib = ctypes.CDLL(path)
     lib.orc_system_create.restype = ctypes.c_void_p
     lib.orc_system_create.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
+    lib.orc_system_create_terms.restype = ctypes.c_void_p
+    lib.orc_system_create_terms.argtypes = [ctypes.c_int32, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p, _i32p]
     lib.orc_system_free.argtypes = [ctypes.c_void_p]
     lib.orc_applicable.argtypes = [ctypes.c_void_p, _i32p, _u8p]
     lib.orc_psi.restype = ctypes.c_uint64
@@ -104,9 +106,14 @@ class Oracle:
         self.lib = _load(lib_path)
         self.m = int(system.m)
         self.R = int(system.R)
-        self._keep = [np.ascontiguousarray(x, dtype=np.int32) for x in
-                      (system.rule_neuron, system.rule_i, system.rule_j, system.M.reshape(-1))]
-        self.h = self.lib.orc_system_create(self.m, self.R, *[_p32(x) for x in self._keep])
+        if getattr(system, "terms", None) is not None:  # general rules: unions of terms
+            self._keep = [np.ascontiguousarray(x, dtype=np.int32) for x in
+                          (system.rule_neuron, *system.term_arrays(), system.M.reshape(-1))]
+            self.h = self.lib.orc_system_create_terms(self.m, self.R, *[_p32(x) for x in self._keep])
+        else:
+            self._keep = [np.ascontiguousarray(x, dtype=np.int32) for x in
+                          (system.rule_neuron, system.rule_i, system.rule_j, system.M.reshape(-1))]
+            self.h = self.lib.orc_system_create(self.m, self.R, *[_p32(x) for x in self._keep])
         self.c0 = np.ascontiguousarray(system.c0, dtype=np.int32)
 
     def __del__(self):

@@ -14,6 +14,9 @@
 //    L(E) and x >= c (Section 2.1, rules (b-1)/(b-3)).  The paper's own rules
 //    "a^k -> a" are E = a^k (a)*, i.e. "at least k spikes"; that is the only
 //    reading that reproduces the printed run.
+//  * General regular expressions (the paper's future work, Section 6) are
+//    read as finite unions of such terms: a^x is in L(E) iff it is in the
+//    language of at least one term.
 //  * A neuron with no applicable rule does not fire: it contributes one
 //    choice, the all-zero block, to the spiking vectors (Eq. psi with
 //    max(1, |sigma_V|)).
@@ -46,7 +49,9 @@ namespace {
 
 struct System {
   int32_t m = 0, R = 0;
-  std::vector<int32_t> rule_neuron, rule_i, rule_j;
+  std::vector<int32_t> rule_neuron;
+  std::vector<int32_t> rule_terms;      // [R + 1]: rule r's terms are [rule_terms[r], rule_terms[r + 1])
+  std::vector<int32_t> term_i, term_j;  // term t is a^term_i[t] (a^term_j[t])*
   std::vector<int32_t> M;  // R x m, row-major: rows are rules, columns neurons
 };
 
@@ -97,10 +102,17 @@ bool in_language(int64_t x, int32_t i, int32_t j) {
   return (x - i) % j == 0;
 }
 
+// Is a^x in L(E) for rule r's expression E, the union of its terms?
+bool in_rule_language(const System& s, int64_t x, int r) {
+  for (int t = s.rule_terms[r]; t < s.rule_terms[r + 1]; ++t)
+    if (in_language(x, s.term_i[t], s.term_j[t])) return true;
+  return false;
+}
+
 // Algorithm 2, II-1: rule r is applicable to configuration C.
 bool applicable(const System& s, const int32_t* C, int r) {
   int64_t x = C[s.rule_neuron[r]];
-  return in_language(x, s.rule_i[r], s.rule_j[r]) && x >= consumed(s, r);
+  return in_rule_language(s, x, r) && x >= consumed(s, r);
 }
 
 // Algorithm 2, II-2: per neuron, the applicable rules in rule order; an empty
@@ -165,14 +177,32 @@ bool exceeds(const int32_t* C, int m, int32_t max_expand) {
 
 extern "C" {
 
+// Rules of the paper's form: one term a^rule_i[r] (a^rule_j[r])* per rule.
 void* orc_system_create(int32_t m, int32_t R, const int32_t* rule_neuron, const int32_t* rule_i,
                         const int32_t* rule_j, const int32_t* M) {
   System* s = new System;
   s->m = m;
   s->R = R;
   s->rule_neuron.assign(rule_neuron, rule_neuron + R);
-  s->rule_i.assign(rule_i, rule_i + R);
-  s->rule_j.assign(rule_j, rule_j + R);
+  s->rule_terms.resize(R + 1);
+  for (int r = 0; r <= R; ++r) s->rule_terms[r] = r;
+  s->term_i.assign(rule_i, rule_i + R);
+  s->term_j.assign(rule_j, rule_j + R);
+  s->M.assign(M, M + (size_t)R * m);
+  return s;
+}
+
+// General rules: rule r's expression is the union of the terms
+// [rule_terms[r], rule_terms[r + 1]).
+void* orc_system_create_terms(int32_t m, int32_t R, const int32_t* rule_neuron, const int32_t* rule_terms,
+                              const int32_t* term_i, const int32_t* term_j, const int32_t* M) {
+  System* s = new System;
+  s->m = m;
+  s->R = R;
+  s->rule_neuron.assign(rule_neuron, rule_neuron + R);
+  s->rule_terms.assign(rule_terms, rule_terms + R + 1);
+  s->term_i.assign(term_i, term_i + rule_terms[R]);
+  s->term_j.assign(term_j, term_j + rule_terms[R]);
   s->M.assign(M, M + (size_t)R * m);
   return s;
 }

@@ -55,7 +55,8 @@ class SnpError(RuntimeError):
 class snp_system_desc(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int32), ("R", ctypes.c_int32),
                 ("rule_neuron", ctypes.c_void_p), ("rule_i", ctypes.c_void_p), ("rule_j", ctypes.c_void_p),
-                ("M", ctypes.c_void_p), ("c0", ctypes.c_void_p)]
+                ("M", ctypes.c_void_p), ("c0", ctypes.c_void_p),
+                ("rule_terms", ctypes.c_void_p), ("term_i", ctypes.c_void_p), ("term_j", ctypes.c_void_p)]
 
 
 class snp_explore_opts(ctypes.Structure):
@@ -164,10 +165,13 @@ def snp_explore_opts_init() -> snp_explore_opts:
     return o
 
 
-def snp_load_system(m, rule_neuron, rule_i, rule_j, M, c0) -> ctypes.c_void_p:
+def snp_load_system(m, rule_neuron, rule_i, rule_j, M, c0, terms=None) -> ctypes.c_void_p:
+    """terms: optional (rule_terms, term_i, term_j) arrays of general (union) rule expressions."""
     lib = load_library()
     arrs = [np.ascontiguousarray(x, dtype=np.int32).reshape(-1) for x in (rule_neuron, rule_i, rule_j, M, c0)]
-    d = snp_system_desc(int(m), int(arrs[0].shape[0]), *[a.ctypes.data for a in arrs])
+    targs = [np.ascontiguousarray(x, dtype=np.int32).reshape(-1) for x in terms] if terms is not None else []
+    d = snp_system_desc(int(m), int(arrs[0].shape[0]), *[a.ctypes.data for a in arrs],
+                        *([a.ctypes.data for a in targs] if targs else [None, None, None]))
     h = ctypes.c_void_p()
     _check(lib.snp_load_system(ctypes.byref(d), ctypes.byref(h)))
     return h
@@ -327,7 +331,8 @@ class System:
     def __init__(self, system):
         self.m = int(system.m)
         self.R = int(system.R)
-        self.h = snp_load_system(self.m, system.rule_neuron, system.rule_i, system.rule_j, system.M, system.c0)
+        self.h = snp_load_system(self.m, system.rule_neuron, system.rule_i, system.rule_j, system.M, system.c0,
+                                 terms=system.term_arrays() if getattr(system, "terms", None) is not None else None)
         self.depth_reached = None
 
     def close(self):

@@ -128,8 +128,11 @@ int validate_desc(const snp_system_desc* d) {
   if (!d) return fail(SNP_E_INVALID, "desc is NULL");
   if (d->m < 1 || d->m > 1024) return fail(SNP_E_INVALID, "m = %d outside [1, 1024]", d->m);
   if (d->R < 1) return fail(SNP_E_INVALID, "R = %d < 1", d->R);
-  if (!d->rule_neuron || !d->rule_i || !d->rule_j || !d->M || !d->c0)
+  if (!d->rule_neuron || !d->M || !d->c0) return fail(SNP_E_INVALID, "NULL array in desc");
+  const bool terms = d->rule_terms != nullptr;
+  if (terms ? (!d->term_i || !d->term_j) : (!d->rule_i || !d->rule_j))
     return fail(SNP_E_INVALID, "NULL array in desc");
+  if (terms && d->rule_terms[0] != 0) return fail(SNP_E_INVALID, "rule_terms[0] = %d must be 0", d->rule_terms[0]);
   int per = 0;
   for (int r = 0; r < d->R; ++r) {
     const int n = d->rule_neuron[r];
@@ -138,8 +141,15 @@ int validate_desc(const snp_system_desc* d) {
       return fail(SNP_E_INVALID, "rule %d: rules must be grouped by neuron in increasing order", r);
     per = (r > 0 && n == d->rule_neuron[r - 1]) ? per + 1 : 1;
     if (per > 32) return fail(SNP_E_INVALID, "neuron %d has more than 32 rules", n);
-    if (d->rule_i[r] < 0 || d->rule_j[r] < 0)
+    if (terms) {
+      const int64_t k = (int64_t)d->rule_terms[r + 1] - d->rule_terms[r];
+      if (k < 1 || k > 64) return fail(SNP_E_INVALID, "rule %d: %lld terms, expected 1 to 64", r, (long long)k);
+      for (int t = d->rule_terms[r]; t < d->rule_terms[r + 1]; ++t)
+        if (d->term_i[t] < 0 || d->term_j[t] < 0)
+          return fail(SNP_E_INVALID, "rule %d: term a^%d(a^%d)* needs i, j >= 0", r, d->term_i[t], d->term_j[t]);
+    } else if (d->rule_i[r] < 0 || d->rule_j[r] < 0) {
       return fail(SNP_E_INVALID, "rule %d: regex a^%d(a^%d)* needs i, j >= 0", r, d->rule_i[r], d->rule_j[r]);
+    }
     for (int j = 0; j < d->m; ++j) {
       const int32_t v = d->M[(size_t)r * d->m + j];
       if (j == n && v > -1) return fail(SNP_E_INVALID, "rule %d: M[%d][%d] = %d must be -c with c >= 1", r, r, j, v);
@@ -187,8 +197,23 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
   h->c0.assign(d->c0, d->c0 + m);
   h->M.assign(d->M, d->M + (size_t)R * m);
   h->rule_neuron.assign(d->rule_neuron, d->rule_neuron + R);
-  h->rule_i.assign(d->rule_i, d->rule_i + R);
-  h->rule_j.assign(d->rule_j, d->rule_j + R);
+  // Rule expressions as unions of terms (one term per rule for the paper's form).
+  h->rterm.assign(R + 1, 0);
+  h->term.clear();
+  for (int r = 0; r < R; ++r) {
+    if (d->rule_terms) {
+      for (int t = d->rule_terms[r]; t < d->rule_terms[r + 1]; ++t) h->term.push_back(make_int2(d->term_i[t], d->term_j[t]));
+    } else {
+      h->term.push_back(make_int2(d->rule_i[r], d->rule_j[r]));
+    }
+    h->rterm[r + 1] = (int32_t)h->term.size();
+  }
+  h->rule_i.resize(R);
+  h->rule_j.resize(R);
+  for (int r = 0; r < R; ++r) {  // the first term, for the tensor-core maps and reports
+    h->rule_i[r] = h->term[h->rterm[r]].x;
+    h->rule_j[r] = h->term[h->rterm[r]].y;
+  }
   h->first_rule.assign(m + 1, 0);
   for (int r = 0; r < R; ++r) h->first_rule[d->rule_neuron[r] + 1]++;
   for (int n = 0; n < m; ++n) h->first_rule[n + 1] += h->first_rule[n];
@@ -196,7 +221,7 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
   h->rule.resize(R + 1);
   for (int r = 0; r < R; ++r) {
     const int32_t* row = &h->M[(size_t)r * m];
-    h->rule[r] = make_int4(d->rule_i[r], d->rule_j[r], -row[d->rule_neuron[r]], (int)h->csr.size());
+    h->rule[r] = make_int4(h->rule_i[r], h->rule_j[r], -row[d->rule_neuron[r]], (int)h->csr.size());
     for (int j = 0; j < m; ++j) {
       if (row[j] != 0) h->csr.push_back(make_int2(j, row[j]));
       h->max_abs_m = std::max(h->max_abs_m, std::abs(row[j]));
@@ -235,8 +260,8 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     for (int e = h->rule[r].w; e < h->rule[r + 1].w; ++e)
       h->rowkey[r] += (uint64_t)(int64_t)h->csr[e].y * h->colkey[h->csr[e].x];
   // Applicable rules by spike count.  Above T = 1 + the largest i or c of a
-  // neuron's rules, a^x in L(a^i (a^j)*) reduces to (x - i) mod j == 0 for the
-  // rules with j >= 1, so the entries repeat with period L = lcm of those j:
+  // neuron's rule terms, a^x in L(a^i (a^j)*) reduces to (x - i) mod j == 0 for
+  // the terms with j >= 1, so the entries repeat with period L = lcm of those j:
   // the table holds x = 0 .. T + L - 1.  Larger x fold onto T + (x - T) mod L
   // on the device, dividing by L as (v * magic) >> shift with
   // shift = 32 + ceil(log2 L) and magic = ceil(2^shift / L), exact for v < 2^31
@@ -250,10 +275,11 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     ni.colkey = h->colkey[n];
     const int r0 = h->first_rule[n], r1 = h->first_rule[n + 1];
     int64_t T = 1, L = 1;
-    for (int r = r0; r < r1 && L <= 64; ++r) {
-      T = std::max<int64_t>(T, 1 + std::max<int64_t>(h->rule[r].x, h->rule[r].z));
-      if (h->rule[r].y >= 1) L = std::lcm<int64_t>(L, h->rule[r].y);
-    }
+    for (int r = r0; r < r1 && L <= 64; ++r)
+      for (int t = h->rterm[r]; t < h->rterm[r + 1] && L <= 64; ++t) {
+        T = std::max<int64_t>(T, 1 + std::max<int64_t>(h->term[t].x, h->rule[r].z));
+        if (h->term[t].y >= 1) L = std::lcm<int64_t>(L, h->term[t].y);
+      }
     if (L > 64 || T + L > 256) continue;  // evaluated from the rules on the device
     uint32_t lg = 0;
     while ((1ll << lg) < L) ++lg;
@@ -264,7 +290,7 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     for (int32_t x = 0; x < T + L; ++x) {
       uint32_t mask = 0;
       for (int r = r0; r < r1; ++r)
-        if (rule_applies(x, h->rule[r])) mask |= 1u << (r - r0);
+        if (rule_applies(x, h->rule[r], h->rterm.data(), h->term.data(), r)) mask |= 1u << (r - r0);
       uint32_t keep = mask;
       for (int k = 0; k < r1 - r0; ++k)
         if (((mask >> k) & 1u) && (h->eqmask[r0 + k] & mask)) keep &= ~(1u << k);
@@ -303,7 +329,7 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
     for (int32_t x = 0; x < snp::kDirect; ++x) {
       uint32_t mask = 0;
       for (int r = h->first_rule[n]; r < h->first_rule[n + 1]; ++r)
-        if (rule_applies(x, h->rule[r])) mask |= 1u << (r - h->first_rule[n]);
+        if (rule_applies(x, h->rule[r], h->rterm.data(), h->term.data(), r)) mask |= 1u << (r - h->first_rule[n]);
       h->dmask[(size_t)n * snp::kDirect + x] = mask;
       h->dhx[(size_t)n * snp::kDirect + x] = (unsigned long long)x * h->colkey[n] +
                                              (mask ? h->rowkey[h->first_rule[n] + __builtin_ctz(mask)] : 0ull);
@@ -328,6 +354,8 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
       (rc = up(h->d_rdesc, h->rdesc.data(), sizeof(int4) * std::max(R, 1))) ||
       (rc = up(h->d_scol, h->scol.data(), sizeof(int32_t) * std::max<size_t>(h->scol.size(), 1))) ||
       (rc = up(h->d_rval, h->rval.data(), sizeof(int32_t) * std::max<size_t>(h->rval.size(), 1))) ||
+      (rc = up(h->d_rterm, h->rterm.data(), sizeof(int32_t) * (R + 1))) ||
+      (rc = up(h->d_term, h->term.data(), sizeof(int2) * h->term.size())) ||
       (rc = up(h->d_dhx, h->dhx.data(), sizeof(unsigned long long) * h->dhx.size())) ||
       (rc = h->d_st.reserve(sizeof(ChunkState) + 64))) {
     delete h;

@@ -55,6 +55,10 @@ struct DevSys {
   const int4* rdesc;
   const int32_t* scol;
   const int32_t* rval;
+  // Rule r's regular expression: the union of a^term[t].x (a^term[t].y)* over
+  // t in [rterm[r], rterm[r + 1]) (one term per rule for the paper's rules).
+  const int32_t* rterm;
+  const int2* term;
 };
 constexpr int kDirect = 64;
 
@@ -138,24 +142,34 @@ __device__ __forceinline__ uint64_t col_hash(const DevSys& s, int j, int32_t v) 
   return (uint64_t)(uint32_t)v * __ldg(s.colkey + j);
 }
 
-// a^x in L(a^i (a^j)*) and x >= c (Section 2.1, rule (b-1)).
-__host__ __device__ __forceinline__ bool rule_applies(int32_t x, int4 rp) {
-  if (x < rp.x || x < rp.z) return false;
-  if (rp.y == 0) return x == rp.x;
-  if (rp.y == 1) return true;
-  return ((x - rp.x) % rp.y) == 0;
+// a^x in L(a^i (a^j)*) (Section 2.1; j = 0: exactly a^i).
+__host__ __device__ __forceinline__ bool term_matches(int32_t x, int32_t i, int32_t j) {
+  if (x < i) return false;
+  if (j == 0) return x == i;
+  if (j == 1) return true;
+  return ((x - i) % j) == 0;
+}
+
+// Rule r applies to x spikes: x >= c (rule.z) and a^x is in the union of its
+// terms (Section 2.1, rule (b-1)).
+__host__ __device__ __forceinline__ bool rule_applies(int32_t x, int4 rule, const int32_t* rterm, const int2* term,
+                                                      int r) {
+  if (x < rule.z) return false;
+  for (int t = rterm[r]; t < rterm[r + 1]; ++t)
+    if (term_matches(x, term[t].x, term[t].y)) return true;
+  return false;
 }
 
 // Applicable rules of neuron n holding x spikes, from the rules themselves
-// (out of line, it is the rare path: it takes the four arrays it reads rather
-// than the whole system).
+// (out of line, it is the rare path: it takes the arrays it reads rather than
+// the whole system).
 static __device__ __noinline__ ApplEntry appl_rules(const int32_t* first_rule, const int4* rule,
-                                                   const uint32_t* eqmask, const unsigned long long* rowkey, int n,
-                                                   int32_t x) {
+                                                   const int32_t* rterm, const int2* term, const uint32_t* eqmask,
+                                                   const unsigned long long* rowkey, int n, int32_t x) {
   const int r0 = __ldg(first_rule + n), r1 = __ldg(first_rule + n + 1);
   uint32_t mask = 0;
   for (int r = r0; r < r1; ++r)
-    if (rule_applies(x, __ldg(rule + r))) mask |= 1u << (r - r0);
+    if (rule_applies(x, __ldg(rule + r), rterm, term, r)) mask |= 1u << (r - r0);
   uint32_t keep = mask;
   for (uint32_t b = mask; b; b &= b - 1) {
     const int k = __ffs(b) - 1;
@@ -191,7 +205,7 @@ __device__ __forceinline__ ApplEntry appl_entry(const DevSys& s, const NeuronInf
     r.hfirst = ((unsigned long long)e.w << 32) | e.z;
     return r;
   }
-  return appl_rules(s.first_rule, s.rule, s.eqmask, s.rowkey, n, x);
+  return appl_rules(s.first_rule, s.rule, s.rterm, s.term, s.eqmask, s.rowkey, n, x);
 }
 
 __device__ __forceinline__ NeuronInfo neuron_info(const DevSys& s, int n) {

@@ -138,7 +138,7 @@ struct snp_system {
   std::vector<int2> csr;
   // device copies of the system
   DevBuf d_first_rule, d_rule, d_csr, d_gain, d_colkey, d_rowkey, d_eqmask, d_ninfo, d_atab, d_dmask, d_dhx, d_rdesc,
-      d_scol, d_rval;
+      d_scol, d_rval, d_rterm, d_term;
   std::vector<uint32_t> eqmask;
   std::vector<snp::NeuronInfo> ninfo;       // per-neuron constants of the applicability scan
   std::vector<snp::ApplEntry> atab;         // applicable rules by spike count
@@ -147,6 +147,8 @@ struct snp_system {
   int32_t gain_small = 0;
   std::vector<int4> rdesc;                  // per rule: support offset, length, value offset, neuron
   std::vector<int32_t> scol, rval;          // neuron supports; rule values on them
+  std::vector<int32_t> rterm;               // [R + 1] terms of rule r: [rterm[r], rterm[r + 1])
+  std::vector<int2> term;                   // {i, j} of each term a^i (a^j)*
   // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
   DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash, d_red;
   int32_t Rp = 0, mp = 0, mt_rows = 0;
@@ -198,6 +200,8 @@ struct snp_system {
     s.rdesc = d_rdesc.as<int4>();
     s.scol = d_scol.as<int32_t>();
     s.rval = d_rval.as<int32_t>();
+    s.rterm = d_rterm.as<int32_t>();
+    s.term = d_term.as<int2>();
     return s;
   }
   snp::DevTable table() const { return snp::DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }

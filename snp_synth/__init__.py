@@ -99,17 +99,31 @@ class SnpSystem:
     M: np.ndarray            # int32 [R, m]  spiking transition matrix (Definition 2)
     name: str = ""
     meta: dict = field(default_factory=dict)
+    # General regular expressions (the paper's future work), read as unions of
+    # terms: rule r's expression is the union of a^i (a^j)* over terms[r]'s
+    # (i, j) pairs.  None: each rule is its single term (rule_i[r], rule_j[r]).
+    terms: Optional[List[List[Tuple[int, int]]]] = None
 
     @property
     def R(self) -> int:
         return int(self.rule_neuron.shape[0])
+
+    def term_arrays(self) -> Tuple[np.ndarray, np.ndarray, np.ndarray]:
+        """(rule_terms [R+1], term_i, term_j): rule r's terms are
+        [rule_terms[r], rule_terms[r+1])."""
+        terms = self.terms if self.terms is not None else [[(int(i), int(j))] for i, j in zip(self.rule_i, self.rule_j)]
+        ptr = np.zeros(self.R + 1, dtype=np.int32)
+        ptr[1:] = np.cumsum([len(t) for t in terms])
+        ti = np.array([i for t in terms for i, _ in t], dtype=np.int32)
+        tj = np.array([j for t in terms for _, j in t], dtype=np.int32)
+        return ptr, ti, tj
 
     def targets(self, s: int) -> np.ndarray:
         return self.syn_dst[self.syn_ptr[s]:self.syn_ptr[s + 1]]
 
 
 def make_system(m, rule_neuron, rule_i, rule_j, rule_c, rule_p, targets, c0,
-                name: str = "", meta: Optional[dict] = None) -> SnpSystem:
+                name: str = "", meta: Optional[dict] = None, terms=None) -> SnpSystem:
     """Assemble a system and lay out M_Pi entry by entry (Definition 2).
 
     targets: per-neuron lists of synapse targets, or a CSR pair (syn_ptr, syn_dst).
@@ -139,7 +153,8 @@ def make_system(m, rule_neuron, rule_i, rule_j, rule_c, rule_p, targets, c0,
     return SnpSystem(m=m, rule_neuron=rule_neuron, rule_i=np.asarray(rule_i, dtype=np.int32),
                      rule_j=np.asarray(rule_j, dtype=np.int32), rule_c=rule_c, rule_p=rule_p,
                      syn_ptr=syn_ptr, syn_dst=syn_dst, c0=np.asarray(c0, dtype=np.int32), M=M,
-                     name=name, meta=dict(meta or {}))
+                     name=name, meta=dict(meta or {}),
+                     terms=None if terms is None else [[(int(i), int(j)) for i, j in t] for t in terms])
 
 
 def paper_example(exact: bool = False) -> SnpSystem:

@@ -26,13 +26,23 @@ def in_language(x: int, i: int, j: int) -> bool:
     return _regex(i, j).fullmatch("a" * x) is not None
 
 
+def in_union_language(x: int, terms) -> bool:
+    """a^x in the union of the terms' languages, decided by one regex."""
+    pattern = "|".join(f"(?:a{{{i}}}(?:a{{{j}}})*)" for i, j in terms)
+    return re.fullmatch(f"(?:{pattern})", "a" * x) is not None
+
+
 def applicable(system, C) -> np.ndarray:
     ok = np.zeros(system.R, dtype=np.uint8)
     for r in range(system.R):
         n = int(system.rule_neuron[r])
         c = -int(system.M[r, n])
         x = int(C[n])
-        ok[r] = 1 if (in_language(x, int(system.rule_i[r]), int(system.rule_j[r])) and x >= c) else 0
+        if getattr(system, "terms", None) is not None:
+            member = in_union_language(x, system.terms[r])
+        else:
+            member = in_language(x, int(system.rule_i[r]), int(system.rule_j[r]))
+        ok[r] = 1 if (member and x >= c) else 0
     return ok
 
 
@@ -133,6 +143,19 @@ def bfs_canonical(system, depth: int, cap: int = 0, budget: int = 0) -> Tuple[Li
             break
         frontier = nxt
     return order, stats
+
+
+def tiny_union_system(rng: np.random.Generator, m_max: int = 4, r_max: int = 9, t_max: int = 3):
+    """tiny_system whose rules have 1..t_max terms a^i (a^j)* each (general rules)."""
+    import snp_synth
+    base = tiny_system(rng, m_max, r_max)
+    terms = [[(int(rng.integers(0, 6)), int(rng.integers(0, 5))) for _ in range(int(rng.integers(1, t_max + 1)))]
+             for _ in range(base.R)]
+    c = -base.M[np.arange(base.R), base.rule_neuron]
+    p = np.array([int(base.M[r].max()) if base.M[r].max() > 0 else 0 for r in range(base.R)])
+    targets = [base.targets(s).tolist() for s in range(base.m)]
+    return snp_synth.make_system(base.m, base.rule_neuron, [t[0][0] for t in terms], [t[0][1] for t in terms], c, p,
+                                 targets, base.c0, name="tiny-union", terms=terms)
 
 
 def tiny_system(rng: np.random.Generator, m_max: int = 4, r_max: int = 9):

@@ -437,3 +437,60 @@ def test_uncapped_growth_rebuilds_the_table(gpu, chunk):
     o = oracle.Oracle(system)
     for k in range(1, got.shape[0], 4999):  # each row is the index-th child of its parent
         assert (o.child(got[parent[k]], int(index[k])) == got[k]).all()
+
+
+# --- general rules: unions of terms a^i (a^j)* ---
+
+@pytest.mark.parametrize("cap,budget", [(0, 0), (3, 0), (0, 40)])
+def test_union_rule_systems(gpu, cap, budget):
+    rng = np.random.default_rng(5000 + 7 * cap + budget)
+    for _ in range(25):
+        system = bf.tiny_union_system(rng, m_max=4, r_max=8)
+        s, e = explore_both(gpu, system, 5, cap=cap, budget=budget)
+        assert_same(s, e)
+        o = oracle.Oracle(system)
+        for _ in range(3):
+            C = rng.integers(0, 14, size=system.m).astype(np.int32)
+            kids, psi = s.step(C)
+            assert psi == o.psi(C)
+            assert (kids == o.step(C)).all()
+
+
+def test_union_rules_at_large_spike_counts(gpu):
+    """Union rules whose tables fold (period lcm(4, 6) = 12), whose period is
+    too long for a table (lcm(7, 9, 11) = 693) or whose threshold is (a^400)."""
+    rules = [  # (neuron, terms, c, p)
+        (0, [(3, 4), (1, 6)], 1, 1), (0, [(2, 0), (9, 4)], 2, 1),
+        (1, [(1, 7), (2, 9), (3, 11)], 1, 2), (1, [(1, 1)], 1, 1),
+        (2, [(400, 0), (1, 2)], 1, 1), (2, [(401, 1)], 3, 1),
+    ]
+    terms = [t for _, t, _, _ in rules]
+    system = snp_synth.make_system(3, [r[0] for r in rules], [t[0][0] for t in terms], [t[0][1] for t in terms],
+                                   [r[2] for r in rules], [r[3] for r in rules], [[1, 2], [2, 0], [0, 1]],
+                                   [0, 0, 0], terms=terms)
+    s = gpu.System(system)
+    o = oracle.Oracle(system)
+    rng = np.random.default_rng(17)
+    for _ in range(300):
+        band = rng.integers(0, 3, size=3)
+        C = np.where(band == 0, rng.integers(0, 30, size=3),
+                     np.where(band == 1, rng.integers(380, 420, size=3), rng.integers(10**5, 10**7, size=3)))
+        C = C.astype(np.int32)
+        kids, psi = s.step(C)
+        assert psi == o.psi(C), C
+        assert (kids == o.step(C)).all(), C
+    system.c0[:] = [13, 400, 401]
+    s, e = explore_both(gpu, system, 6, cap=2000)
+    assert_same(s, e)
+
+
+def test_union_rules_in_the_batch_engine(gpu):
+    rng = np.random.default_rng(77)
+    systems = [bf.tiny_union_system(rng, m_max=4, r_max=8) for _ in range(30)]
+    handles = [gpu.System(x) for x in systems]
+    st = gpu.explore_batch(handles, 5, cap=64, budget=512)
+    assert (st == 0).all()
+    for h, x in zip(handles, systems):
+        e = oracle.Oracle(x).explore(5, cap=64, budget=512)
+        assert (h.reachable() == e.configs).all()
+        assert [(a.new, a.examined) for a in h.depth_stats()] == [(b.new, b.examined) for b in e.depths]

@@ -224,6 +224,42 @@ def test_truncation_matches_brute_force(cap, budget):
                 assert e.depths[d].examined == st["examined"]
 
 
+# --- general rules: unions of terms a^i (a^j)* ---
+
+def test_union_rule_applicability_by_hand():
+    """E = a^2 + a^5 (a^3)*, consuming 2: applicable at 2, 5, 8, 11, ... only."""
+    s = snp_synth.make_system(2, [0, 1], [2, 1], [0, 1], [2, 1], [1, 1], [[1], [0]], [0, 0],
+                              terms=[[(2, 0), (5, 3)], [(1, 1)]])
+    o = oracle.Oracle(s)
+    got = [x for x in range(20) if o.applicable(np.array([x, 0], dtype=np.int32))[0]]
+    assert got == [2, 5, 8, 11, 14, 17]
+
+
+def test_union_applicability_matches_regex():
+    rng = np.random.default_rng(41)
+    for _ in range(200):
+        s = bf.tiny_union_system(rng)
+        o = oracle.Oracle(s)
+        for _ in range(5):
+            C = rng.integers(0, 14, size=s.m).astype(np.int32)
+            assert (o.applicable(C) == bf.applicable(s, C)).all()
+
+
+def test_union_systems_match_brute_force():
+    rng = np.random.default_rng(43)
+    for _ in range(30):
+        s = bf.tiny_union_system(rng, m_max=3, r_max=6)
+        o = oracle.Oracle(s)
+        for _ in range(3):
+            C = rng.integers(0, 8, size=s.m)
+            want = bf.children_canonical(s, C)
+            assert o.psi(C) == len(want)
+            assert (o.step(C) == want).all()
+        order, stats = bf.bfs_canonical(s, 4, cap=5, budget=0)
+        e = o.explore(4, cap=5)
+        assert [tuple(int(x) for x in r) for r in e.configs] == order
+
+
 # --- closed forms and invariants ---
 
 def test_psi_saturates():
