@@ -187,6 +187,22 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
  * SNP_E_INTERNAL, SNP_E_CUDA. */
 int snp_explore(snp_handle h, const snp_explore_opts* opts, int32_t* depth_reached, int32_t* truncated_flags);
 
+/* Resumes an exploration from a checkpoint taken at a depth boundary: the
+ * configurations found so far in discovery order (snp_reachable) and the
+ * per-depth records (snp_depth_stats, depth 0 first).  The paper has no
+ * counterpart (it keeps no state between runs); because the exploration order
+ * is canonical and the hash table holds exactly the configurations found,
+ * rebuilding the table from the rows and continuing the breadth-first search
+ * from depth nstats to opts->depth gives the same result as one exploration
+ * to opts->depth with the same options.
+ *  rows   [n * m] host or device, n = the sum of stats[d].new_configs.
+ *  stats  [nstats] host, nstats >= 1 (stats[0] is C0's record).
+ * The previous exploration of h, if any, is discarded; opts as for
+ * snp_explore (record_parents must be 0), opts->depth >= nstats - 1.
+ * Errors: as snp_explore; SNP_E_INVALID also for an inconsistent checkpoint. */
+int snp_explore_resume(snp_handle h, const int32_t* rows, int64_t n, const snp_depth_info* stats, int32_t nstats,
+                       const snp_explore_opts* opts, int32_t* depth_reached, int32_t* truncated_flags);
+
 /* Every configuration found by the last snp_explore, C0 first, in discovery
  * order (depth by depth, each depth in canonical candidate order), into
  * out[capacity * m] (host or device).  *n receives the count.  With

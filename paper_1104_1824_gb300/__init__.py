@@ -42,6 +42,7 @@ ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOME
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
            "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
+           "snp_explore_resume",
            "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune", "snp_server_create",
            "snp_server_submit", "snp_server_poll", "snp_server_wait", "snp_server_stats", "snp_server_destroy"]
 
@@ -190,6 +191,21 @@ def snp_step(h, C, capacity: int, out) -> int:
 def snp_explore(h, opts: snp_explore_opts, truncated_flags: Optional[np.ndarray] = None) -> int:
     dr = ctypes.c_int32()
     _check(load_library().snp_explore(h, ctypes.byref(opts), ctypes.byref(dr), _ptr(truncated_flags)))
+    return dr.value
+
+
+def snp_explore_resume(h, rows: np.ndarray, stats, opts: snp_explore_opts,
+                       truncated_flags: Optional[np.ndarray] = None) -> int:
+    """rows: [n, m] int32 (host array or a torch device tensor); stats: a ctypes array of snp_depth_info."""
+    dr = ctypes.c_int32()
+    if hasattr(rows, "data_ptr"):
+        ptr, n = rows.data_ptr(), int(rows.shape[0])
+    else:
+        rows = np.ascontiguousarray(rows, dtype=np.int32)
+        ptr, n = rows.ctypes.data, int(rows.shape[0])
+    _check(load_library().snp_explore_resume(h, ctypes.c_void_p(ptr), ctypes.c_int64(n), stats,
+                                             ctypes.c_int32(len(stats)), ctypes.byref(opts), ctypes.byref(dr),
+                                             _ptr(truncated_flags)))
     return dr.value
 
 
@@ -370,6 +386,36 @@ class System:
         o.kernel_timing = 1 if kernel_timing else 0
         self.truncated = np.zeros(int(depth) + 1, dtype=np.int32)
         self.depth_reached = snp_explore(self.h, o, self.truncated)
+        return self.depth_reached
+
+    def checkpoint(self) -> Tuple[np.ndarray, np.ndarray]:
+        """State at the last depth boundary: (rows [n, m] in discovery order,
+        per-depth records as raw bytes) -- what resume() takes back; both can
+        be written to disk as they are."""
+        rows = self.reachable()
+        infos = []
+        d = 0
+        while True:
+            info = snp_depth_info()
+            if load_library().snp_depth_stats(self.h, d, ctypes.byref(info)) != SNP_OK:
+                break
+            infos.append(info)
+            d += 1
+        arr = (snp_depth_info * len(infos))(*infos)
+        return rows, np.frombuffer(bytes(arr), dtype=np.uint8).copy()
+
+    def resume(self, checkpoint, depth: int, cap: int = 0, budget: int = 0, transition: int = SNP_T_SPARSE_I32,
+               max_expand: int = -1, chunk: int = 0, stream=None) -> int:
+        """Continues the exploration a checkpoint() was taken from up to `depth`."""
+        rows, raw = checkpoint
+        raw = np.ascontiguousarray(raw, dtype=np.uint8)
+        k = raw.nbytes // ctypes.sizeof(snp_depth_info)
+        stats = (snp_depth_info * k).from_buffer_copy(raw.tobytes())
+        o = snp_explore_opts_init()
+        o.depth, o.transition, o.frontier_cap, o.candidate_budget = int(depth), int(transition), int(cap), int(budget)
+        o.max_expand_value, o.chunk, o.stream = int(max_expand), int(chunk), _stream_handle(stream)
+        self.truncated = np.zeros(int(depth) + 1, dtype=np.int32)
+        self.depth_reached = snp_explore_resume(self.h, rows, stats, o, self.truncated)
         return self.depth_reached
 
     def count(self) -> int:

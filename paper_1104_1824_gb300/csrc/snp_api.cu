@@ -426,10 +426,35 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
   return SNP_OK;
 }
 
-int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags) {
+}  // extern "C"
+
+namespace {
+
+// State a resumed exploration starts from (snp_explore_resume).
+struct ResumeFrom {
+  const int32_t* rows;        // [n x m] configurations in discovery order, host or device
+  int64_t n;
+  const snp_depth_info* stats;  // [nstats] per-depth records, depth 0 first
+  int32_t nstats;
+};
+
+int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags,
+                 const ResumeFrom* rs) {
   g_err.clear();
   if (!h || !o) return fail(SNP_E_INVALID, "bad arguments");
   if (o->depth < 0) return fail(SNP_E_INVALID, "depth = %d < 0", o->depth);
+  if (rs) {
+    if (!rs->rows || !rs->stats || rs->nstats < 1 || rs->n < 1 || rs->n > 0x7FFFFFF0ll)
+      return fail(SNP_E_INVALID, "bad checkpoint");
+    int64_t sum = 0;
+    for (int d = 0; d < rs->nstats; ++d) sum += rs->stats[d].new_configs;
+    if (sum != rs->n || rs->stats[0].new_configs != 1)
+      return fail(SNP_E_INVALID, "checkpoint: per-depth counts add up to %lld, not %lld rows", (long long)sum,
+                  (long long)rs->n);
+    if (o->depth < rs->nstats - 1)
+      return fail(SNP_E_INVALID, "checkpoint already holds depth %d > %d", rs->nstats - 1, o->depth);
+    if (o->record_parents) return fail(SNP_E_INVALID, "parent records cannot be resumed");
+  }
   if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_I8)
     return fail(SNP_E_INVALID, "unknown transition %d", o->transition);
   if (o->transition == SNP_T_TC_I8 && h->max_abs_m > 127)
@@ -468,6 +493,11 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     const long double want = 1.0L + (long double)o->depth * (long double)budget;
     if (want < 2.0e9L) rows_plan = std::max<int64_t>(rows_plan, std::min<int64_t>((int64_t)want, 1 << 20));
   }
+  if (rs) {  // the rows so far, plus what the remaining depths may add
+    const long double more = cap > 0 ? (long double)(o->depth - rs->nstats + 1) * (long double)cap : 4096.0L;
+    rows_plan = (int64_t)std::min<long double>(2.0e9L, std::max<long double>((long double)rows_plan,
+                                                                             (long double)rs->n + more));
+  }
   // The store keeps every claimed row where its owner wrote it (claims past
   // the cap included, at most one pass's worth per depth); perm lists the
   // configurations in discovery order.
@@ -493,11 +523,23 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
   TRY(ensure_chunk_buffers(h, std::min<uint64_t>(qmax, 1 << 16), st));
   TRY(h->d_ctr.reserve(3 * sizeof(unsigned long long)));
 
-  // Root level: C0, store row 0.
-  h->n_rows = 1;
-  h->n_store = 1;
-  CK(cudaMemcpyAsync(h->d_pool.p, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(h->d_perm.p, 0, sizeof(uint32_t), st));
+  int64_t level_lo = 0, level_hi = 1;
+  int d_start = 1;
+  if (rs) {  // the checkpoint's rows become store rows 0 .. n-1, in discovery order
+    h->n_rows = rs->n;
+    h->n_store = rs->n;
+    CK(cudaMemcpyAsync(h->d_pool.p, rs->rows, sizeof(int32_t) * (size_t)m * rs->n, cudaMemcpyDefault, st));
+    launch_iota_u32(h->d_perm.as<uint32_t>(), rs->n, st);
+    CK(cudaGetLastError());
+    level_hi = rs->n;
+    level_lo = rs->n - rs->stats[rs->nstats - 1].new_configs;
+    d_start = rs->nstats;
+  } else {  // root level: C0, store row 0
+    h->n_rows = 1;
+    h->n_store = 1;
+    CK(cudaMemcpyAsync(h->d_pool.p, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(h->d_perm.p, 0, sizeof(uint32_t), st));
+  }
   if (o->record_parents) {
     const int64_t rp = -1;
     const uint64_t ri = 0;
@@ -510,16 +552,22 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
         (uint64_t)((long double)(rows_plan + (int64_t)std::min<uint64_t>(qmax, 1 << 16)) * 4.0L / 3.0L / kBucket) + 1;
     TRY(rebuild_table(h, pow2_at_least(want), st));
   }
-  snp_depth_info s0;
-  std::memset(&s0, 0, sizeof s0);
-  s0.new_configs = 1;
-  s0.launches = 2;  // the table build above
-  h->stats.push_back(s0);
-  int64_t level_lo = 0, level_hi = 1;
+  if (rs) {
+    h->stats.assign(rs->stats, rs->stats + rs->nstats);
+    for (int d = 0; d < rs->nstats; ++d)
+      if (rs->stats[d].new_configs > 0) h->depth_reached = d;
+    if (rs->stats[rs->nstats - 1].new_configs == 0) d_start = o->depth + 1;  // the exploration had ended
+  } else {
+    snp_depth_info s0;
+    std::memset(&s0, 0, sizeof s0);
+    s0.new_configs = 1;
+    s0.launches = 2;  // the table build above
+    h->stats.push_back(s0);
+  }
   int64_t tombs = 0;
   double rate = 1.0;  // new configurations per candidate, for chunk sizing
 
-  for (int d = 1; d <= o->depth; ++d) {
+  for (int d = d_start; d <= o->depth; ++d) {
     snp_depth_info sd;
     std::memset(&sd, 0, sizeof sd);
     const int64_t P = level_hi - level_lo;
@@ -783,6 +831,20 @@ int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached,
     for (int d = 0; d <= o->depth; ++d)
       truncated_flags[d] = d < (int)h->stats.size() ? h->stats[d].truncated : 0;
   return SNP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int snp_explore(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags) {
+  return explore_impl(h, o, depth_reached, truncated_flags, nullptr);
+}
+
+int snp_explore_resume(snp_handle h, const int32_t* rows, int64_t n, const snp_depth_info* stats, int32_t nstats,
+                       const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags) {
+  const ResumeFrom rs{rows, n, stats, nstats};
+  return explore_impl(h, o, depth_reached, truncated_flags, &rs);
 }
 
 int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int64_t* per_depth_new) {

@@ -295,6 +295,16 @@ __global__ void __launch_bounds__(256) k_commit(CommitArgs a) {
   }
 }
 
+__global__ void k_iota_u32(uint32_t* out, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (uint32_t)k;
+}
+
+void launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+  k_iota_u32<<<blocks, 256, 0, st>>>(out, n);
+}
+
 // out[k] = pool[perm[k]] for k < n, one warp per row (16-byte pieces when
 // m % 4 == 0).
 __global__ void k_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out) {

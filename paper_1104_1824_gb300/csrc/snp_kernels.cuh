@@ -132,6 +132,7 @@ size_t tc_rows_smem(int mp);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);
+void launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t st);
 void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out, cudaStream_t st);
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st);
 __global__ void k_insert_rows(DevSys s, const int32_t* pool, const uint32_t* perm, int64_t r0, int64_t r1, DevTable t,

@@ -494,3 +494,74 @@ def test_union_rules_in_the_batch_engine(gpu):
         e = oracle.Oracle(x).explore(5, cap=64, budget=512)
         assert (h.reachable() == e.configs).all()
         assert [(a.new, a.examined) for a in h.depth_stats()] == [(b.new, b.examined) for b in e.depths]
+
+
+# --- checkpoint and resume at depth boundaries ---
+
+def same_run(a, b):
+    assert (a.reachable() == b.reachable()).all()
+    key = lambda x: (x.new, x.examined, x.candidates, x.truncated, x.parents)
+    assert [key(x) for x in a.depth_stats()] == [key(x) for x in b.depth_stats()]
+    assert a.depth_reached == b.depth_reached
+
+
+@pytest.mark.parametrize("at", [0, 1, 4])
+def test_resume_equals_one_run(gpu, tmp_path, at):
+    system = snp_synth.random_64(1)
+    opts = dict(cap=4096, budget=1 << 16)
+    first = gpu.System(system)
+    first.explore(at, **opts)
+    rows, stats = first.checkpoint()
+    np.save(tmp_path / "rows.npy", rows)
+    np.save(tmp_path / "stats.npy", stats)
+    later = gpu.System(system)
+    later.resume((np.load(tmp_path / "rows.npy"), np.load(tmp_path / "stats.npy")), 8, **opts)
+    fresh = gpu.System(system)
+    fresh.explore(8, **opts)
+    same_run(later, fresh)
+    e = oracle.Oracle(system).explore(8, **opts)
+    assert (later.reachable() == e.configs).all()
+
+
+def test_resume_from_device_rows_and_other_transition(gpu):
+    import torch
+    system = snp_synth.random_64(1)
+    first = gpu.System(system)
+    first.explore(2, cap=2048, budget=1 << 15)
+    rows, stats = first.checkpoint()
+    later = gpu.System(system)
+    later.resume((torch.from_numpy(rows).cuda(), stats), 5, cap=2048, budget=1 << 15, transition=gpu.SNP_T_TC_I8)
+    fresh = gpu.System(system)
+    fresh.explore(5, cap=2048, budget=1 << 15)
+    assert (later.reachable() == fresh.reachable()).all()
+
+
+def test_resume_after_the_search_ended(gpu):
+    paper = snp_synth.paper_example()
+    first = gpu.System(paper)
+    first.explore(60, max_expand=9)  # the replay ends by repetition before depth 60
+    ckpt = first.checkpoint()
+    later = gpu.System(paper)
+    later.resume(ckpt, 80, max_expand=9)
+    fresh = gpu.System(paper)
+    fresh.explore(80, max_expand=9)
+    same_run(later, fresh)
+    assert later.count() == 48
+
+
+def test_resume_rejects_inconsistent_checkpoints(gpu):
+    system = snp_synth.random_64(1)
+    first = gpu.System(system)
+    first.explore(2, cap=100, budget=1000)
+    rows, stats = first.checkpoint()
+    later = gpu.System(system)
+    with pytest.raises(gpu.SnpError) as ei:
+        later.resume((rows[:-1], stats), 4, cap=100, budget=1000)
+    assert ei.value.code == gpu.SNP_E_INVALID
+    with pytest.raises(gpu.SnpError) as ei:
+        later.resume((rows, stats), 1, cap=100, budget=1000)  # the checkpoint is already at depth 2
+    assert ei.value.code == gpu.SNP_E_INVALID
+    later.resume((rows, stats), 4, cap=100, budget=1000)  # the handle is still usable
+    fresh = gpu.System(system)
+    fresh.explore(4, cap=100, budget=1000)
+    same_run(later, fresh)
