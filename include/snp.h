@@ -332,6 +332,13 @@ int snp_tc_peak_tops(int32_t iters, double* tops);
 /* Message for the last failed call on this thread ("" if none). */
 const char* snp_last_error(void);
 
+/* Testing hook (no counterpart in the paper): the k-th device allocation from
+ * now on (k >= 1, counting every buffer the library allocates or grows) fails
+ * as if the device were out of memory, so that error paths can be exercised
+ * without exhausting the device; k <= 0 turns it off.  The failing call
+ * returns SNP_E_NOMEM and leaves every handle usable.  Process-wide. */
+int snp_debug_fail_allocation(int64_t k);
+
 /* SNP_ABI_VERSION of the loaded library. */
 int snp_abi_version(void);
 

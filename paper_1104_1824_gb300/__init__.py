@@ -42,7 +42,7 @@ ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOME
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
            "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
-           "snp_explore_resume",
+           "snp_explore_resume", "snp_debug_fail_allocation",
            "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune", "snp_server_create",
            "snp_server_submit", "snp_server_poll", "snp_server_wait", "snp_server_stats", "snp_server_destroy"]
 
@@ -192,6 +192,11 @@ def snp_explore(h, opts: snp_explore_opts, truncated_flags: Optional[np.ndarray]
     dr = ctypes.c_int32()
     _check(load_library().snp_explore(h, ctypes.byref(opts), ctypes.byref(dr), _ptr(truncated_flags)))
     return dr.value
+
+
+def snp_debug_fail_allocation(k: int) -> None:
+    """Testing hook: the k-th device allocation from now on fails (k <= 0: off)."""
+    _check(load_library().snp_debug_fail_allocation(ctypes.c_int64(int(k))))
 
 
 def snp_explore_resume(h, rows: np.ndarray, stats, opts: snp_explore_opts,

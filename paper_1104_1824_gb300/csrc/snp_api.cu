@@ -16,6 +16,7 @@ using namespace snp;
 namespace snp {
 
 thread_local std::string g_err;
+std::atomic<long long> g_alloc_countdown{0};
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -179,6 +180,11 @@ void snp_explore_opts_init(snp_explore_opts* o) {
 }
 
 const char* snp_last_error(void) { return g_err.c_str(); }
+
+int snp_debug_fail_allocation(int64_t k) {
+  g_alloc_countdown.store(k > 0 ? k : 0);
+  return SNP_OK;
+}
 
 int snp_abi_version(void) { return SNP_ABI_VERSION; }
 

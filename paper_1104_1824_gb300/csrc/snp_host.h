@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdarg>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <memory>
@@ -42,6 +43,10 @@ bool is_device_ptr(const void* p);
   } while (0)
 
 // A device allocation that grows on demand (contents are not preserved unless asked).
+// Testing hook (snp_debug_fail_allocation): while positive, each device
+// allocation counts it down and the one that reaches zero fails.
+extern std::atomic<long long> g_alloc_countdown;
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -53,6 +58,8 @@ struct DevBuf {
   }
   inline int reserve(size_t want, cudaStream_t st = nullptr, bool keep = false) {
     if (want <= bytes) return SNP_OK;
+    if (g_alloc_countdown.load(std::memory_order_relaxed) > 0 && g_alloc_countdown.fetch_sub(1) == 1)
+      return fail(SNP_E_NOMEM, "cudaMalloc(%zu bytes): refused by the fault-injection hook", want);
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, want);
     if (e != cudaSuccess) {

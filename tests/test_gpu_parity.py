@@ -565,3 +565,40 @@ def test_resume_rejects_inconsistent_checkpoints(gpu):
     fresh = gpu.System(system)
     fresh.explore(4, cap=100, budget=1000)
     same_run(later, fresh)
+
+
+# --- failure detection on the host (no GPU fault involved) ---
+
+def test_allocation_failures_leave_handles_usable(gpu):
+    """Each device allocation of a load and an exploration is refused in turn
+    (the library's fault-injection hook): the call reports SNP_E_NOMEM, and the
+    same handle then explores correctly once allocations succeed again."""
+    system = snp_synth.random_64(1)
+    want = oracle.Oracle(system).explore(3, cap=2000, budget=20000)
+    refused = 0
+    try:
+        for k in range(1, 200):
+            gpu.snp_debug_fail_allocation(k)
+            try:
+                s = gpu.System(system)
+            except gpu.SnpError as e:
+                assert e.code == gpu.SNP_E_NOMEM
+                refused += 1
+                continue
+            try:
+                s.explore(3, cap=2000, budget=20000)
+            except gpu.SnpError as e:
+                assert e.code == gpu.SNP_E_NOMEM
+                refused += 1
+                gpu.snp_debug_fail_allocation(0)
+                s.explore(3, cap=2000, budget=20000)
+                assert (s.reachable() == want.configs).all()
+                continue
+            gpu.snp_debug_fail_allocation(0)
+            assert (s.reachable() == want.configs).all()  # k is past the last allocation
+            break
+        else:
+            raise AssertionError("the hook never ran out of allocations to refuse")
+    finally:
+        gpu.snp_debug_fail_allocation(0)
+    assert refused > 10
