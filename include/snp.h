@@ -148,8 +148,8 @@ typedef struct {
   float expand_ms;       /* device time of the expand kernel (kernel_timing) */
   int64_t expand_bytes;  /* algorithmic DRAM bytes of the expand kernel: per
                             candidate an 8-byte slot probe, per duplicate a
-                            4m-byte key compare, per new key a 4m-byte staged
-                            row and an 8-byte slot write, per parent a 4m-byte
+                            4m-byte key compare, per new key a 4m-byte row
+                            write and an 8-byte slot write, per parent a 4m-byte
                             row read */
   int64_t launches;      /* kernels launched for this depth */
 } snp_depth_info;

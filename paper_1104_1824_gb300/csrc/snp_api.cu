@@ -53,8 +53,9 @@ int check_device_errors(snp_system* h, cudaStream_t st, const char* where) {
   return fail(SNP_E_INTERNAL, "%s: device consistency check failed (bits 0x%x)", where, e);
 }
 
-// Staging and first-occurrence buffers for chunks of up to q candidates
-// (grow only; a fresh first-occurrence bitmap starts cleared).
+// Per-pass buffers for chunks of up to q candidates: owners' store rows and
+// the first-occurrence records (grow only; a fresh first-occurrence bitmap
+// starts cleared).
 int ensure_chunk_buffers(snp_system* h, uint64_t q, cudaStream_t st) {
   if (h->q_cap >= q) return SNP_OK;
   q = std::max<uint64_t>(q, std::min<uint64_t>(h->q_cap * 2, 1ull << 30));
@@ -480,8 +481,8 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   const int64_t budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
   const bool tc = o->transition == SNP_T_TC_I8;
 
-  // Chunk size bound: staging of at most ~512 MiB; the tensor-core form works
-  // on chunks of at most 65536 spiking vectors.
+  // Chunk size bound: at most ~512 MiB of rows claimed per pass; the
+  // tensor-core form works on chunks of at most 65536 spiking vectors.
   uint64_t qmax = o->chunk > 0 ? (uint64_t)o->chunk
                                : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 29) / (4ull * m)));
   qmax = std::min<uint64_t>(qmax, 1ull << 30);

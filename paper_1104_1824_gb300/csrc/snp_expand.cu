@@ -21,9 +21,10 @@
 //   once before they are resolved.
 //
 // Resolving a row (step d): probe the hash table, compare full keys, and
-// either find the key (seen before, or staged earlier in this chunk: then
-// lower that key's first-occurrence index) or claim an empty slot, stage the
-// row and publish the slot.
+// either find the key (seen before, or claimed earlier in this chunk: then
+// lower that key's first-occurrence index) or claim an empty slot, write the
+// row (to the next store row; the batch engine and the allocation-free path
+// use staging row lid) and publish the slot.
 #include "snp_kernels.cuh"
 
 namespace snp {

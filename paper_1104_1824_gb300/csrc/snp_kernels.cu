@@ -7,13 +7,16 @@
 //   per chunk of candidates [g0, g0 + Q) in canonical order:
 //     k_expand steps (b)-(d) (snp_expand.cu): decode the spiking vector, C' = C + S . M_Pi
 //              (Eq. next-config), fingerprint, look C' up; a key never seen is
-//              claimed in the table and staged, and every candidate holding a
-//              staged key lowers that key's first-occurrence index;
+//              claimed in the table and its row written (to the store, or to
+//              staging row lid), and every candidate holding such a pending
+//              key lowers that key's first-occurrence index;
 //     k_mark   one bit per first occurrence;
 //     scan     ranks of the first occurrences in candidate order;
-//     k_commit the first `remaining` of them are copied, in rank order, to the
-//              configuration pool and their table slots point there; the rest
-//              become tombstones (the cap stops the depth).
+//     k_commit the first `remaining` of them get their discovery index, in
+//              rank order (the row map entry; or a copy of the staged row
+//              into the discovery-ordered pool), and their table slots point
+//              at their rows; the rest become tombstones (the cap stops the
+//              depth).
 #include "snp_kernels.cuh"
 
 namespace snp {

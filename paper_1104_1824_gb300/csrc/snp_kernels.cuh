@@ -36,7 +36,7 @@ struct CommitArgs {
   uint32_t nwords;            // ceil(Q / 32)
   const uint32_t* bits;       // [nwords] first-occurrence bitmap over chunk-local indices
   const uint32_t* wbase;      // [nwords] exclusive prefix of popcounts
-  const uint32_t* srow;       // [Q] staging row of each first occurrence
+  const uint32_t* srow;       // [Q] owner (candidate that claimed the key) of each first occurrence
   const uint32_t* slot_of;
   const int32_t* staging;
   DevTable table;
