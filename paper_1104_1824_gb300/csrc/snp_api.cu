@@ -481,10 +481,12 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   const int64_t budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
   const bool tc = o->transition == SNP_T_TC_I8;
 
-  // Chunk size bound: at most ~512 MiB of rows claimed per pass; the
-  // tensor-core form works on chunks of at most 65536 spiking vectors.
+  // Chunk size bound: 2^20 spiking vectors, or more while the rows a pass may
+  // claim stay within ~512 MiB (passes of wide rows need 2^20 to keep every
+  // warp of the expand kernel busy); the tensor-core form works on chunks of
+  // at most 65536 spiking vectors.
   uint64_t qmax = o->chunk > 0 ? (uint64_t)o->chunk
-                               : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 16, (1ull << 29) / (4ull * m)));
+                               : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 20, (1ull << 29) / (4ull * m)));
   qmax = std::min<uint64_t>(qmax, 1ull << 30);
   if (tc) {
     qmax = std::min<uint64_t>(qmax, 1ull << 16);

@@ -60,6 +60,17 @@ __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
   return (b + 15) & ~size_t(15);
 }
 
+// Wide rows (more than kWideM neurons): a warp keeps one scratch row instead
+// of one row per lane, and queues up to 32 crossing-batch candidates.
+constexpr int kWideM = 128;
+constexpr int kWideB = 32;
+constexpr int kWide = 2;  // KIND of the wide mode
+__host__ __device__ inline size_t expand_wide_bytes(int m) {
+  const int m4 = round4(m);
+  size_t b = (size_t)m4 * 4 + expand_keys_bytes(kWideB) + (size_t)m4 * 16 + 32 + (size_t)m4;
+  return (b + 15) & ~size_t(15);
+}
+
 __device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
@@ -554,6 +565,360 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
   return w;
 }
 
+// Per-warp shared memory of the wide mode: the scratch row, the queue of
+// crossing-batch candidates, then the parent state as in expand_smem (no
+// change list: the odometer's swaps go straight into the block base).
+__device__ __forceinline__ ExpandSmem expand_smem_wide(unsigned char* base, int m) {
+  const int m4 = round4(m);
+  ExpandSmem w;
+  w.tile = reinterpret_cast<int32_t*>(base);
+  w.keys = reinterpret_cast<unsigned long long*>(w.tile + m4);
+  w.dpc = reinterpret_cast<long long*>(w.keys + kWideB);
+  w.dt = reinterpret_cast<unsigned long long*>(w.dpc + kWideB);
+  w.lids = reinterpret_cast<uint32_t*>(w.dt + kWideB);
+  w.par = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(w.keys) + expand_keys_bytes(kWideB));
+  w.buf = w.par + m4;
+  w.msk = reinterpret_cast<uint32_t*>(w.buf + m4);
+  w.ntl = reinterpret_cast<int32_t*>(w.msk + m4);
+  w.chg = nullptr;
+  w.hdr = reinterpret_cast<int*>(w.ntl + m4);
+  w.dig = reinterpret_cast<uint8_t*>(w.hdr + 8);
+  return w;
+}
+
+// dst = src for a row in shared memory, by the whole warp.
+template <bool VEC>
+__device__ __forceinline__ void warp_copy_row(const int32_t* src, int32_t* dst, int m, int lane) {
+  if (VEC) {
+    const int4* a = reinterpret_cast<const int4*>(src);
+    int4* b = reinterpret_cast<int4*>(dst);
+    for (int j = lane; j < (m >> 2); j += 32) b[j] = a[j];
+  } else {
+    for (int j = lane; j < m; j += 32) dst[j] = src[j];
+  }
+}
+
+// row += M[rn] - M[ro] for two rules of one neuron, by the whole warp: the
+// columns of the neuron's support are distinct, so the lanes share them out.
+__device__ __forceinline__ void warp_swap_rule(const DevSys& s, int32_t* row, int ro, int rn, int lane) {
+  const int4 dn = __ldg(s.rdesc + rn);
+  const int32_t* vn = s.rval + dn.z;
+  const int32_t* vo = s.rval + __ldg(&s.rdesc[ro].z);
+  const int32_t* col = s.scol + dn.x;
+  for (int i = lane; i < dn.y; i += 32) row[__ldg(col + i)] += __ldg(vn + i) - __ldg(vo + i);
+  __syncwarp();
+}
+
+// Row of candidate L of the current block in the scratch row: the block base
+// with the low digits of L (all lanes decode the same digits).
+template <bool VEC>
+__device__ __forceinline__ void build_block_row(const DevSys& s, ExpandSmem& w, int L, int nlow, int lane) {
+  __syncwarp();
+  warp_copy_row<VEC>(w.buf, w.tile, s.m, lane);
+  __syncwarp();
+  uint32_t q = (uint32_t)L;
+  for (int i = 0; i < nlow; ++i) {
+    const int n = w.ntl[i];
+    const uint32_t radix = __popc(w.msk[n]);
+    const uint32_t d = q % radix;
+    q /= radix;
+    if (d != 0) warp_swap_rule(s, w.tile, rule_of(s, w, n, 0), rule_of(s, w, n, (int)d), lane);
+  }
+}
+
+// Row of candidate t of parent pc (a crossing-batch candidate) in the scratch
+// row: each lane decodes the digits of its own ceil(m / 32) neurons, whose
+// place value is the product of the choice counts of the later lanes' neurons
+// (last neuron least significant), and adds its chosen rules' rows.
+template <bool VEC>
+__device__ __forceinline__ void build_flat_row(const ClaimArgs& a, int32_t* row, int64_t pc, uint64_t t, int lane) {
+  const DevSys& s = a.sys;
+  const int32_t* prow = parent_row(a, pc);
+  __syncwarp();
+  for (int n = lane; n < s.m; n += 32) row[n] = prow[n];
+  const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
+  uint64_t prod = 1;
+  for (int n = n0; n < n1; ++n) {
+    const uint32_t mask = (uint32_t)appl(s, n, prow[n]);
+    prod = sat_mul(prod, mask ? (uint64_t)__popc(mask) : 1ull);
+  }
+  uint64_t v = prod;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane + o < 32) v = sat_mul(v, u);
+  }
+  const uint64_t nxt = __shfl_down_sync(0xffffffffu, v, 1);
+  const uint64_t after = lane == 31 ? 1ull : nxt;
+  __syncwarp();
+  uint64_t q = (after > t) ? 0ull : t / after;
+  for (int n = n1 - 1; n >= n0; --n) {
+    const uint32_t mask = (uint32_t)appl(s, n, prow[n]);
+    if (!mask) continue;
+    const int kb = nth_set_bit(mask, (int)next_digit(q, __popc(mask)));
+    add_row_shared(s, row, __ldg(s.first_rule + n) + kb, 1);
+  }
+  __syncwarp();
+}
+
+// Full-key compare of the scratch row with a stored row, by the whole warp.
+template <bool VEC>
+__device__ __forceinline__ bool warp_rows_equal(const int32_t* row, const int32_t* other, int m, int lane) {
+  int diff = 0;
+  if (VEC) {
+    const int4* a = reinterpret_cast<const int4*>(row);
+    const int4* b = reinterpret_cast<const int4*>(other);
+    for (int j = lane; j < (m >> 2); j += 32) {
+      const int4 x = a[j], y = __ldcg(b + j);
+      diff |= (x.x ^ y.x) | (x.y ^ y.y) | (x.z ^ y.z) | (x.w ^ y.w);
+    }
+  } else {
+    for (int j = lane; j < m; j += 32) diff |= row[j] ^ __ldcg(other + j);
+  }
+  return !__any_sync(0xffffffffu, diff != 0);
+}
+
+// The scratch row to global memory, by the whole warp (coalesced).
+template <bool VEC>
+__device__ __forceinline__ void warp_store_row(const int32_t* row, int32_t* dst, int m, int lane) {
+  if (VEC) {
+    const int4* a = reinterpret_cast<const int4*>(row);
+    int4* b = reinterpret_cast<int4*>(dst);
+    for (int j = lane; j < (m >> 2); j += 32) __stcg(b + j, a[j]);
+  } else {
+    for (int j = lane; j < m; j += 32) __stcg(dst + j, row[j]);
+  }
+}
+
+constexpr int kProbe = 3, kCompare = 4;
+
+// Step (d) in the wide mode, for one key per lane (lanes with todo set).
+// Lanes walk their own probe sequences as resolve_lane does; a row is built,
+// by the whole warp in the scratch row, only where a stored row with the same
+// fingerprint must be compared or where the lane has claimed a slot and
+// writes its row.  build(L) builds lane L's row.  As in resolve_warp_body, no
+// lane waits inside a pass: a lane that meets a reserved slot with its
+// fingerprint starts over in a later pass, and owners publish before the pass
+// ends.
+template <bool VEC, typename Build>
+__device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* scratch, uint64_t key, uint32_t lid,
+                                                  bool todo, int lane, Build&& build) {
+  const int m = a.sys.m;
+  const uint32_t fp = fp32_of(key);
+  const unsigned long long mine = ((unsigned long long)fp << 32) | kRowReserved;
+  int st = todo ? kRetry : kDone;
+  uint64_t bucket = 0, probes = 0;
+  uint32_t match = 0, empty = 0;
+  bool loaded = false;
+  uint32_t orf = 0;
+  const int32_t* other = nullptr;
+  unsigned long long* owned = nullptr;
+  for (int pass = 0;; ++pass) {
+    if (st == kRetry) {
+      st = kProbe;
+      bucket = key & a.table.bmask;
+      probes = 0;
+      loaded = false;
+    }
+    for (;;) {
+      // each probing lane goes on to its next compare, claim, retry or end
+      while (st == kProbe) {
+        unsigned long long* bs = a.table.slots + bucket * kBucket;
+        if (!loaded) {
+          if (probes > a.table.bmask) {
+            atomicOr(&a.st->error, kErrTableFull);
+            st = kDone;
+            break;
+          }
+          const ulonglong2* b2 = reinterpret_cast<const ulonglong2*>(bs);
+          match = 0;
+          empty = 0;
+#pragma unroll
+          for (int q = 0; q < kBucket / 2; ++q) {
+            const ulonglong2 x = __ldcg(b2 + q);
+            empty |= (x.x == kEmpty ? 1u : 0u) << (2 * q);
+            empty |= (x.y == kEmpty ? 1u : 0u) << (2 * q + 1);
+            match |= ((uint32_t)(x.x >> 32) == fp && (uint32_t)x.x != kRowTomb && x.x != kEmpty ? 1u : 0u) << (2 * q);
+            match |= ((uint32_t)(x.y >> 32) == fp && (uint32_t)x.y != kRowTomb && x.y != kEmpty ? 1u : 0u)
+                     << (2 * q + 1);
+          }
+          loaded = true;
+        }
+        if (match) {
+          const int j = __ffs(match) - 1;
+          match &= match - 1;
+          orf = (uint32_t)__ldcg(bs + j);
+          if (orf == kRowReserved) {
+            st = kRetry;
+            break;
+          }
+          if (orf & kPending) {
+            (void)ld_acquire(bs + j);
+            const uint32_t o = orf & ~kPending;
+            other = a.store_ctr ? a.pool + (size_t)__ldcg(a.sidx_of + o) * m : a.staging + (size_t)o * m;
+          } else {
+            other = a.pool + (size_t)orf * m;
+          }
+          st = kCompare;
+          break;
+        }
+        if (empty) {
+          const int j = __ffs(empty) - 1;
+          if (atomicCAS(bs + j, kEmpty, mine) == kEmpty) {
+            owned = bs + j;
+            st = kOwner;
+            break;
+          }
+          loaded = false;  // look at this bucket again
+          continue;
+        }
+        ++probes;
+        bucket = (bucket + 1) & a.table.bmask;
+        loaded = false;
+      }
+      // compares, one lane's row at a time
+      for (uint32_t cm = __ballot_sync(0xffffffffu, st == kCompare); cm; cm &= cm - 1) {
+        const int L = __ffs(cm) - 1;
+        const int32_t* o = reinterpret_cast<const int32_t*>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(other), L));
+        build(L);
+        const bool eq = warp_rows_equal<VEC>(scratch, o, m, lane);
+        if (lane == L) {
+          if (eq) {
+            if (orf & kPending) atomicMin(a.gmin + (orf & ~kPending), lid);
+            st = kDone;
+          } else {
+            st = kProbe;
+          }
+        }
+      }
+      // owners: consecutive store rows with one atomic, rows written by the
+      // whole warp, then each owner publishes its slot
+      const uint32_t ob = __ballot_sync(0xffffffffu, st == kOwner);
+      if (ob) {
+        uint64_t sidx = 0;
+        if (a.store_ctr) {
+          const int leader = __ffs(ob) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(a.store_ctr, (unsigned long long)__popc(ob));
+          sidx = __shfl_sync(0xffffffffu, base, leader) + __popc(ob & ((1u << lane) - 1u));
+        }
+        for (uint32_t ow = ob; ow; ow &= ow - 1) {
+          const int L = __ffs(ow) - 1;
+          const uint64_t sl = __shfl_sync(0xffffffffu, sidx, L);
+          const uint32_t ll = __shfl_sync(0xffffffffu, lid, L);
+          if (a.store_ctr && sl >= a.store_cap) continue;  // reported by lane L below
+          build(L);
+          warp_store_row<VEC>(scratch, a.store_ctr ? a.pool + (size_t)sl * m : a.staging + (size_t)ll * m, m,
+                              lane);
+        }
+        __threadfence();
+        __syncwarp();
+        if (st == kOwner) {
+          st = kDone;
+          if (a.store_ctr) {
+            if (sidx >= a.store_cap) {  // the host sizes the store for every claim of the chunk
+              atomicOr(&a.st->error, kErrStaging);
+              owned = nullptr;
+            } else {
+              a.sidx_of[lid] = (uint32_t)sidx;
+            }
+          }
+          if (owned) {
+            a.gmin[lid] = lid;
+            a.slot_of[lid] = (uint32_t)(owned - a.table.slots);
+            atomicOr(a.ownbits + (lid >> 5), 1u << (lid & 31));
+            st_release(owned, ((unsigned long long)fp << 32) | (kPending | lid));
+          }
+        }
+      }
+      if (!__any_sync(0xffffffffu, st == kProbe)) break;
+    }
+    if (__all_sync(0xffffffffu, st != kRetry)) break;
+    if (pass >= kSpinLimit) {
+      if (st == kRetry) atomicOr(&a.st->error, kErrTimeout);
+      break;
+    }
+    __nanosleep(32);
+  }
+  __syncwarp();
+}
+
+// Resolves the queued crossing-batch candidates in the wide mode.
+template <bool VEC>
+__device__ __forceinline__ void flush_queue_wide(const ClaimArgs& a, ExpandSmem& w, int fill, int lane) {
+  const bool mine = lane < fill;
+  resolve_warp_wide<VEC>(a, w.tile, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine, lane,
+                         [&](int L) { build_flat_row<VEC>(a, w.tile, w.dpc[L], w.dt[L], lane); });
+}
+
+// Block mode in the wide mode: lane k < RL owns candidate k of each block as
+// in block_run, but keeps only its hash; rows are built on demand from the
+// block base, to which the odometer applies its swaps directly.
+template <bool VEC>
+__device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSmem& w, int64_t p, uint64_t p_lo,
+                                                   uint64_t p_hi, uint64_t l, uint64_t lb, int64_t& cached_p,
+                                                   uint64_t& after, int lane) {
+  const DevSys& s = a.sys;
+  const uint64_t g = a.g0 + l;
+  const uint64_t gend = min(p_hi, a.g0 + lb);
+  if (p != cached_p) {
+    after = parent_state(s, parent_row(a, p), w, kWideB, lane);
+    cached_p = p;
+  }
+  const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
+  const uint64_t b = (g - p_lo) / (uint64_t)RL;
+  decode_full(s, w, b * (uint64_t)RL, after, lane);
+  uint64_t hk = 0;
+  bool redk = true;
+  if (lane < RL) {
+    redk = false;
+    uint32_t q = (uint32_t)lane;
+    for (int i = 0; i < nlow; ++i) {
+      const int n = w.ntl[i];
+      const uint32_t mask = w.msk[n];
+      const uint32_t radix = __popc(mask);
+      const uint32_t d = q % radix;
+      q /= radix;
+      if (d == 0) continue;
+      const int r0 = rule_of(s, w, n, 0), rd = rule_of(s, w, n, (int)d);
+      hk += __ldg(s.rowkey + rd) - __ldg(s.rowkey + r0);
+      redk |= redundant_choice(s, mask, rd);
+    }
+  }
+  uint64_t gb = p_lo + b * (uint64_t)RL;
+  for (;;) {
+    const uint64_t c = gb + lane;
+    const bool todo = lane < RL && c >= g && c < gend && !redk && w.hdr[kNred] == 0;
+    resolve_warp_wide<VEC>(a, w.tile, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo, lane,
+                           [&](int L) { build_block_row<VEC>(s, w, L, nlow, lane); });
+    gb += (uint64_t)RL;
+    if (gb >= gend) break;
+    // next block: the odometer, every lane following the same digits
+    uint64_t h = hbase_of(w);
+    int red = w.hdr[kNred];
+    for (int i = nlow; i < nnt; ++i) {
+      const int n = w.ntl[i];
+      const uint32_t mask = w.msk[n];
+      const int d = w.dig[n];
+      const int nd = (d + 1 == __popc(mask)) ? 0 : d + 1;
+      const int ro = rule_of(s, w, n, d), rn = rule_of(s, w, n, nd);
+      h += __ldg(s.rowkey + rn) - __ldg(s.rowkey + ro);
+      red += (redundant_choice(s, mask, rn) ? 1 : 0) - (redundant_choice(s, mask, ro) ? 1 : 0);
+      warp_swap_rule(s, w.buf, ro, rn, lane);
+      if (lane == 0) w.dig[n] = (uint8_t)nd;
+      if (nd != 0) break;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      hbase_of(w) = h;
+      w.hdr[kNred] = red;
+    }
+    __syncwarp();
+  }
+  return gend - a.g0;
+}
+
 // Resolves the queued rows of crossing batches (building them first).
 template <bool VEC, int KIND>
 __device__ __forceinline__ void flush_queue(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
@@ -640,6 +1005,14 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   return gend - a.g0;
 }
 
+template <bool VEC, int KIND>
+__device__ __forceinline__ void flush_any(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
+  if constexpr (KIND == kWide)
+    flush_queue_wide<VEC>(a, w, fill, lane);
+  else
+    flush_queue<VEC, KIND>(a, w, ts, fill, lane);
+}
+
 // Steps (b)-(d) for the tasks task0, task0 + tstride, ... of chunk a (a task
 // is a run of a.run consecutive candidates), by one warp: block mode while
 // the parent has 32 or more candidates left, else crossing batches.
@@ -673,11 +1046,14 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       const uint64_t g = a.g0 + l;
       if (done || p_hi - g >= 32) {
         if (fill > 0) {  // the tile is about to be reused, or the task ends
-          flush_queue<VEC, KIND>(a, w, ts, fill, lane);
+          flush_any<VEC, KIND>(a, w, ts, fill, lane);
           fill = 0;
         }
         if (done) break;
-        l = block_run<VEC, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, cached_p, after, lane);
+        if constexpr (KIND == kWide)
+          l = block_run_wide<VEC>(a, w, p, p_lo, p_hi, l, lb, cached_p, after, lane);
+        else
+          l = block_run<VEC, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, cached_p, after, lane);
         const uint64_t gn = a.g0 + l;
         if (l < lb) {
           do {
@@ -694,7 +1070,7 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       const int nb = flat_decode<VEC>(a, g, (int)min((uint64_t)B, lb - l), p, p_lo, lane, f, keep);
       const uint32_t kept = __ballot_sync(0xffffffffu, keep);
       if (fill + __popc(kept) > B) {
-        flush_queue<VEC, KIND>(a, w, ts, fill, lane);
+        flush_any<VEC, KIND>(a, w, ts, fill, lane);
         fill = 0;
       }
       if (keep) {
@@ -735,6 +1111,16 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   ExpandSmem w = expand_smem(smem_raw + (size_t)wib * expand_warp_bytes(a.sys.m, B, ts), a.sys.m, B, ts);
   expand_warp<VEC, 0>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
+}
+
+// The wide mode of k_expand (rows of more than kWideM neurons).
+template <bool VEC>
+__global__ void __launch_bounds__(256, 1) k_expand_wide(ClaimArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  if (a.ctr && __ldcg(a.ctr + 1) == 0) return;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  ExpandSmem w = expand_smem_wide(smem_raw + (size_t)wib * expand_wide_bytes(a.sys.m), a.sys.m);
+  expand_warp<VEC, kWide>(a, kWideB, 0, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
 }
 
 // Step (d) for rows already built in global memory (the tensor-core form):
@@ -779,6 +1165,19 @@ void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long l
 
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const int m = a.sys.m;
+  if (m > kWideM) {
+    const size_t per_warp = expand_wide_bytes(m);
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (220u << 10) / per_warp));
+    const size_t smem = per_warp * wpb;
+    const uint64_t two_per_warp = 2ull * nsm * wpb;
+    a.run = (uint32_t)std::max<uint64_t>(8ull * kWideB, ((uint64_t)a.Q + two_per_warp - 1) / two_per_warp);
+    const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
+    const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm);
+    auto fn = (m % 4) == 0 ? k_expand_wide<true> : k_expand_wide<false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fn<<<blocks > 0 ? blocks : 1, wpb * 32, smem, st>>>(a);
+    return 1;
+  }
   const int ts = round4(m) + 4;  // tile row stride (words): 16-byte aligned, rotates banks
   const int B = (int)std::min<size_t>(32, std::max<size_t>(1, (32u << 10) / (4u * ts)));
   const size_t per_warp = expand_warp_bytes(m, B, ts);

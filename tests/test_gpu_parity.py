@@ -118,6 +118,66 @@ def test_neuron_counts(gpu, m):
     assert_same(s, e)
 
 
+# --- rows of more than 128 neurons: built on demand by the whole warp ---
+
+@pytest.mark.parametrize("m,rules,chunk", [(129, (1, 2), 0), (130, (1, 3), 5), (150, (1, 4), 0),
+                                           (200, (2, 3), 1000), (257, (1, 2), 37), (1023, (1, 2), 0)])
+def test_wide_rows(gpu, m, rules, chunk):
+    """Block mode and crossing batches, rows with and without a multiple of
+    four neurons, one to four rules per neuron, several pass sizes."""
+    system = snp_synth.random_system(900 + m, m, rules, (1, 4), (0, 4), "sparse")
+    s, e = explore_both(gpu, system, 4, cap=2000, budget=20000, chunk=chunk)
+    assert_same(s, e)
+
+
+def few_choice_system(seed, m, k):
+    """Neurons 0 .. k-1 with two rules each (one or two spikes sent for one
+    consumed), the others with one rule (fire while holding a spike): at most
+    2^k spiking vectors per parent, so with k < 5 every candidate goes through
+    a crossing batch."""
+    rng = np.random.default_rng(seed)
+    rn, ri, rj, rc, rp = [], [], [], [], []
+    for n in range(m):
+        for p in ((1, 2) if n < k else (1,)):
+            rn.append(n)
+            ri.append(1)
+            rj.append(1)
+            rc.append(1)
+            rp.append(p)
+    targets = [sorted(rng.choice([t for t in range(m) if t != n], size=2, replace=False).tolist()) for n in range(m)]
+    c0 = [5] * k + rng.integers(0, 2, size=m - k).tolist()
+    return snp_synth.make_system(m, rn, ri, rj, rc, rp, targets, c0, name="few-choice")
+
+
+@pytest.mark.parametrize("m,k,chunk,depth", [(160, 2, 0, 6), (301, 3, 17, 6), (1024, 4, 0, 5)])
+def test_wide_rows_in_crossing_batches(gpu, m, k, chunk, depth):
+    s, e = explore_both(gpu, few_choice_system(m + k, m, k), depth, cap=3000, budget=30000, chunk=chunk)
+    assert_same(s, e)
+
+
+def many_duplicates_system(m, k):
+    """k neurons with two rules each, both consuming one spike, one sending a
+    spike to the last neuron and one forgetting: a parent's 2^k spiking vectors
+    give only k + 1 children, so most candidates meet a row that another lane
+    of the same warp has just claimed."""
+    rn, ri, rj, rc, rp = [], [], [], [], []
+    for n in range(k):
+        for p in (1, 0):
+            rn.append(n)
+            ri.append(1)
+            rj.append(1)
+            rc.append(1)
+            rp.append(p)
+    targets = [[m - 1] for _ in range(k)] + [[] for _ in range(m - k)]
+    return snp_synth.make_system(m, rn, ri, rj, rc, rp, targets, [3] * k + [0] * (m - k), name="duplicates")
+
+
+@pytest.mark.parametrize("m,k,chunk", [(64, 6, 0), (200, 6, 0), (200, 7, 9), (1024, 5, 0), (1022, 8, 100)])
+def test_duplicates_within_a_warp(gpu, m, k, chunk):
+    s, e = explore_both(gpu, many_duplicates_system(m, k), 4, chunk=chunk)
+    assert_same(s, e)
+
+
 def test_batch_style_systems(gpu):
     for system in snp_synth.batch_systems(6):
         s, e = explore_both(gpu, system, 4, cap=1 << 9, budget=1 << 13)
