@@ -574,6 +574,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
+    ap.add_argument("--cap", type=int, default=0, help="override the workload's frontier cap (profiling cases)")
+    ap.add_argument("--chunk", type=int, default=0, help="override the pass size (profiling cases)")
     ap.add_argument("--autotune", action="store_true", help="batch4096: pick pass size, tile and warps first")
     ap.add_argument("--requests", type=int, default=2000, help="serving: arrivals of the stream to run")
     ap.add_argument("--max-active", type=int, default=2048, help="serving: requests on the device at once")
@@ -583,6 +585,10 @@ def main():
     args = ap.parse_args()
     if args.depth > 0:
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], depth=args.depth)
+    if args.cap > 0:
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], cap=args.cap)
+    if args.chunk > 0:
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], chunk=args.chunk)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -445,6 +445,9 @@ struct ResumeFrom {
   int32_t nstats;
 };
 
+// Frontier rows whose Psi goes first when the last depth's Psi sum saturated.
+constexpr int64_t kPsiHead = 8192;
+
 int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags,
                  const ResumeFrom* rs) {
   g_err.clear();
@@ -533,6 +536,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   TRY(h->d_ctr.reserve(3 * sizeof(unsigned long long)));
 
   int64_t level_lo = 0, level_hi = 1;
+  bool psi_saturated_before = false;  // the last depth's Psi sum reached 2^64 - 1
   int d_start = 1;
   if (rs) {  // the checkpoint's rows become store rows 0 .. n-1, in discovery order
     h->n_rows = rs->n;
@@ -594,7 +598,17 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
     uint64_t* psi = h->d_psi.as<uint64_t>();
     CK(cudaMemsetAsync(psi + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, pperm, P, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
+    // When the previous depth's Psi sum saturated, the first rows alone may
+    // hold 2^64 - 1 candidates: they go first, and if they do, the rest are
+    // not read (no candidate and no statistic depends on them).
+    const int64_t P0 = psi_saturated_before && P > 2 * kPsiHead ? kPsiHead : P;
+    launch_psi(h->dev(), parents, pperm, P0, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
+    if (P0 < P) {
+      launch_psi_head_check(psi, P0, h->d_st.as<ChunkState>(), st);
+      launch_psi(h->dev(), parents, pperm + P0, P - P0, o->max_expand_value, psi + P0, nullptr,
+                 h->d_st.as<ChunkState>(), st, nsm);
+      sd.launches += 2;
+    }
     CK(cudaGetLastError());
     sd.launches += 1 + scan_u64_sat(psi, h->d_off.as<uint64_t>(), P + 1, h->d_scan_tmp.p, st);
     CK(cudaGetLastError());
@@ -603,6 +617,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     TRY(check_device_errors(h, st, "applicability scan"));
     total = *h->pin.u64;
     sd.candidates = total;
+    psi_saturated_before = total == ~0ull;
     // Parent records serve the batches that cross parents; with few
     // candidates per parent they are worth a second pass over the frontier.
     const bool with_records = !tc && P > 0 && total <= 256ull * (uint64_t)P;

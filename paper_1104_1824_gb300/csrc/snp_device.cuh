@@ -112,7 +112,7 @@ struct ChunkState {
   unsigned int total_first;   // distinct new keys in the chunk
   unsigned int capped;        // the cap was reached inside the chunk
   unsigned int last_lid;      // chunk-local index of the last accepted first occurrence
-  unsigned int pad;
+  unsigned int psi_saturated;  // Psi summed over the first parents already reached 2^64 - 1
   unsigned long long p_first;  // first and last frontier row the chunk's candidates come from
   unsigned long long p_last;
 };

@@ -44,8 +44,10 @@ struct ExpandSmem {
   int2* chg;                  // [m4] (old rule, new rule) pairs of the last block step
   int* hdr;                   // [8] kNnt, kNlow, kRL, kNchg, kNred; hbase at hdr + 6
   uint8_t* dig;               // [m4] digits of the block base
+  int32_t* low;               // wide mode: per low neuron (start, length), then the table of its
+                              // support columns and M[rule d] - M[rule 0] on them, d = 1 .. radix - 1
 };
-enum { kNnt = 0, kNlow = 1, kRL = 2, kNchg = 3, kNred = 4 };
+enum { kNnt = 0, kNlow = 1, kRL = 2, kNchg = 3, kNred = 4, kLowOk = 5 };
 __device__ __forceinline__ unsigned long long& hbase_of(const ExpandSmem& w) {
   return *reinterpret_cast<unsigned long long*>(w.hdr + 6);
 }
@@ -65,9 +67,13 @@ __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
 constexpr int kWideM = 128;
 constexpr int kWideB = 32;
 constexpr int kWide = 2;  // KIND of the wide mode
+// words of the low neurons' header: (start, length) per low neuron, then the
+// packed low digits of the block's candidates (5 bits per neuron); then the table
+constexpr int kLowDig = 16, kLowHdr = 48, kLowTab = 1536;
 __host__ __device__ inline size_t expand_wide_bytes(int m) {
   const int m4 = round4(m);
-  size_t b = (size_t)m4 * 4 + expand_keys_bytes(kWideB) + (size_t)m4 * 16 + 32 + (size_t)m4;
+  size_t b = (size_t)m4 * 4 + expand_keys_bytes(kWideB) + (size_t)m4 * 16 + 32 + (size_t)(kLowHdr + kLowTab) * 4 +
+             (size_t)m4;
   return (b + 15) & ~size_t(15);
 }
 
@@ -562,6 +568,7 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
   w.chg = reinterpret_cast<int2*>(w.ntl + m4);
   w.hdr = reinterpret_cast<int*>(w.chg + m4);
   w.dig = reinterpret_cast<uint8_t*>(w.hdr + 8);
+  w.low = nullptr;
   return w;
 }
 
@@ -582,7 +589,8 @@ __device__ __forceinline__ ExpandSmem expand_smem_wide(unsigned char* base, int 
   w.ntl = reinterpret_cast<int32_t*>(w.msk + m4);
   w.chg = nullptr;
   w.hdr = reinterpret_cast<int*>(w.ntl + m4);
-  w.dig = reinterpret_cast<uint8_t*>(w.hdr + 8);
+  w.low = w.hdr + 8;
+  w.dig = reinterpret_cast<uint8_t*>(w.low + kLowHdr + kLowTab);
   return w;
 }
 
@@ -592,6 +600,7 @@ __device__ __forceinline__ void warp_copy_row(const int32_t* src, int32_t* dst, 
   if (VEC) {
     const int4* a = reinterpret_cast<const int4*>(src);
     int4* b = reinterpret_cast<int4*>(dst);
+#pragma unroll 4
     for (int j = lane; j < (m >> 2); j += 32) b[j] = a[j];
   } else {
     for (int j = lane; j < m; j += 32) dst[j] = src[j];
@@ -600,12 +609,28 @@ __device__ __forceinline__ void warp_copy_row(const int32_t* src, int32_t* dst, 
 
 // row += M[rn] - M[ro] for two rules of one neuron, by the whole warp: the
 // columns of the neuron's support are distinct, so the lanes share them out.
+// A lane's loads for up to three support columns are all issued before its
+// updates, so that a support of up to 96 columns costs one round trip.
 __device__ __forceinline__ void warp_swap_rule(const DevSys& s, int32_t* row, int ro, int rn, int lane) {
   const int4 dn = __ldg(s.rdesc + rn);
   const int32_t* vn = s.rval + dn.z;
   const int32_t* vo = s.rval + __ldg(&s.rdesc[ro].z);
   const int32_t* col = s.scol + dn.x;
-  for (int i = lane; i < dn.y; i += 32) row[__ldg(col + i)] += __ldg(vn + i) - __ldg(vo + i);
+  for (int i0 = 0; i0 < dn.y; i0 += 96) {
+    int c[3], v[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int i = i0 + lane + 32 * u;
+      c[u] = -1;
+      if (i < dn.y) {
+        c[u] = __ldg(col + i);
+        v[u] = __ldg(vn + i) - __ldg(vo + i);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      if (c[u] >= 0) row[c[u]] += v[u];
+  }
   __syncwarp();
 }
 
@@ -616,14 +641,78 @@ __device__ __forceinline__ void build_block_row(const DevSys& s, ExpandSmem& w, 
   __syncwarp();
   warp_copy_row<VEC>(w.buf, w.tile, s.m, lane);
   __syncwarp();
-  uint32_t q = (uint32_t)L;
+  const bool tab = w.hdr[kLowOk] != 0;
+  const uint32_t pk = (uint32_t)w.low[kLowDig + L];
   for (int i = 0; i < nlow; ++i) {
+    const uint32_t d = (pk >> (5 * i)) & 31u;
+    if (d == 0) continue;
     const int n = w.ntl[i];
-    const uint32_t radix = __popc(w.msk[n]);
-    const uint32_t d = q % radix;
-    q /= radix;
-    if (d != 0) warp_swap_rule(s, w.tile, rule_of(s, w, n, 0), rule_of(s, w, n, (int)d), lane);
+    if (tab) {  // the support's columns are distinct: a lane reads its three before it writes them
+      const int len = w.low[2 * i + 1];
+      const int32_t* col = w.low + kLowHdr + w.low[2 * i];
+      const int32_t* dv = col + (int)d * len;
+      for (int k0 = 0; k0 < len; k0 += 96) {
+        int c[3], v[3], x[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          const int k = k0 + lane + 32 * u;
+          c[u] = k < len ? col[k] : -1;
+          v[u] = k < len ? dv[k] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 3; ++u) x[u] = c[u] >= 0 ? w.tile[c[u]] : 0;
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+          if (c[u] >= 0) w.tile[c[u]] = x[u] + v[u];
+      }
+      __syncwarp();
+    } else {
+      warp_swap_rule(s, w.tile, rule_of(s, w, n, 0), rule_of(s, w, n, (int)d), lane);
+    }
   }
+}
+
+// The low neurons' swap table of the loaded parent (by the whole warp): for
+// low neuron i, its support columns, then for each choice d > 0 the support's
+// entries of M[rule d] - M[rule 0].  Left unused (kLowOk = 0) when it does not
+// fit in kLowTab words.
+__device__ __forceinline__ void build_low_table(const DevSys& s, ExpandSmem& w, int lane) {
+  const int nlow = w.hdr[kNlow];
+  if (lane < w.hdr[kRL]) {  // RL <= 32 with every radix >= 2: at most 5 low neurons, digits < 32
+    uint32_t q = (uint32_t)lane, pk = 0;
+    for (int i = 0; i < nlow; ++i) {
+      const uint32_t radix = __popc(w.msk[w.ntl[i]]);
+      pk |= (q % radix) << (5 * i);
+      q /= radix;
+    }
+    w.low[kLowDig + lane] = (int32_t)pk;
+  }
+  int at = 0;
+  bool fits = true;
+  for (int i = 0; fits && i < nlow; ++i) {
+    const int n = w.ntl[i];
+    const int radix = __popc(w.msk[n]);
+    const int4 d0 = __ldg(s.rdesc + rule_of(s, w, n, 0));
+    const int len = d0.y;
+    if (at + len * radix > kLowTab) {
+      fits = false;
+      break;
+    }
+    int32_t* t = w.low + kLowHdr + at;
+    for (int k = lane; k < len; k += 32) t[k] = __ldg(s.scol + d0.x + k);
+    for (int d = 1; d < radix; ++d) {
+      const int vz = __ldg(&s.rdesc[rule_of(s, w, n, d)].z);
+      for (int k = lane; k < len; k += 32) t[d * len + k] = __ldg(s.rval + vz + k) - __ldg(s.rval + d0.z + k);
+    }
+    if (lane == 0) {
+      w.low[2 * i] = at;
+      w.low[2 * i + 1] = len;
+    }
+    at += len * radix;
+  }
+  __syncwarp();
+  if (lane == 0) w.hdr[kLowOk] = fits ? 1 : 0;
+  __syncwarp();
 }
 
 // Row of candidate t of parent pc (a crossing-batch candidate) in the scratch
@@ -684,6 +773,7 @@ __device__ __forceinline__ void warp_store_row(const int32_t* row, int32_t* dst,
   if (VEC) {
     const int4* a = reinterpret_cast<const int4*>(row);
     int4* b = reinterpret_cast<int4*>(dst);
+#pragma unroll 4
     for (int j = lane; j < (m >> 2); j += 32) __stcg(b + j, a[j]);
   } else {
     for (int j = lane; j < m; j += 32) __stcg(dst + j, row[j]);
@@ -864,6 +954,7 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   const uint64_t gend = min(p_hi, a.g0 + lb);
   if (p != cached_p) {
     after = parent_state(s, parent_row(a, p), w, kWideB, lane);
+    build_low_table(s, w, lane);
     cached_p = p;
   }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
@@ -1167,10 +1258,12 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const int m = a.sys.m;
   if (m > kWideM) {
     const size_t per_warp = expand_wide_bytes(m);
-    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (220u << 10) / per_warp));
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (226u << 10) / per_warp));
     const size_t smem = per_warp * wpb;
-    const uint64_t two_per_warp = 2ull * nsm * wpb;
-    a.run = (uint32_t)std::max<uint64_t>(8ull * kWideB, ((uint64_t)a.Q + two_per_warp - 1) / two_per_warp);
+    // one task per warp: a task's first block costs a full decode (C + S . M
+    // over every neuron), which wide rows make expensive
+    const uint64_t warps = (uint64_t)nsm * wpb;
+    a.run = (uint32_t)std::max<uint64_t>(8ull * kWideB, ((uint64_t)a.Q + warps - 1) / warps);
     const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
     const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm);
     auto fn = (m % 4) == 0 ? k_expand_wide<true> : k_expand_wide<false>;

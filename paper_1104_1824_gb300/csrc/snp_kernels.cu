@@ -91,6 +91,11 @@ template <bool REC>
 __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
                                              int32_t max_expand, uint64_t* psi, ParentRec* rec, ChunkState* st) {
   const int m = s.m;
+  if (st && __ldcg(&st->psi_saturated)) {  // these rows lie past the last candidate: Psi is not needed
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x)
+      psi[p] = 0;
+    return;
+  }
   bool over = false;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += (int64_t)gridDim.x * blockDim.x) {
     const int32_t* row = rows + (size_t)(perm ? __ldg(perm + p) : (uint64_t)p) * m;
@@ -119,6 +124,10 @@ __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t*
   __shared__ int32_t slab[kPsiRows][kPsiSlab + 1];
   const int m = s.m;
   const int t = threadIdx.x;
+  if (st && __ldcg(&st->psi_saturated)) {  // as in k_psi
+    for (int64_t p = (int64_t)blockIdx.x * kPsiRows + t; p < P; p += (int64_t)gridDim.x * kPsiRows) psi[p] = 0;
+    return;
+  }
   bool over = false;
   for (int64_t p0 = (int64_t)blockIdx.x * kPsiRows; p0 < P; p0 += (int64_t)gridDim.x * kPsiRows) {
     const int nrows = (int)min((int64_t)kPsiRows, P - p0);
@@ -152,6 +161,28 @@ __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t*
     }
   }
   if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
+}
+
+// st->psi_saturated = 1 when the saturating sum of psi[0 .. n) is 2^64 - 1
+// (one block).
+__global__ void __launch_bounds__(1024) k_psi_head_saturated(const uint64_t* psi, int64_t n, ChunkState* st) {
+  __shared__ uint64_t part[32];
+  uint64_t v = 0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v = sat_add(v, psi[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = sat_add(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = sat_add(t, part[w]);
+    if (t == kSat) st->psi_saturated = 1u;
+  }
+}
+
+int launch_psi_head_check(const uint64_t* psi, int64_t n, ChunkState* st, cudaStream_t stream) {
+  k_psi_head_saturated<<<1, 1024, 0, stream>>>(psi, n, st);
+  return 1;
 }
 
 int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, int32_t max_expand, uint64_t* psi,

@@ -115,6 +115,10 @@ __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0
 int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, int32_t max_expand, uint64_t* psi,
                ParentRec* rec, ChunkState* st,
                cudaStream_t stream, int nsm);
+// Sets st->psi_saturated when Psi summed (saturating) over psi[0 .. n) is
+// 2^64 - 1: later frontier rows then hold no candidate, and launch_psi with
+// that st writes Psi = 0 for them without reading them.
+int launch_psi_head_check(const uint64_t* psi, int64_t n, ChunkState* st, cudaStream_t stream);
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
 // Step (d) for candidate rows already in global memory (rows[lid * m], hash[lid]).

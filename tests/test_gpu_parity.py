@@ -155,6 +155,32 @@ def test_wide_rows_in_crossing_batches(gpu, m, k, chunk, depth):
     assert_same(s, e)
 
 
+def broadcast_system(m, k, seed):
+    """Neurons 0 .. k-1 with two rules each and a synapse to every other
+    neuron, the others with one rule and two synapses: the supports of the
+    multi-choice neurons are too large for the low neurons' swap table, so
+    rows are built with swaps read from global memory."""
+    rng = np.random.default_rng(seed)
+    rn, ri, rj, rc, rp = [], [], [], [], []
+    for n in range(m):
+        for p in ((1, 2) if n < k else (1,)):
+            rn.append(n)
+            ri.append(1)
+            rj.append(1)
+            rc.append(1)
+            rp.append(p)
+    targets = [[t for t in range(m) if t != n] if n < k else
+               sorted(rng.choice([t for t in range(m) if t != n], size=2, replace=False).tolist()) for n in range(m)]
+    c0 = [3] * k + rng.integers(0, 2, size=m - k).tolist()
+    return snp_synth.make_system(m, rn, ri, rj, rc, rp, targets, c0, name="broadcast")
+
+
+@pytest.mark.parametrize("m,k,chunk", [(800, 6, 0), (801, 7, 50)])
+def test_wide_rows_with_large_supports(gpu, m, k, chunk):
+    s, e = explore_both(gpu, broadcast_system(m, k, m), 3, cap=800, budget=6000, chunk=chunk)
+    assert_same(s, e)
+
+
 def many_duplicates_system(m, k):
     """k neurons with two rules each, both consuming one spike, one sending a
     spike to the last neuron and one forgetting: a parent's 2^k spiking vectors
@@ -176,6 +202,47 @@ def many_duplicates_system(m, k):
 def test_duplicates_within_a_warp(gpu, m, k, chunk):
     s, e = explore_both(gpu, many_duplicates_system(m, k), 4, chunk=chunk)
     assert_same(s, e)
+
+
+def saturating_system(kind):
+    """'steady': 100 neurons with two rules each (a+ / a -> a or a^2) that stay
+    applicable, so every configuration has 2^100 spiking vectors.  'drain': 70
+    neurons with one spike and two rules (a -> lambda, a -> a into a private
+    sink): the root has 2^70 spiking vectors, its children have one each."""
+    rn, ri, rj, rc, rp = [], [], [], [], []
+    if kind == "steady":
+        m = 100
+        for n in range(m):
+            for p in (1, 2):
+                rn += [n]
+                ri += [1]
+                rj += [1]
+                rc += [1]
+                rp += [p]
+        targets = [[(n + 1) % m, (n + 7) % m] for n in range(m)]
+        return snp_synth.make_system(m, rn, ri, rj, rc, rp, targets, [6] * m, name="steady")
+    k = 70
+    for n in range(k):
+        for p in (0, 1):
+            rn += [n]
+            ri += [1]
+            rj += [0]
+            rc += [1]
+            rp += [p]
+    targets = [[k + n] for n in range(k)] + [[] for _ in range(k)]
+    return snp_synth.make_system(2 * k, rn, ri, rj, rc, rp, targets, [1] * k + [0] * k, name="drain")
+
+
+@pytest.mark.parametrize("kind", ["steady", "drain"])
+def test_saturated_psi_sums(gpu, kind):
+    """Frontiers of 20000 rows after a depth whose Psi sum saturated: the
+    first 8192 rows go first, and the rest are read only when those do not
+    already give 2^64 - 1 candidates ('steady': they do; 'drain': they
+    do not)."""
+    s, e = explore_both(gpu, saturating_system(kind), 3, cap=20000, budget=1 << 16)
+    assert_same(s, e)
+    assert e.depths[1].candidates == 2**64 - 1
+    assert (e.depths[2].candidates == 2**64 - 1) == (kind == "steady")
 
 
 def test_batch_style_systems(gpu):
