@@ -273,7 +273,8 @@ def bench_ours(args):
         achieved = expand_bytes / (expand_ms * 1e-3) / 1e9 if expand_ms > 0 else None
         traffic = profiled_traffic(args.workload)
         roofline = {
-            "kernel": "k_expand (decode, C' = C + S.M, hash, probe/compare/claim)",
+            "kernel": ("k_expand_wide" if system.m > 128 else "k_expand") +
+                      " (decode, C' = C + S.M, hash, probe/compare/claim)",
             "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
             "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
             "frac": round(achieved / peak, 4) if achieved else None,

@@ -64,7 +64,6 @@ __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
 
 // Wide rows (more than kWideM neurons): a warp keeps one scratch row instead
 // of one row per lane, and queues up to 32 crossing-batch candidates.
-constexpr int kWideM = 128;
 constexpr int kWideB = 32;
 constexpr int kWide = 2;  // KIND of the wide mode
 // words of the low neurons' header: (start, length) per low neuron, then the
@@ -187,6 +186,7 @@ __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const int32_t*
 // The block base becomes candidate t of the loaded parent: digits, child in
 // buf, hash, and the count of neurons whose digit picks a rule that repeats an
 // earlier applicable rule's row.
+template <bool WIDE = false>
 __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint64_t t, uint64_t after, int lane) {
   for (int n = lane; n < s.m; n += 32) w.buf[n] = w.par[n];
   uint64_t hp = 0;
@@ -213,7 +213,19 @@ __device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint
     }
     w.dig[n] = (uint8_t)d;
     const int r = __ldg(s.first_rule + n) + nth_set_bit(mask, (int)d);
-    add_row_shared(s, w.buf, r, 1);
+    if (WIDE) {  // long rows of M_Pi: eight loads in flight before their adds
+      const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
+      for (int e = e0; e < e1; e += 8) {
+        int2 cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) cv[u] = e + u < e1 ? __ldg(s.csr + e + u) : make_int2(-1, 0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (cv[u].x >= 0) atomicAdd(&w.buf[cv[u].x], cv[u].y);
+      }
+    } else {
+      add_row_shared(s, w.buf, r, 1);
+    }
     hp += __ldg(s.rowkey + r);
     red += redundant_choice(s, mask, r) ? 1 : 0;
   }
@@ -959,7 +971,7 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
   const uint64_t b = (g - p_lo) / (uint64_t)RL;
-  decode_full(s, w, b * (uint64_t)RL, after, lane);
+  decode_full<true>(s, w, b * (uint64_t)RL, after, lane);
   uint64_t hk = 0;
   bool redk = true;
   if (lane < RL) {

@@ -120,6 +120,9 @@ int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, i
 // that st writes Psi = 0 for them without reading them.
 int launch_psi_head_check(const uint64_t* psi, int64_t n, ChunkState* st, cudaStream_t stream);
 // Steps (b)-(d) for the chunk's candidates (k_expand); returns the launches made.
+// Rows of more than kWideM neurons go through the kernel's wide mode (one
+// scratch row per warp, rows built on demand).
+constexpr int kWideM = 128;
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm);
 // Step (d) for candidate rows already in global memory (rows[lid * m], hash[lid]).
 // Candidates with redundant[lid] set repeat an earlier candidate and are skipped.
