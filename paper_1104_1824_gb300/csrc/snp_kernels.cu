@@ -111,6 +111,38 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, cons
   if (__any_sync(0xffffffffu, over) && (threadIdx.x & 31) == 0) set_error(st, kErrOverflow);
 }
 
+// k_psi for small frontiers (no records): a warp per row, lane l visiting
+// neurons l, l + 32, ... (coalesced), the lanes' products combined with the
+// saturating product, so that a row of many neurons is not one thread's
+// serial walk.
+__global__ void __launch_bounds__(256) k_psi_warp(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
+                                                  int32_t max_expand, uint64_t* psi, ChunkState* st) {
+  const int m = s.m;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (st && __ldcg(&st->psi_saturated)) {  // as in k_psi
+    for (int64_t p = w0; p < P; p += nw)
+      if (lane == 0) psi[p] = 0;
+    return;
+  }
+  bool over = false;
+  for (int64_t p = w0; p < P; p += nw) {
+    const int32_t* row = rows + (size_t)(perm ? __ldg(perm + p) : (uint64_t)p) * m;
+    PsiAcc acc;
+    for (int n = lane; n < m; n += 32) acc.visit<false>(s, n, __ldg(row + n), max_expand, nullptr);
+    acc.flush();
+    uint64_t v = acc.prod;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = sat_mul(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const bool skip = __any_sync(0xffffffffu, acc.skip);
+    const bool ov = __any_sync(0xffffffffu, acc.ov);
+    if (lane == 0) psi[p] = skip ? 0ull : v;
+    over |= ov && !skip;
+  }
+  if (over && lane == 0) set_error(st, kErrOverflow);
+}
+
 // k_psi for m % 4 == 0 with coalesced loads: a block takes 256 rows at a
 // time and moves them through shared memory 32 columns at a time (each row's
 // slab is 128 contiguous bytes, read by 8 consecutive threads); thread t then
@@ -190,6 +222,11 @@ int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, i
   const int threads = 256;
   const int64_t want = (P + threads - 1) / threads;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
+  if (!rec && P <= (int64_t)nsm * 256) {  // a warp per row
+    const int wb = (int)std::max<int64_t>(1, (P + 7) / 8);
+    k_psi_warp<<<wb, 256, 0, stream>>>(s, rows, perm, P, max_expand, psi, st);
+    return 1;
+  }
   if ((s.m % 4) == 0) {
     const int64_t tiles = (P + kPsiRows - 1) / kPsiRows;
     const int tb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * 6));
