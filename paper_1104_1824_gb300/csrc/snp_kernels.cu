@@ -169,10 +169,12 @@ __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t*
       const int w = min(kPsiSlab, m - n0);  // columns in this slab (a multiple of 4)
       const int q4 = w >> 2;                // 16-byte pieces per row
       __syncthreads();
+      // rows stream through L2 only, so that they do not evict the
+      // applicability table every visit reads from L1
       for (int i = t; i < nrows * q4; i += kPsiRows) {
         const int r = i / q4, q = i - r * q4;
-        const uint64_t pr = perm ? __ldg(perm + p0 + r) : (uint64_t)(p0 + r);
-        const int4 v = __ldg(reinterpret_cast<const int4*>(rows + (size_t)pr * m + n0) + q);
+        const uint64_t pr = perm ? __ldcg(perm + p0 + r) : (uint64_t)(p0 + r);
+        const int4 v = __ldcg(reinterpret_cast<const int4*>(rows + (size_t)pr * m + n0) + q);
         int32_t* d = &slab[r][4 * q];
         d[0] = v.x;
         d[1] = v.y;
