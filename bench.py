@@ -17,7 +17,9 @@ system from host arrays, explores, and copies every configuration back to
 pinned host memory; wall clock around all of it.
 
 With --gpus N > 1 (torchrun), every rank explores its own copy of the system
-(replicas: one system's BFS is not sharded); the value aggregates all ranks.
+(replicas: one system's BFS is not sharded); the batch workload gives rank r
+its own block of 4096 systems (seeds 1000 + 4096 r ...).  The value aggregates
+all ranks.
 --impl reference times the CPU oracle on bounded samples instead.
 """
 from __future__ import annotations
@@ -72,11 +74,33 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def make_system(name):
+def aggregate_ranks(ms: float, counts, dist=None, device=None):
+    """The job's time and totals: the max over ranks of the timed region (ms)
+    and the sums over ranks of `counts` (units processed, launches, ...).
+    Without a process group (one rank) the inputs come back unchanged."""
+    counts = [float(c) for c in counts]
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return ms, counts
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(counts, device=device, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), [float(x) for x in c.tolist()]
+
+
+def batch_seed_base(w, rank: int) -> int:
+    """First seed of the systems rank `rank` explores: ranks take consecutive
+    blocks of w["n"] independent systems (a shard of an N x n batch; no data
+    is exchanged between ranks)."""
+    return w["base_seed"] + rank * w["n"]
+
+
+def make_system(name, rank: int = 0):
     import snp_synth
     w = WORKLOADS[name]
     if name == "batch4096":
-        return snp_synth.batch_systems(w["n"], w["base_seed"])
+        return snp_synth.batch_systems(w["n"], batch_seed_base(w, rank))
     return snp_synth.random_64(w["seed"]) if name == "random64" else snp_synth.dense_1024(w["seed"])
 
 
@@ -203,7 +227,7 @@ def bench_ours(args):
     w = WORKLOADS[args.workload]
     if args.workload == "serving":
         return bench_serving(args, w, snp, torch, rank)
-    system = make_system(args.workload)
+    system = make_system(args.workload, rank)
     if args.workload == "batch4096":
         return bench_batch(args, w, system, snp, torch, dist, dev, rank, world, local)
     s = snp.System(system)
@@ -241,15 +265,8 @@ def bench_ours(args):
     ms = ev0.elapsed_time(ev1)
     per_depth = [{"depth": d, "new": x.new, "examined": x.examined, "chunks": x.chunks, "ms": round(x.ms, 4),
                   "new_per_s": round(x.new / (x.ms * 1e-3)) if x.ms > 0 else None} for d, x in enumerate(st) if d > 0]
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-        t = torch.tensor([float(total_new), float(launches)], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        total_all, launches_all = int(t[0].item()), int(t[1].item())
-    else:
-        ms_max, total_all, launches_all = ms, total_new, launches
+    ms_max, (total_all, launches_all) = aggregate_ranks(ms, [total_new, launches], dist if world > 1 else None, dev)
+    total_all, launches_all = int(total_all), int(launches_all)
     value = total_all / (ms_max * 1e-3)
 
     nlaunch_expand = sum(x.chunks for x in st) * args.steps
@@ -320,8 +337,8 @@ def bench_ours(args):
 
 
 def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
-    """Each rank explores its own copy of all systems (the systems would shard
-    across ranks without any exchange: weak scaling)."""
+    """Each rank explores its own block of n independent systems (seeds
+    batch_seed_base(w, rank) ...): weak scaling, no exchange between ranks."""
     import numpy as np
     handles = [snp.System(x) for x in systems]
     hs = [h.h for h in handles]
@@ -363,13 +380,8 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
             bytes_step += a.examined * 8 + dups * row + a.new * (row + 8) + a.new * 2 * row + a.parents * row
             per_depth.setdefault(d, 0)
             per_depth[d] += a.new
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    else:
-        ms_max = ms
-    total_all = new_step * args.steps * world
+    ms_max, (total_all,) = aggregate_ranks(ms, [new_step * args.steps], dist if world > 1 else None, dev)
+    total_all = int(total_all)
     value = total_all / (ms_max * 1e-3)
     peak, peak_kind = measured_peaks()
     achieved = bytes_step * args.steps / (ms * 1e-3) / 1e9
@@ -412,7 +424,8 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
                                 "autotune_s": round(tune_s, 2)},
                        "new_per_step": new_step, "per_depth_new": [per_depth[d] for d in sorted(per_depth)],
                        "l2": "inputs larger than L2 (pools of all systems, tens of GB)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": f"dp{world}: rank r explores systems of seeds {w['base_seed']} + {w['n']} r ..."
+                       if world > 1 else "single GPU"},
             "roofline": {"kernel": "k_batch_depth (one launch per depth, all systems)", "bound": "hbm",
                          "achieved": round(achieved, 1), "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth",
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
