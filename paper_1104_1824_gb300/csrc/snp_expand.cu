@@ -20,6 +20,13 @@
 //   Surviving candidates are queued in the tile and their rows built all at
 //   once before they are resolved.
 //
+// Rows of more than kWideM neurons (k_expand_wide) are too long for a row per
+// lane: lanes keep only their candidates' hashes and probe for them, and the
+// whole warp builds a row in one scratch row when it has to be compared with
+// a stored row or written by the lane that claimed its key; the odometer's
+// swaps go into the block base itself, and the low neurons' swaps come from a
+// per-parent table in shared memory.
+//
 // Resolving a row (step d): probe the hash table, compare full keys, and
 // either find the key (seen before, or claimed earlier in this chunk: then
 // lower that key's first-occurrence index) or claim an empty slot, write the
