@@ -1,0 +1,38 @@
+"""Host-side helpers of bench.py that need no GPU: the code-only hash that ties
+a committed ncu summary to the kernel sources it was taken on."""
+import bench
+
+
+def test_comments_and_blank_lines_do_not_count():
+    a = "int f(int x) {\n  return x + 1;  // add one\n}\n"
+    b = "/* header\n   over two lines */\nint f(int x) {\n\n  return x + 1;\n}\n"
+    assert bench.strip_comments(a) == bench.strip_comments(b) == "int f(int x) {\n  return x + 1;\n}"
+
+
+def test_code_and_literals_count():
+    assert bench.strip_comments("int a = 1;") != bench.strip_comments("int a = 2;")
+    s = "const char* p = \"a // not a comment /* nor this */\"; char c = '/';"
+    assert bench.strip_comments(s) == s
+    q = r'const char* q = "say \"//\" twice"; int y;'
+    assert bench.strip_comments(q + "  // gone") == q
+
+
+def _fake_tree(tmp_path, monkeypatch, code):
+    csrc = tmp_path / "paper_1104_1824_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text(code)
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return csrc / "k.cu"
+
+
+def test_profiled_traffic_follows_the_code(tmp_path, monkeypatch):
+    src = _fake_tree(tmp_path, monkeypatch, "__global__ void k() {}\n")
+    prof = tmp_path / "profiles" / "expand_kernel_w.txt"
+    prof.write_text(f"# summary\nkernel_source_hash: {bench.kernel_source_hash()}\ndram_bytes_per_candidate: 12.5\n")
+    assert bench.profiled_traffic("w") == {"bytes_per_candidate": 12.5}
+    src.write_text("// the kernel\n__global__ void k() {}  // empty\n\n")
+    assert bench.profiled_traffic("w") == {"bytes_per_candidate": 12.5}
+    src.write_text("__global__ void k() { int x = 0; }\n")
+    assert bench.profiled_traffic("w") is None
+    assert bench.profiled_traffic("other") is None
