@@ -108,7 +108,14 @@ typedef struct {
  *                    in some neuron is recorded but not expanded; < 0: off.
  *  record_parents    1: remember, per configuration, its parent's discovery
  *                    index and the spiking vector's index (snp_parents).
- *  chunk             candidates per device pass; <= 0 chooses automatically.
+ *  chunk             candidates per device pass; <= 0 chooses automatically:
+ *                    up to 2^22 while the rows a pass may claim stay within
+ *                    512 MiB, at least 2^20; 2^21 for systems of more than
+ *                    128 neurons while the store's reserve for claims past
+ *                    the cap (one pass per depth) stays within 64 GiB; the
+ *                    last passes of a capped depth are shortened to what the
+ *                    cap is expected to take; 65536 at most in the
+ *                    tensor-core form.
  *  stream            cudaStream_t to run on, or NULL for the default stream.
  *  kernel_timing     1: time the expand kernel of every pass with CUDA events
  *                    on `stream` (snp_depth_info.expand_ms).
