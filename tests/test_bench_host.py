@@ -36,3 +36,56 @@ def test_profiled_traffic_follows_the_code(tmp_path, monkeypatch):
     src.write_text("__global__ void k() { int x = 0; }\n")
     assert bench.profiled_traffic("w") is None
     assert bench.profiled_traffic("other") is None
+
+
+def test_e2e_steps_load_explore_and_read_back_every_time():
+    """Every timed e2e step goes through the C ABI from host arrays to a full
+    read-back; only the pinned result buffer is sized in an untimed step."""
+    import types
+
+    import torch
+
+    import snp_synth
+
+    calls = []
+
+    class FakeLibrary:
+        SNP_T_TC_I8, SNP_T_SPARSE_I32 = 1, 0
+
+        def snp_load_system(self, m, *arrays):
+            calls.append("load")
+            return object()
+
+        def snp_explore_opts_init(self):
+            return types.SimpleNamespace()
+
+        def snp_explore(self, h, o):
+            calls.append("explore")
+
+        def snp_reachable_count(self, h):
+            return 10
+
+        def snp_reachable(self, h, out, n):
+            calls.append("read")
+
+        def snp_free(self, h):
+            calls.append("free")
+
+    class TorchOnCpu:
+        int32 = torch.int32
+
+        class cuda:
+            @staticmethod
+            def synchronize():
+                pass
+
+        @staticmethod
+        def empty(shape, dtype, pin_memory):
+            calls.append("alloc")
+            return torch.empty(shape, dtype=dtype)
+
+    args = types.SimpleNamespace(steps=5, transition="sparse")
+    r = bench.bench_e2e(args, snp_synth.random_64(1), bench.WORKLOADS["random64"], FakeLibrary(), TorchOnCpu, None)
+    step = ["load", "explore", "read", "free"]
+    assert calls == ["load", "explore", "alloc", "read", "free"] + step * 3
+    assert r["steps"] == 3 and r["d2h_bytes_per_step"] == 10 * 64 * 4 and r["h2d_bytes_per_step"] > 0
