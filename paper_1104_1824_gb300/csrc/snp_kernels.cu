@@ -2,10 +2,15 @@
 //
 // One depth (Algorithm 1, one round of steps II-IV) runs as:
 //   k_psi      step (a) for every frontier configuration: applicable rules and
-//              Psi = prod_n max(1, omega_n) (Eq. psi), saturating;
+//              Psi = prod_n max(1, omega_n) (Eq. psi), saturating (k_psi_tiled
+//              for rows of a multiple of four neurons, k_psi_warp with a warp
+//              per row for small frontiers; after a depth whose Psi sum
+//              saturated, k_psi_head_saturated lets the rows past the first
+//              8192 be skipped when those already hold 2^64 - 1 candidates);
 //   scan       exclusive prefix sums of Psi give each parent's first candidate;
 //   per chunk of candidates [g0, g0 + Q) in canonical order:
-//     k_expand steps (b)-(d) (snp_expand.cu): decode the spiking vector, C' = C + S . M_Pi
+//     k_expand steps (b)-(d) (snp_expand.cu; k_expand_wide for rows of more
+//              than kWideM neurons): decode the spiking vector, C' = C + S . M_Pi
 //              (Eq. next-config), fingerprint, look C' up; a key never seen is
 //              claimed in the table and its row written (to the store, or to
 //              staging row lid), and every candidate holding such a pending
