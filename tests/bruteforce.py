@@ -11,7 +11,7 @@ from __future__ import annotations
 import itertools
 import re
 from functools import lru_cache
-from typing import Dict, List, Sequence, Tuple
+from typing import Dict, List, Tuple
 
 import numpy as np
 

@@ -14,7 +14,7 @@ import pytest
 import bruteforce as bf
 import oracle
 import snp_synth
-from conftest import GOLDEN, parse_configs, read_golden
+from conftest import GOLDEN, read_golden
 
 pytestmark = pytest.mark.gpu
 

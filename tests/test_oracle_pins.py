@@ -14,7 +14,7 @@ import pytest
 import bruteforce as bf
 import oracle
 import snp_synth
-from conftest import parse_configs, parse_literal, read_golden
+from conftest import parse_literal, read_golden
 
 
 @pytest.fixture(scope="module")
