@@ -51,6 +51,7 @@ extern "C" {
 /* Transition forms for step (c). */
 #define SNP_T_SPARSE_I32 0 /* gather over M_Pi's nonzeros, int32 on the CUDA cores */
 #define SNP_T_TC_I8 1      /* dense 0/1 x int8 tensor-core product (mma.sync s8), int32 accumulation */
+#define SNP_T_TC_F8 2      /* e4m3 tensor-core product on tcgen05 (TMEM, fp32 accumulation, exact for |M| <= 16) */
 
 /* Saturation value of Psi and of sums of Psi: "at least 2^64 - 1". */
 #define SNP_PSI_SAT UINT64_MAX
@@ -99,7 +100,16 @@ typedef struct {
  *  depth             number of BFS expansions (depth >= 0).  Exploration ends
  *                    earlier when a depth finds no new configuration
  *                    (Algorithm 1, stopping criteria).
- *  transition        SNP_T_SPARSE_I32 or SNP_T_TC_I8.
+ *  transition        SNP_T_SPARSE_I32, SNP_T_TC_I8 or SNP_T_TC_F8.  The
+ *                    tensor-core forms compute Eq. next-config as a matrix
+ *                    product: SNP_T_TC_I8 the whole product S . M_Pi with
+ *                    int8 operands; SNP_T_TC_F8 tiles of 128 candidates of
+ *                    one parent as C_ref + (S - S_ref) . M_Pi over the 32-rule
+ *                    blocks in which S differs from a reference spiking
+ *                    vector S_ref (the full S . M_Pi for tiles crossing
+ *                    parents and rows of at most 128 neurons), e4m3 operands
+ *                    and fp32 accumulation, exact because every partial sum
+ *                    is an integer below 2^24.
  *  frontier_cap      most new configurations accepted per depth; <= 0: no cap.
  *                    The accepted ones are the first ones in candidate order.
  *  candidate_budget  most candidates (parent, spiking vector) examined per
@@ -115,7 +125,7 @@ typedef struct {
  *                    the cap (one pass per depth) stays within 64 GiB; the
  *                    last passes of a capped depth are shortened to what the
  *                    cap is expected to take; 65536 at most in the
- *                    tensor-core form.
+ *                    int8 tensor-core form, 2^20 at most in the fp8 form.
  *  stream            cudaStream_t to run on, or NULL for the default stream.
  *  kernel_timing     1: time the expand kernel of every pass with CUDA events
  *                    on `stream` (snp_depth_info.expand_ms).
@@ -153,11 +163,12 @@ typedef struct {
   int32_t chunks;        /* device passes used */
   float ms;              /* device time of the depth (CUDA events) */
   float expand_ms;       /* device time of the expand kernel (kernel_timing) */
-  int64_t expand_bytes;  /* algorithmic DRAM bytes of the expand kernel: per
-                            candidate an 8-byte slot probe, per duplicate a
-                            4m-byte key compare, per new key a 4m-byte row
-                            write and an 8-byte slot write, per parent a 4m-byte
-                            row read */
+  int64_t expand_bytes;  /* algorithmic DRAM bytes of the expand kernel, over
+                            the candidates examined: per candidate an 8-byte
+                            slot probe, per candidate not accepted a 4m-byte
+                            key compare, per accepted configuration a 4m-byte
+                            row write and an 8-byte slot write, per parent a
+                            4m-byte row read */
   int64_t launches;      /* kernels launched for this depth */
 } snp_depth_info;
 
@@ -190,7 +201,8 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
  * truncated_flags (host, [opts->depth + 1], may be NULL) receives 1 for each
  * depth stopped by the cap or the budget.  A new call discards the previous
  * exploration.  Errors: SNP_E_INVALID, SNP_E_RANGE (SNP_T_TC_I8 with an entry
- * of M_Pi outside [-127, 127]), SNP_E_NOMEM, SNP_E_OVERFLOW, SNP_E_TIMEOUT,
+ * of M_Pi outside [-127, 127], SNP_T_TC_F8 with one outside [-16, 16]),
+ * SNP_E_NOMEM, SNP_E_OVERFLOW, SNP_E_TIMEOUT,
  * SNP_E_INTERNAL, SNP_E_CUDA. */
 int snp_explore(snp_handle h, const snp_explore_opts* opts, int32_t* depth_reached, int32_t* truncated_flags);
 

@@ -33,6 +33,7 @@ SNP_E_STATE = 8
 SNP_E_INTERNAL = 9
 SNP_T_SPARSE_I32 = 0
 SNP_T_TC_I8 = 1
+SNP_T_TC_F8 = 2
 SNP_PSI_SAT = (1 << 64) - 1
 
 ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOMEM", 4: "SNP_E_CUDA",

@@ -109,6 +109,53 @@ int tc_prepare(snp_system* h, uint64_t q, cudaStream_t st) {
   return SNP_OK;
 }
 
+// e4m3 byte of an integer v with |v| <= 16 (exact: 1 sign, 4 exponent bits
+// with bias 7, 3 mantissa bits).
+uint8_t e4m3_of_int(int v) {
+  if (v == 0) return 0;
+  const int a = std::abs(v);
+  int e = 0;
+  while ((2 << e) <= a) ++e;
+  const int mant = ((a << 3) >> e) - 8;
+  return (uint8_t)((v < 0 ? 0x80 : 0) | ((e + 7) << 3) | mant);
+}
+
+// fp8 tensor-core form: M_Pi^T in e4m3 for the tcgen05 B operand, uploaded on
+// first use.  Block b holds rules 32b .. 32b + 31 (zero past R) for every
+// column (zero past m, np = m rounded up to 16); within a block, columns come
+// in chunks of up to 256, each laid out as 8-column x 16-rule core matrices
+// (128 contiguous bytes: 8 columns of 16 rules), the two 16-rule halves 128
+// bytes apart and the 8-column groups 256 bytes apart.  Per-candidate hash
+// and repeat buffers for q candidates.
+int tc5_prepare(snp_system* h, uint64_t q) {
+  if (!h->d_MB.p) {
+    const int m = h->m, R = h->R;
+    const int np = (m + 15) / 16 * 16, nblocks = (R + 31) / 32;
+    std::vector<uint8_t> mb((size_t)nblocks * np * 32, 0);
+    for (int b = 0; b < nblocks; ++b)
+      for (int j = 0; j < m; ++j) {
+        const int c0 = j / 256 * 256, cc = j - c0;
+        for (int k = 0; k < 32; ++k) {
+          const int r = b * 32 + k;
+          if (r >= R) break;
+          const size_t o = ((size_t)b * np + c0) * 32 + (size_t)((cc >> 3) * 256 + (k >> 4) * 128 + (cc & 7) * 16 +
+                                                                 (k & 15));
+          mb[o] = e4m3_of_int(h->M[(size_t)r * m + j]);
+        }
+      }
+    TRY(h->d_MB.reserve(mb.size()));
+    CK(cudaMemcpy(h->d_MB.p, mb.data(), mb.size(), cudaMemcpyHostToDevice));
+    h->t5_np = np;
+    h->t5_nblocks = nblocks;
+  }
+  if (h->tc_cap < q) {
+    TRY(h->d_hash.reserve(sizeof(unsigned long long) * q));
+    TRY(h->d_red.reserve(q));
+    h->tc_cap = q;
+  }
+  return SNP_OK;
+}
+
 // Clears the table and inserts the configurations found so far (2 launches);
 // row k lives in store row perm[k].
 int rebuild_table(snp_system* h, uint64_t nbuckets, cudaStream_t st) {
@@ -465,10 +512,12 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
       return fail(SNP_E_INVALID, "checkpoint already holds depth %d > %d", rs->nstats - 1, o->depth);
     if (o->record_parents) return fail(SNP_E_INVALID, "parent records cannot be resumed");
   }
-  if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_I8)
+  if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_I8 && o->transition != SNP_T_TC_F8)
     return fail(SNP_E_INVALID, "unknown transition %d", o->transition);
   if (o->transition == SNP_T_TC_I8 && h->max_abs_m > 127)
     return fail(SNP_E_RANGE, "int8 transition refused: |M_Pi| reaches %d > 127", h->max_abs_m);
+  if (o->transition == SNP_T_TC_F8 && h->max_abs_m > 16)
+    return fail(SNP_E_RANGE, "fp8 transition refused: |M_Pi| reaches %d > 16", h->max_abs_m);
   CK(cudaSetDevice(h->device));
   cudaStream_t st = static_cast<cudaStream_t>(o->stream);
   h->explored = false;
@@ -483,6 +532,8 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
   const int64_t budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
   const bool tc = o->transition == SNP_T_TC_I8;
+  // fp8 form: every candidate's row is written to its own store row
+  const bool tc5 = o->transition == SNP_T_TC_F8;
 
   // Chunk size bound: 2^20 spiking vectors, or more while the rows a pass may
   // claim stay within ~512 MiB (passes of wide rows need 2^20 to keep every
@@ -500,6 +551,10 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   if (tc) {
     qmax = std::min<uint64_t>(qmax, 1ull << 16);
     TRY(tc_prepare(h, qmax, st));
+  }
+  if (tc5) {
+    qmax = std::min<uint64_t>(qmax, 1ull << 20);
+    TRY(tc5_prepare(h, qmax));
   }
   // Pool: exact when capped, growing otherwise.
   int64_t rows_plan = 1 << 12;
@@ -524,8 +579,11 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     h->perm_rows = rows_plan;
   }
   {
-    // claims past the cap come from the pass that reaches it: one pass per depth
-    const long double extra = (long double)qmax * (cap > 0 ? (long double)std::max(o->depth, 1) : 1.0L);
+    // claims past the cap come from the pass that reaches it: one pass per
+    // depth (the fp8 form takes a row per candidate: the pass that reaches
+    // the cap and the one in flight behind it)
+    const long double extra =
+        (long double)qmax * (cap > 0 ? (long double)std::max(o->depth, 1) * (tc5 ? 2.0L : 1.0L) : 1.0L);
     const int64_t store_plan = (int64_t)std::min<long double>(2147483632.0L, (long double)rows_plan + extra);
     if (h->pool_rows < store_plan) {
       TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * store_plan));
@@ -626,7 +684,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     psi_saturated_before = total == ~0ull;
     // Parent records serve the batches that cross parents; with few
     // candidates per parent they are worth a second pass over the frontier.
-    const bool with_records = !tc && P > 0 && total <= 256ull * (uint64_t)P;
+    const bool with_records = !tc && !tc5 && P > 0 && total <= 256ull * (uint64_t)P;
     if (with_records) {
       launch_psi(h->dev(), parents, pperm, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(),
                  h->d_st.as<ChunkState>(), st, nsm);
@@ -674,15 +732,17 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
         CK(cudaEventElapsedTime(&kms, h->evk[f.slot][0], h->evk[f.slot][1]));
         sd.expand_ms += kms;
       }
-      {
-        // algorithmic bytes of the expand kernel (include/snp.h, snp_depth_info)
-        const int64_t row = 4ll * m;
-        const int64_t dups = (int64_t)f.Q - (int64_t)cs.n_alloc;
-        const int64_t nparents = (int64_t)(cs.p_last - cs.p_first + 1);
-        sd.expand_bytes += (int64_t)f.Q * 8 + dups * row + (int64_t)cs.n_alloc * (row + 8) + nparents * row;
-      }
       const uint64_t acc = std::min<uint64_t>(cs.n_alloc, remaining);
-      h->n_store += (int64_t)cs.n_alloc;  // every claim took a store row
+      {
+        // algorithmic bytes of the expand kernel (include/snp.h, snp_depth_info),
+        // over the candidates examined (a pass that reaches the cap examines
+        // its candidates up to the last one accepted)
+        const int64_t row = 4ll * m;
+        const int64_t qx = cs.capped ? (int64_t)cs.last_lid + 1 : (int64_t)f.Q;
+        const int64_t nparents = (int64_t)(cs.p_last - cs.p_first + 1);
+        sd.expand_bytes += qx * 8 + (qx - (int64_t)acc) * row + (int64_t)acc * (row + 8) + nparents * row;
+      }
+      h->n_store += tc5 ? (int64_t)f.Q : (int64_t)cs.n_alloc;  // every claim (fp8 form: candidate) took a store row
       tombs += (int64_t)(cs.n_alloc - acc);
       nnew += (int64_t)acc;
       h->n_rows += (int64_t)acc;
@@ -775,7 +835,31 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
           a.ctr = h->d_ctr.as<unsigned long long>();
           a.st = h->d_st.as<ChunkState>();
           if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][0], st));
-          if (tc) {
+          if (tc5) {
+            Tc5Args t;
+            t.s = a.sys;
+            t.parents = parents;
+            t.pperm = pperm;
+            t.off = a.off;
+            t.P = P;
+            t.g0 = g0;
+            t.Q = (uint32_t)Q;
+            t.MB = h->d_MB.as<uint8_t>();
+            t.np = h->t5_np;
+            t.nblocks = h->t5_nblocks;
+            t.slots = tc5_slots(m, h->t5_nblocks);
+            t.delta = m > kWideM ? 1 : 0;
+            a.inplace = 1;
+            a.inplace_base = (uint64_t)h->n_store + pend_q;
+            t.out = h->d_pool.as<int32_t>() + (size_t)a.inplace_base * m;
+            t.hash = h->d_hash.as<unsigned long long>();
+            t.red = h->d_red.as<uint8_t>();
+            t.ctr = a.ctr;
+            t.st = a.st;
+            launch_tc5(t, st, nsm);
+            launch_resolve_rows(a, t.out, t.hash, t.red, st, nsm);
+            sd.launches += 2;
+          } else if (tc) {
             launch_tc_digits(a.sys, parents, pperm, a.off, P, g0, (uint32_t)Q, h->d_loc.as<uint8_t>(), h->mp,
                              h->d_pidx.as<uint32_t>(), h->d_red.as<uint8_t>(), st, nsm);
             CK(cudaMemsetAsync(h->d_hash.p, 0, sizeof(unsigned long long) * Q, st));

@@ -398,6 +398,21 @@ __device__ __forceinline__ void finish_owner(const ClaimArgs& a, const int32_t* 
   st_release(owned, ((unsigned long long)fp32_of(key) << 32) | (kPending | lid));
 }
 
+// The owner's work when its row is already in the store (row sidx, written
+// there by the fp8 tensor-core form): the claim records, then the publish.
+__device__ __forceinline__ void finish_owner_inplace(const ClaimArgs& a, uint64_t key, uint32_t lid,
+                                                     unsigned long long* owned, uint64_t sidx) {
+  if (sidx >= a.store_cap) {
+    atomicOr(&a.st->error, kErrStaging);
+    return;
+  }
+  a.sidx_of[lid] = (uint32_t)sidx;
+  a.gmin[lid] = lid;
+  a.slot_of[lid] = (uint32_t)(owned - a.table.slots);
+  atomicOr(a.ownbits + (lid >> 5), 1u << (lid & 31));
+  st_release(owned, ((unsigned long long)fp32_of(key) << 32) | (kPending | lid));
+}
+
 // Step (d) for one row per lane (lanes with todo set): passes until every
 // row is resolved; a lane never waits inside a pass, so owners in this warp
 // publish before anyone looks again.  KIND separates the out-of-line copies
@@ -1248,8 +1263,13 @@ __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t
       if (!done) {
         unsigned long long* owned = nullptr;
         const int status = resolve_lane<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned);
-        if (status == kOwner)
-          finish_owner<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned, a.store_ctr ? atomicAdd(a.store_ctr, 1ull) : 0ull);
+        if (status == kOwner) {
+          if (a.inplace)
+            finish_owner_inplace(a, key, (uint32_t)lid, owned, a.inplace_base + lid);
+          else
+            finish_owner<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned,
+                              a.store_ctr ? atomicAdd(a.store_ctr, 1ull) : 0ull);
+        }
         done = status != kRetry;
       }
       if (__all_sync(0xffffffffu, done)) break;

@@ -158,6 +158,9 @@ struct snp_system {
   std::vector<int2> term;                   // {i, j} of each term a^i (a^j)*
   // tensor-core form: M_Pi^T as int8 [mt_rows][Rp], per-rule neuron and position
   DevBuf d_MT, d_rn, d_rk, d_loc, d_pidx, d_rows, d_hash, d_red;
+  // fp8 tensor-core form: M_Pi^T in e4m3 (tc5_pack_mt), its column and block counts
+  DevBuf d_MB;
+  int32_t t5_np = 0, t5_nblocks = 0;
   int32_t Rp = 0, mp = 0, mt_rows = 0;
   uint64_t tc_cap = 0;  // candidates the tensor-core chunk buffers hold
   std::vector<unsigned long long> colkey, rowkey;

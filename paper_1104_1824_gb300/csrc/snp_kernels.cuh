@@ -29,6 +29,10 @@ struct ClaimArgs {
   const ParentRec* prec;      // [P] parent summaries, or nullptr (decode from the rows)
   const unsigned long long* ctr;  // device counters {rows, still acceptable} or nullptr; none left: no work
   ChunkState* st;
+  // Rows already in the store (the fp8 tensor-core form writes candidate
+  // lid's row to store row inplace_base + lid): an owner publishes it there.
+  int32_t inplace = 0;
+  uint64_t inplace_base = 0;
 };
 
 struct CommitArgs {
@@ -136,6 +140,30 @@ void launch_tc_rows(DevSys s, const int32_t* parents, const uint8_t* loc, int mp
                     const int8_t* MT, int Rp, const int16_t* rn, const uint8_t* rk, int32_t* rows,
                     unsigned long long* hash, cudaStream_t st);
 size_t tc_rows_smem(int mp);
+// fp8 tensor-core form of step (c) on tcgen05 (snp_tc5.cu): candidate rows
+// C' = C + S . M_Pi written to out[lid * m], their linear hashes and repeat flags.
+struct Tc5Args {
+  DevSys s;
+  const int32_t* parents;     // the store (parents + pperm[p] * m) or frontier rows
+  const uint32_t* pperm;
+  const uint64_t* off;        // [P + 1] saturating exclusive scan of Psi
+  int64_t P;
+  uint64_t g0;
+  uint32_t Q;
+  const uint8_t* MB;          // M_Pi^T in e4m3, tc5_pack_mt layout
+  int np;                     // columns rounded up to 16
+  int nblocks;                // rule blocks: ceil(R / 32)
+  int slots;                  // rule blocks held in shared memory at once (tc5_slots)
+  int delta;                  // 1: delta form for tiles within one parent
+  int32_t* out;               // [Q][m]: row lid = candidate lid's configuration
+  unsigned long long* hash;   // [Q] linear hash h(C') of each candidate
+  uint8_t* red;               // [Q] 1: repeats an earlier candidate of the same parent
+  const unsigned long long* ctr;  // device counters {rows, still acceptable}: none left: no work
+  ChunkState* st;
+};
+size_t tc5_smem_bytes(int m, int nblocks, int slots);
+int tc5_slots(int m, int nblocks);
+void launch_tc5(const Tc5Args& a, cudaStream_t st, int nsm);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);
