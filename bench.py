@@ -239,6 +239,10 @@ def run_cpu_baseline(system, sample):
     return new, dt
 
 
+def transition_code(snp, name: str) -> int:
+    return {"sparse": snp.SNP_T_SPARSE_I32, "tc": snp.SNP_T_TC_I8, "f8": snp.SNP_T_TC_F8}[name]
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -263,7 +267,7 @@ def bench_ours(args):
     stream = torch.cuda.Stream(device=dev)
     tc = args.transition == "tc"
     kw = dict(cap=w["cap"], budget=w["budget"], stream=stream, chunk=w.get("chunk", 0),
-              transition=snp.SNP_T_TC_I8 if tc else snp.SNP_T_SPARSE_I32)
+              transition=transition_code(snp, args.transition))
     for _ in range(args.warmup):
         s.explore(w["depth"], **kw)
     if world > 1:
@@ -567,7 +571,7 @@ def bench_e2e(args, system, w, snp, torch, dev):
         o = snp.snp_explore_opts_init()
         o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
         o.chunk = w.get("chunk", 0)
-        o.transition = snp.SNP_T_TC_I8 if args.transition == "tc" else snp.SNP_T_SPARSE_I32
+        o.transition = transition_code(snp, args.transition)
         snp.snp_explore(h, o)
         n = snp.snp_reachable_count(h)
         if host_out is None or host_out.shape[0] < n:
@@ -631,8 +635,9 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serving: arrivals of the stream to run")
     ap.add_argument("--max-active", type=int, default=2048, help="serving: requests on the device at once")
     ap.add_argument("--calibrate", action="store_true", help="serving: submit all at once, report the capacity")
-    ap.add_argument("--transition", choices=["sparse", "tc"], default="sparse",
-                    help="step (c): sparse int32 gather, or the exact int8 tensor-core product")
+    ap.add_argument("--transition", choices=["sparse", "tc", "f8"], default="sparse",
+                    help="step (c): sparse int32 gather, the exact int8 tensor-core product (mma.sync), or the "
+                         "exact fp8 product on tcgen05")
     args = ap.parse_args()
     if args.depth > 0:
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], depth=args.depth)

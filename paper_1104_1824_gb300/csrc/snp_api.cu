@@ -122,11 +122,11 @@ uint8_t e4m3_of_int(int v) {
 
 // fp8 tensor-core form: M_Pi^T in e4m3 for the tcgen05 B operand, uploaded on
 // first use.  Block b holds rules 32b .. 32b + 31 (zero past R) for every
-// column (zero past m, np = m rounded up to 16); within a block, columns come
-// in chunks of up to 256, each laid out as 8-column x 16-rule core matrices
-// (128 contiguous bytes: 8 columns of 16 rules), the two 16-rule halves 128
-// bytes apart and the 8-column groups 256 bytes apart.  Per-candidate hash
-// and repeat buffers for q candidates.
+// column (zero past m, np = m rounded up to 16) as 8-column x 16-rule core
+// matrices (128 contiguous bytes: 8 columns of 16 rules), the two 16-rule
+// halves 128 bytes apart and the 8-column groups 256 bytes apart, so any run
+// of columns starting at a multiple of 8 is one contiguous copy.
+// Per-candidate hash and repeat buffers for q candidates.
 int tc5_prepare(snp_system* h, uint64_t q) {
   if (!h->d_MB.p) {
     const int m = h->m, R = h->R;
@@ -134,12 +134,10 @@ int tc5_prepare(snp_system* h, uint64_t q) {
     std::vector<uint8_t> mb((size_t)nblocks * np * 32, 0);
     for (int b = 0; b < nblocks; ++b)
       for (int j = 0; j < m; ++j) {
-        const int c0 = j / 256 * 256, cc = j - c0;
         for (int k = 0; k < 32; ++k) {
           const int r = b * 32 + k;
           if (r >= R) break;
-          const size_t o = ((size_t)b * np + c0) * 32 + (size_t)((cc >> 3) * 256 + (k >> 4) * 128 + (cc & 7) * 16 +
-                                                                 (k & 15));
+          const size_t o = ((size_t)b * np + (j & ~7)) * 32 + (size_t)((k >> 4) * 128 + (j & 7) * 16 + (k & 15));
           mb[o] = e4m3_of_int(h->M[(size_t)r * m + j]);
         }
       }
@@ -852,11 +850,15 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
             a.inplace = 1;
             a.inplace_base = (uint64_t)h->n_store + pend_q;
             t.out = h->d_pool.as<int32_t>() + (size_t)a.inplace_base * m;
+            t.store_row0 = a.inplace_base;
+            CUtensorMap map;
+            std::memset(&map, 0, sizeof map);
+            t.use_map = tc5_store_map(&map, h->d_pool.as<int32_t>(), m, (uint64_t)h->pool_rows) ? 1 : 0;
             t.hash = h->d_hash.as<unsigned long long>();
             t.red = h->d_red.as<uint8_t>();
             t.ctr = a.ctr;
             t.st = a.st;
-            launch_tc5(t, st, nsm);
+            launch_tc5(t, map, st, nsm);
             launch_resolve_rows(a, t.out, t.hash, t.red, st, nsm);
             sd.launches += 2;
           } else if (tc) {

@@ -2,6 +2,8 @@
 // launch code in snp_api.cu and the definitions in snp_kernels.cu).
 #pragma once
 
+#include <cuda.h>
+
 #include "snp_device.cuh"
 
 namespace snp {
@@ -155,7 +157,9 @@ struct Tc5Args {
   int nblocks;                // rule blocks: ceil(R / 32)
   int slots;                  // rule blocks held in shared memory at once (tc5_slots)
   int delta;                  // 1: delta form for tiles within one parent
-  int32_t* out;               // [Q][m]: row lid = candidate lid's configuration
+  int32_t* out;               // [Q][m]: row lid = candidate lid's configuration (store row store_row0 + lid)
+  uint64_t store_row0;        // store row of candidate 0 (the TMA store's row coordinate)
+  int use_map;                // 1: rows go out through the tensor map given at launch
   unsigned long long* hash;   // [Q] linear hash h(C') of each candidate
   uint8_t* red;               // [Q] 1: repeats an earlier candidate of the same parent
   const unsigned long long* ctr;  // device counters {rows, still acceptable}: none left: no work
@@ -163,7 +167,11 @@ struct Tc5Args {
 };
 size_t tc5_smem_bytes(int m, int nblocks, int slots);
 int tc5_slots(int m, int nblocks);
-void launch_tc5(const Tc5Args& a, cudaStream_t st, int nsm);
+// Tensor map of the store (int32 [rows][m]) for the TMA row stores: 32 x 32
+// boxes, 128-byte swizzle.  false: not available (m % 4 != 0, m < 32, or no
+// driver entry point); rows are then stored by the threads.
+bool tc5_store_map(CUtensorMap* map, int32_t* pool, int m, uint64_t rows);
+void launch_tc5(const Tc5Args& a, const CUtensorMap& map, cudaStream_t st, int nsm);
 __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, uint32_t* srow, uint32_t nwords,
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);

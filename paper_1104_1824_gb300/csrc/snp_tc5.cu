@@ -4,13 +4,14 @@
 // (TMEM) and read back with tcgen05.ld.
 //
 // Exactness.  Entries of M_Pi are integers with |M| <= 16 and the left
-// operand holds 0, +1 or -1, all exact in e4m3.  Every output is a sum of at
-// most 2 m such products, |sum| <= 2 * 16 * 1024 < 2^24, so each partial sum
-// is an integer that fp32 holds exactly, whatever order the tensor core adds
-// in; the int32 base row is added after the conversion back to int32.
+// operand holds 0, +1 or -1, all exact in e4m3.  Every product sum D is an
+// integer with |D| <= 2 * 16 * 1024 < 2^15.  The accumulator starts at
+// 1.5 * 2^23, so every partial sum stays in [2^23, 2^24), where fp32 holds
+// every integer: the result's bits are 0x4B400000 + D exactly, and the row is
+// C' = base + D in int32, one integer add per entry.
 //
 // Work unit: a tile of 128 consecutive candidates (the MMA's M, one TMEM lane
-// and one thread per candidate).  Two forms of the left operand:
+// and one epilogue thread per candidate).  Two forms of the left operand:
 //  * delta (rows of more than 128 neurons, tile within one parent): a CTA
 //    keeps one reference candidate t_ref of the parent, its child row
 //    C_ref = C + S_ref . M_Pi in shared memory, and the parent's neurons with
@@ -23,19 +24,24 @@
 //  * full (rows of at most 128 neurons, or a tile that crosses parents):
 //    C'_t = C_p + S_t . M_Pi with the 0/1 spiking vector S_t (Algorithm 2,
 //    II-3) of every firing neuron.
-// Each tile's active rule blocks are collected, the left operand is written
-// in shared memory in the canonical no-swizzle K-major layout (8 x 16-byte
-// core matrices), the matching blocks of M_Pi^T (prepared once per system in
-// the same layout, column chunks of up to 256) arrive by cp.async.bulk, one
-// thread issues the MMAs and commits to an mbarrier, and every thread turns
-// its TMEM lane into C' = base + D, written to the candidate's store row (the
-// rows stay where they are written: the resolve step publishes them in place).
-// The linear hash h(C') = h(base) + sum of +-H[r] and whether the candidate
-// repeats an earlier one through a rule with an identical row of M_Pi come
-// from the digits, for the resolve step.
-//
-// Every wait on an mbarrier is bounded; a wait that runs out records
-// SNP_E_TIMEOUT in the chunk's error word, and the CTA still frees its TMEM.
+// A CTA per SM runs a contiguous run of tiles with two roles:
+//  * four epilogue warps decode the tile's candidates (hash
+//    h(C') = h(base) + sum of +-H[r], repeats through rules with identical
+//    rows of M_Pi, active rule blocks), write the left operand in the
+//    canonical no-swizzle K-major layout (8 x 16-byte core matrices), and per
+//    128-column chunk turn their TMEM lane into C' = base + D, stored to the
+//    candidate's store row by TMA (128-byte swizzled staging, 32 x 32 boxes);
+//  * one control thread streams the M_Pi^T blocks of each chunk into a ring
+//    of shared-memory stages by cp.async.bulk, issues the MMAs into one of
+//    two TMEM accumulators (128 columns each) while the epilogue drains the
+//    other, and commits to the mbarriers the epilogue waits on.
+// Two CTAs share an SM, so one's decode overlaps the other's stores.
+// The rows stay where they are written: the resolve step publishes them in
+// place.  Every mbarrier wait is bounded; a wait that runs out records
+// SNP_E_TIMEOUT in the chunk's error word, stops both roles, lets copies and
+// products in flight land, and the CTA still frees its TMEM.
+#include <cudaTypedefs.h>
+
 #include "snp_kernels.cuh"
 
 namespace snp {
@@ -43,7 +49,7 @@ namespace snp {
 namespace {
 
 constexpr int kT5M = 128;       // candidates per tile (MMA M = TMEM lanes)
-constexpr int kT5NC = 256;      // columns per MMA (TMEM columns of a CTA)
+constexpr int kT5NC = 128;      // columns per MMA (one of the two TMEM accumulators of a CTA)
 constexpr int kT5K = 32;        // rules per block (K of one kind::f8f6f4 MMA)
 constexpr int kT5ABytes = kT5M * kT5K;  // one block of the left operand: 4 KB
 constexpr int kT5MaxSlots = 8;
@@ -133,45 +139,105 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, uint32_t (&r)[32]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// tcgen05.st of 32 equal words into 32 consecutive columns of the warp's lanes.
+__device__ __forceinline__ void tmem_fill32(uint32_t addr, uint32_t v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(addr),
+      "r"(v)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Byte offset of (row, k) in one 128 x 32 block of the left operand.
 __device__ __forceinline__ uint32_t a_off(int row, int k) {
   return (uint32_t)((row >> 3) * 256 + (k >> 4) * 128 + (row & 7) * 16 + (k & 15));
 }
 
+// Barrier of the four epilogue warps only (the control warp does not take part).
+__device__ __forceinline__ void ew_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ bool ew_sync_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, 1, 128, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Bounded wait that also gives up once the CTA has been told to stop.
+__device__ __forceinline__ bool bar_wait_or_stop(uint32_t bar, uint32_t parity, const volatile int* stop) {
+  for (uint32_t i = 0; i < kT5SpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((i & 63) == 63 && *stop) return false;
+    __nanosleep(20);
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+constexpr int kT5Stages = 8;     // operand-B ring: one (rule block, column chunk) unit per stage
+constexpr int kT5Stg = 2;        // TMA store staging buffers per epilogue warp (32 rows x 128 bytes each)
+constexpr int kT5Ent = 64;       // multi-choice neurons a digit walk can reach (indices below 2^64)
+constexpr int kT5Threads = 160;  // four epilogue warps (TMEM lanes 0-127) and one control warp
+constexpr uint32_t kT5Bias = 0x4B400000u;  // bits of 1.5 * 2^23: bits(1.5 * 2^23 + v) = kT5Bias + v for |v| < 2^22
+
 struct Tc5Smem {
-  uint8_t* A;          // [slots][4096]
-  uint8_t* B;          // [slots][ncmax * 32]
-  int32_t* ref;        // [np] reference child row (delta form)
+  uint8_t* A;          // [slots][4096] left operand, one block per slot
+  uint8_t* B;          // [kT5Stages][ncmax * 32] right operand ring
+  uint8_t* stg;        // [4 warps][kT5Stg][4096] store staging (128-byte swizzle)
+  int32_t* adj;        // [np] C_ref - kT5Bias (delta form)
   uint32_t* masks;     // [m] applicable rules of the cached parent
   uint16_t* list;      // [m] its neurons with >= 2 applicable rules, least significant first
   uint8_t* refd;       // [m] digits of t_ref over list
+  uint4* ent;          // [kT5Ent] per list entry: {mask, repeated-row choices (bit d), first rule, radix}
   uint32_t* bitmap;    // [nbw] active rule blocks of the tile
   uint16_t* slot_of;   // [nblocks] position of an active block in the tile's list
   uint16_t* act;       // [nblocks] active blocks in increasing order
-  unsigned long long* bars;  // [2]: operand arrival, MMA completion
+  unsigned long long* bars;  // a_full, a_empty, acc_full[2], acc_empty[2], drain, b_full[S], b_empty[S]
   uint32_t* tmem_slot;
   long long* cp;       // cached parent (frontier index), -1: none
-  unsigned long long* scal;  // t_ref, h_ref, p_first
-  int* iscal;          // list_len, ref_len, ref_red, nact, single
+  unsigned long long* scal;  // [0] t_ref, [1] h_ref, [2] p_first
+  int* iscal;          // [0] list_len, [1] ref_len, [2] ref_red, [3] nact, [4] single, [5] stop
 };
 
 }  // namespace
-
 
 size_t tc5_smem_bytes(int m, int nblocks, int slots) {
   const int np = (m + 15) / 16 * 16, ncmax = np < kT5NC ? np : kT5NC;
   const int nbw = (nblocks + 31) / 32;
   size_t b = 0;
   b += (size_t)slots * kT5ABytes;
-  b += (size_t)slots * ncmax * kT5K;
+  b += (size_t)kT5Stages * ncmax * kT5K;
+  b += (size_t)4 * kT5Stg * 4096;
   b += (size_t)np * 4;
   b += (size_t)((m + 3) / 4 * 4) * 4;
   b += (size_t)((m + 7) / 8 * 8) * 2;
   b += (size_t)((m + 15) / 16 * 16);
+  b += (size_t)kT5Ent * 16;
   b += (size_t)nbw * 4;
   b += (size_t)((nblocks + 7) / 8 * 8) * 2 * 2;
-  b += 256;  // barriers, TMEM address, cached parent, scalars, alignment
-  return (b + 1023) / 1024 * 1024 + 1024;  // + alignment of the base to 1024
+  b += (size_t)(7 + 2 * kT5Stages) * 8 + 256;  // barriers, TMEM address, cached parent, scalars, alignment
+  return (b + 1023) / 1024 * 1024 + 1024;      // + alignment of the base to 1024
 }
 
 namespace {
@@ -180,11 +246,13 @@ __device__ __forceinline__ Tc5Smem carve(unsigned char* base, int m, int np, int
   const int ncmax = np < kT5NC ? np : kT5NC;
   unsigned char* p = base;
   Tc5Smem w;
+  w.stg = p;  // 1024-aligned (128-byte swizzle)
+  p += (size_t)4 * kT5Stg * 4096;
   w.A = p;
   p += (size_t)slots * kT5ABytes;
   w.B = p;
-  p += (size_t)slots * ncmax * kT5K;
-  w.ref = reinterpret_cast<int32_t*>(p);
+  p += (size_t)kT5Stages * ncmax * kT5K;
+  w.adj = reinterpret_cast<int32_t*>(p);
   p += (size_t)np * 4;
   w.masks = reinterpret_cast<uint32_t*>(p);
   p += (size_t)((m + 3) / 4 * 4) * 4;
@@ -192,6 +260,8 @@ __device__ __forceinline__ Tc5Smem carve(unsigned char* base, int m, int np, int
   p += (size_t)((m + 7) / 8 * 8) * 2;
   w.refd = p;
   p += (size_t)((m + 15) / 16 * 16);
+  w.ent = reinterpret_cast<uint4*>(p);
+  p += (size_t)kT5Ent * 16;
   w.bitmap = reinterpret_cast<uint32_t*>(p);
   p += (size_t)((nblocks + 31) / 32) * 4;
   p = reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
@@ -201,15 +271,35 @@ __device__ __forceinline__ Tc5Smem carve(unsigned char* base, int m, int np, int
   p += (size_t)((nblocks + 7) / 8 * 8) * 2;
   p = reinterpret_cast<unsigned char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
   w.bars = reinterpret_cast<unsigned long long*>(p);
-  p += 16;
+  p += (size_t)(7 + 2 * kT5Stages) * 8;
   w.tmem_slot = reinterpret_cast<uint32_t*>(p);
-  p += 16;
+  p += 8;
   w.cp = reinterpret_cast<long long*>(p);
   p += 8;
   w.scal = reinterpret_cast<unsigned long long*>(p);
   p += 32;
   w.iscal = reinterpret_cast<int*>(p);
   return w;
+}
+
+// Barrier addresses.
+struct Tc5Bars {
+  uint32_t a_full, a_empty, acc_full[2], acc_empty[2], drain, b_full, b_empty;  // b_*: stage 0, 8 bytes apart
+};
+
+__device__ __forceinline__ Tc5Bars bars_of(const Tc5Smem& w) {
+  Tc5Bars b;
+  const uint32_t p = saddr(w.bars);
+  b.a_full = p;
+  b.a_empty = p + 8;
+  b.acc_full[0] = p + 16;
+  b.acc_full[1] = p + 24;
+  b.acc_empty[0] = p + 32;
+  b.acc_empty[1] = p + 40;
+  b.drain = p + 48;
+  b.b_full = p + 56;
+  b.b_empty = p + 56 + 8 * kT5Stages;
+  return b;
 }
 
 // Frontier row of frontier index p.
@@ -245,23 +335,23 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t& q, uint32_t radix) {
   return d;
 }
 
-// Walks the nonzero entries of the candidate's left-operand row: f(rule, sign).
-// Delta form: the neurons whose digit differs from t_ref's.  Full form: the
-// chosen rule of every firing neuron of parent row prow (whose applicability
-// is evaluated on the way).  Returns false if t is not a valid index.
+// Walks the nonzero entries of the candidate's left-operand row.  Delta form:
+// f(rule of t, rule of t_ref, change in the count of repeated-row choices) for
+// each neuron whose digit differs from t_ref's.  Full form: f(chosen rule or -1, mask, spikes, neuron) for every
+// neuron of parent row prow (applicability evaluated on the way).  Returns
+// false if t is not a valid index.
 template <typename F>
 __device__ __forceinline__ bool t5_walk_delta(const DevSys& s, const Tc5Smem& w, int list_len, int ref_len, uint64_t t,
                                               F&& f) {
   uint64_t q = t;
-  int e = 0;
-  for (; e < list_len && (q != 0 || e < ref_len); ++e) {
-    const int n = w.list[e];
-    const uint32_t mask = w.masks[n];
-    const uint32_t d = digit_of(q, (uint32_t)__popc(mask));
+  const int lim = min(list_len, kT5Ent);
+  for (int e = 0; e < lim && (q != 0 || e < ref_len); ++e) {
+    const uint4 en = w.ent[e];  // mask, repeated-row choices, first rule, radix
+    const uint32_t d = digit_of(q, en.w);
     const uint32_t dr = e < ref_len ? w.refd[e] : 0u;
     if (d != dr) {
-      const int fr = __ldg(s.first_rule + n);
-      f(fr + nth_set_bit(mask, (int)d), fr + nth_set_bit(mask, (int)dr), mask);
+      const int fr = (int)en.z;
+      f(fr + nth_set_bit(en.x, (int)d), fr + nth_set_bit(en.x, (int)dr), (int)((en.y >> d) & 1u) - (int)((en.y >> dr) & 1u));
     }
   }
   return q == 0;
@@ -292,27 +382,28 @@ __device__ __forceinline__ void put_entry(const Tc5Smem& w, int row, int r, bool
   if (pos >= g0 && pos < g1) w.A[(size_t)(pos - g0) * kT5ABytes + a_off(row, r & 31)] = plus ? kF8PlusOne : kF8MinusOne;
 }
 
-// Builds the cached parent's state for the delta form: masks, the list of
-// multi-choice neurons (least significant first), the digits of t_ref, the
-// reference child row C_ref = C + S_ref . M_Pi and its hash and count of
-// repeated-row choices.
+// Builds the cached parent's state for the delta form (epilogue warps only):
+// masks, the list of multi-choice neurons (least significant first), the
+// digits of t_ref, the reference child row C_ref = C + S_ref . M_Pi (kept as
+// C_ref - kT5Bias) and its hash and count of repeated-row choices.
 __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, uint64_t t_ref) {
   const DevSys& s = a.s;
   const int m = s.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t* prow = t5_parent_row(a, p);
-  __syncthreads();
-  for (int n = tid; n < m; n += blockDim.x) {
+  int32_t* ref = w.adj;  // C_ref while it is built, then C_ref - kT5Bias
+  ew_sync();
+  for (int n = tid; n < m; n += kT5M) {
     const int32_t x = __ldcg(prow + n);
     w.masks[n] = (uint32_t)appl(s, n, x);
-    w.ref[n] = x;
+    ref[n] = x;
   }
   const int np = a.np;
-  for (int n = m + tid; n < np; n += blockDim.x) w.ref[n] = 0;
+  for (int n = m + tid; n < np; n += kT5M) ref[n] = 0;
   if (tid == 0) {
     w.scal[1] = 0ull;  // h_ref
     w.iscal[2] = 0;    // ref_red
   }
-  __syncthreads();
+  ew_sync();
   if (warp == 0) {  // multi-choice neurons, last neuron first
     int cnt = 0;
     for (int base = m - 1; base >= 0; base -= 32) {
@@ -331,23 +422,31 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
       w.iscal[0] = cnt;
       w.iscal[1] = e;
     }
+    for (int e = lane; e < min(cnt, kT5Ent); e += 32) {  // the walk's per-entry constants
+      const int n = w.list[e];
+      const uint32_t mask = w.masks[n];
+      const int fr = __ldg(s.first_rule + n);
+      uint32_t redbits = 0;
+      for (int d = 0; d < __popc(mask); ++d) redbits |= (redundant_choice(s, mask, fr + nth_set_bit(mask, d)) ? 1u : 0u) << d;
+      w.ent[e] = make_uint4(mask, redbits, (uint32_t)fr, (uint32_t)__popc(mask));
+    }
   }
-  __syncthreads();
+  ew_sync();
   const int ref_len = w.iscal[1];
   // C_ref: every firing neuron's first applicable rule, then the swaps of the
   // neurons whose reference digit is not 0
   int red = 0;
-  for (int n = tid; n < m; n += blockDim.x) {
+  for (int n = tid; n < m; n += kT5M) {
     const uint32_t mask = w.masks[n];
     if (!mask) continue;
     const int r = __ldg(s.first_rule + n) + __ffs(mask) - 1;
     const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
     for (int e = e0; e < e1; ++e) {
       const int2 cv = __ldg(s.csr + e);
-      atomicAdd(w.ref + cv.x, cv.y);
+      atomicAdd(ref + cv.x, cv.y);
     }
   }
-  for (int e = tid; e < ref_len; e += blockDim.x) {
+  for (int e = tid; e < ref_len; e += kT5M) {
     const uint32_t d = w.refd[e];
     if (d == 0) continue;
     const int n = w.list[e];
@@ -356,17 +455,17 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
     const int rn = fr + nth_set_bit(mask, (int)d), ro = fr + __ffs(mask) - 1;
     for (int k = __ldg(&s.rule[rn].w); k < __ldg(&s.rule[rn + 1].w); ++k) {
       const int2 cv = __ldg(s.csr + k);
-      atomicAdd(w.ref + cv.x, cv.y);
+      atomicAdd(ref + cv.x, cv.y);
     }
     for (int k = __ldg(&s.rule[ro].w); k < __ldg(&s.rule[ro + 1].w); ++k) {
       const int2 cv = __ldg(s.csr + k);
-      atomicAdd(w.ref + cv.x, -cv.y);
+      atomicAdd(ref + cv.x, -cv.y);
     }
     red += redundant_choice(s, mask, rn) ? 1 : 0;
   }
-  __syncthreads();
+  ew_sync();
   uint64_t h = 0;
-  for (int n = tid; n < m; n += blockDim.x) h += col_hash(s, n, w.ref[n]);
+  for (int n = tid; n < m; n += kT5M) h += col_hash(s, n, ref[n]);
   h = warp_sum_u64(h);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) red += __shfl_xor_sync(0xffffffffu, red, o);
@@ -374,52 +473,135 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
     atomicAdd(w.scal + 1, (unsigned long long)h);
     atomicAdd(w.iscal + 2, red);
   }
+  ew_sync();
+  for (int n = tid; n < np; n += kT5M) ref[n] = (int32_t)((uint32_t)ref[n] - kT5Bias);
   if (tid == 0) {
     *w.cp = p;
     w.scal[0] = t_ref;
   }
-  __syncthreads();
+  ew_sync();
 }
 
-__global__ void __launch_bounds__(kT5M) k_tc5_expand(Tc5Args a) {
-  if (a.ctr && __ldcg(a.ctr + 1) == 0) return;  // the depth is full: nothing to do
-  extern __shared__ unsigned char t5_raw[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)t5_raw + 1023) & ~(uintptr_t)1023);
+// Tile schedule of a CTA: a contiguous run of tiles.
+__device__ __forceinline__ void tile_range(const Tc5Args& a, uint64_t& t0, uint64_t& t1) {
+  const uint64_t ntiles = ((uint64_t)a.Q + kT5M - 1) / kT5M;
+  const uint64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  t0 = min(ntiles, (uint64_t)blockIdx.x * per);
+  t1 = min(ntiles, t0 + per);
+}
+
+// The control warp's lane 0: for every tile and column chunk, the operand-B
+// blocks by cp.async.bulk into the ring and the MMAs into the free TMEM
+// buffer (which the epilogue warps filled with the bias), then the commits.
+__device__ void t5_control(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b, uint32_t tmem) {
+  const int np = a.np, slots = a.slots;
+  const int ncmax = np < kT5NC ? np : kT5NC;
+  const int nchunks = (np + kT5NC - 1) / kT5NC;
+  volatile int* stop = w.iscal + 5;
+  uint64_t tile0, tile1;
+  tile_range(a, tile0, tile1);
+  uint32_t ph_afull = 0, ph_accempty[2] = {1u, 1u}, ph_bempty[kT5Stages], ph_bfull[kT5Stages];
+  for (int i = 0; i < kT5Stages; ++i) {
+    ph_bempty[i] = 1u;
+    ph_bfull[i] = 0u;
+  }
+  uint32_t pending = 0;  // stages with a copy in flight
+  int stage = 0, buf = 0;
+  bool ok = true;
+  for (uint64_t tile = tile0; tile < tile1 && ok; ++tile) {
+    // the tile's blocks are known once its first left operand is ready
+    ok = bar_wait_or_stop(b.a_full, ph_afull, stop);
+    ph_afull ^= 1u;
+    if (!ok) break;
+    const int nact = w.iscal[3];
+    const int ngroups = (nact + slots - 1) / slots;
+    for (int nc = 0; nc < nchunks && ok; ++nc) {
+      const int c0 = nc * kT5NC, nc_cols = min(kT5NC, np - c0);
+      const uint32_t id = idesc_f8(kT5M, nc_cols), bytes = (uint32_t)nc_cols * kT5K;
+      ok = bar_wait_or_stop(b.acc_empty[buf], ph_accempty[buf], stop);
+      ph_accempty[buf] ^= 1u;
+      if (!ok) break;
+      fence_after_sync();
+      const uint32_t d = tmem + (uint32_t)(buf * kT5NC);
+      for (int gi = 0; gi < ngroups && ok; ++gi) {
+        const int ga = gi * slots, gn = min(nact, ga + slots) - ga;
+        if (ngroups > 1 && (nc > 0 || gi > 0)) {  // this group's left operand
+          ok = bar_wait_or_stop(b.a_full, ph_afull, stop);
+          ph_afull ^= 1u;
+          if (!ok) break;
+        }
+        // operand B (block act[ga + k], this column chunk) runs up to a ring
+        // ahead of the MMAs: a stage is refilled once the MMA that read it
+        // has been issued (its commit frees the stage)
+        const int st0 = stage;
+        int issued = 0;
+        for (int k = 0; k < gn && ok; ++k) {
+          for (; issued < gn && issued < k + kT5Stages && ok; ++issued) {
+            const int sL = (st0 + issued) % kT5Stages;
+            ok = bar_wait_or_stop(b.b_empty + 8 * sL, ph_bempty[sL], stop);
+            ph_bempty[sL] ^= 1u;
+            if (!ok) break;
+            bar_expect_tx(b.b_full + 8 * sL, bytes);
+            bulk_g2s(saddr(w.B + (size_t)sL * ncmax * kT5K), a.MB + ((size_t)w.act[ga + issued] * np + c0) * kT5K,
+                     bytes, b.b_full + 8 * sL);
+            pending |= 1u << sL;
+          }
+          if (!ok) break;
+          const int sI = (st0 + k) % kT5Stages;
+          ok = bar_wait_or_stop(b.b_full + 8 * sI, ph_bfull[sI], stop);
+          ph_bfull[sI] ^= 1u;
+          if (!ok) break;
+          pending &= ~(1u << sI);
+          fence_after_sync();
+          const uint64_t ad = smem_desc(saddr(w.A + (size_t)k * kT5ABytes), 128, 256);
+          const uint64_t bd = smem_desc(saddr(w.B + (size_t)sI * ncmax * kT5K), 128, 256);
+          mma_f8(d, ad, bd, id, 1u);  // accumulates onto the bias
+          mma_commit(b.b_empty + 8 * sI);
+        }
+        stage = (st0 + gn) % kT5Stages;
+        if (ngroups > 1 && ok) mma_commit(b.a_empty);
+      }
+      if (!ok) break;
+      mma_commit(b.acc_full[buf]);
+      buf ^= 1;
+    }
+    if (ngroups <= 1 && ok) mma_commit(b.a_empty);
+  }
+  if (!ok) {
+    atomicOr(&a.st->error, kErrTimeout);
+    *stop = 1;
+    // copies still in flight land before the CTA leaves
+    for (int i = 0; i < kT5Stages; ++i)
+      if (pending & (1u << i)) (void)bar_wait(b.b_full + 8 * i, ph_bfull[i]);
+  }
+  // every MMA issued completes before the TMEM is released
+  mma_commit(b.drain);
+  (void)bar_wait(b.drain, 0);
+}
+
+// The epilogue warps: per tile the digits (hash, repeats, active blocks), the
+// left operand, then per column chunk C' = base + D from TMEM to the store.
+__device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b, uint32_t tmem,
+                            const CUtensorMap* map) {
   const DevSys& s = a.s;
   const int m = s.m, np = a.np, nblocks = a.nblocks, slots = a.slots;
   const int nbw = (nblocks + 31) / 32;
-  const int ncmax = np < kT5NC ? np : kT5NC;
   const int nchunks = (np + kT5NC - 1) / kT5NC;
-  Tc5Smem w = carve(base, m, np, nblocks, slots);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t bar_b = saddr(w.bars), bar_m = saddr(w.bars + 1);
-  if (tid == 0) {
-    bar_init(bar_b, 1);
-    bar_init(bar_m, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    *w.cp = -1;
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(w.tmem_slot)),
-                 "r"((uint32_t)kT5NC));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
-  const uint32_t tmem = *w.tmem_slot;
-  uint32_t ph_b = 0, ph_m = 0;  // parities of the next phase of each barrier
-  bool failed = false;
-
+  volatile int* stop = w.iscal + 5;
   const uint64_t ntiles = ((uint64_t)a.Q + kT5M - 1) / kT5M;
-  const uint64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
-  const uint64_t tile0 = (uint64_t)blockIdx.x * per, tile1 = min(ntiles, tile0 + per);
-  for (uint64_t tile = tile0; tile < tile1 && !failed; ++tile) {
+  uint64_t tile0, tile1;
+  tile_range(a, tile0, tile1);
+  uint32_t ph_aempty = 1u, ph_accfull[2] = {0u, 0u};
+  int buf = 0, stg_i = 0;
+  uint8_t* my_stg = w.stg + (size_t)warp * kT5Stg * 4096;
+  const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+  bool ok = true;
+  for (uint64_t tile = tile0; tile < tile1 && ok; ++tile) {
     const uint64_t lid0 = tile * kT5M;
     const uint32_t nrows = (uint32_t)min((uint64_t)kT5M, (uint64_t)a.Q - lid0);
     const uint64_t g_first = a.g0 + lid0, g_last = g_first + nrows - 1;
-    // parent of the tile's first candidate, and whether the tile stays in it
-    if (warp == 0) {
+    if (warp == 0) {  // parent of the tile's first candidate, and whether the tile stays in it
       const long long cp = *w.cp;
       int64_t p;
       if (cp >= 0 && __ldcg(a.off + cp) <= g_first && g_first < __ldcg(a.off + cp + 1)) p = cp;
@@ -429,8 +611,8 @@ __global__ void __launch_bounds__(kT5M) k_tc5_expand(Tc5Args a) {
         w.iscal[4] = (a.delta && g_last < __ldcg(a.off + p + 1)) ? 1 : 0;
       }
     }
-    for (int i = tid; i < nbw; i += blockDim.x) w.bitmap[i] = 0u;
-    __syncthreads();
+    for (int i = tid; i < nbw; i += kT5M) w.bitmap[i] = 0u;
+    ew_sync();
     const int64_t p_first = (int64_t)w.scal[2];
     const bool single = w.iscal[4] != 0;
     if (single && *w.cp != p_first) t5_load_parent(a, w, p_first, g_first - __ldcg(a.off + p_first));
@@ -451,19 +633,19 @@ __global__ void __launch_bounds__(kT5M) k_tc5_expand(Tc5Args a) {
     uint64_t h = 0;
     bool red = false;
     if (valid) {
-      bool ok;
+      bool good;
       if (single) {
         h = w.scal[1];
         int rc = w.iscal[2];
-        ok = t5_walk_delta(s, w, list_len, ref_len, t, [&](int rn, int ro, uint32_t mask) {
+        good = t5_walk_delta(s, w, list_len, ref_len, t, [&](int rn, int ro, int dred) {
           mark_block(w, rn);
           mark_block(w, ro);
           h += __ldg(s.rowkey + rn) - __ldg(s.rowkey + ro);
-          rc += (redundant_choice(s, mask, rn) ? 1 : 0) - (redundant_choice(s, mask, ro) ? 1 : 0);
+          rc += dred;
         });
         red = rc > 0;
       } else {
-        ok = t5_walk_full(s, prow, t, [&](int r, uint32_t mask, int32_t x, int n) {
+        good = t5_walk_full(s, prow, t, [&](int r, uint32_t mask, int32_t x, int n) {
           h += col_hash(s, n, x);
           if (r < 0) return;
           mark_block(w, r);
@@ -471,149 +653,252 @@ __global__ void __launch_bounds__(kT5M) k_tc5_expand(Tc5Args a) {
           red |= redundant_choice(s, mask, r);
         });
       }
-      if (!ok) atomicOr(&a.st->error, kErrInternal);
+      if (!good) atomicOr(&a.st->error, kErrInternal);
       a.hash[lid] = h;
       a.red[lid] = red ? 1 : 0;
     }
-    __syncthreads();
-    // active blocks in increasing order
-    if (warp == 0) {
+    // the previous tile's MMAs have read the left operand and the block list
+    ok = bar_wait_or_stop(b.a_empty, ph_aempty, stop);
+    ph_aempty ^= 1u;
+    if (ew_sync_or(!ok)) {
+      ok = false;
+      break;
+    }
+    if (warp == 0) {  // active blocks in increasing order
       int cnt = 0;
       for (int b0 = 0; b0 < nblocks; b0 += 32) {
-        const int b = b0 + lane;
-        const bool on = b < nblocks && ((w.bitmap[b >> 5] >> (b & 31)) & 1u);
+        const int bk = b0 + lane;
+        const bool on = bk < nblocks && ((w.bitmap[bk >> 5] >> (bk & 31)) & 1u);
         const uint32_t bb = __ballot_sync(0xffffffffu, on);
         if (on) {
           const int pos = cnt + __popc(bb & ((1u << lane) - 1u));
-          w.act[pos] = (uint16_t)b;
-          w.slot_of[b] = (uint16_t)pos;
+          w.act[pos] = (uint16_t)bk;
+          w.slot_of[bk] = (uint16_t)pos;
         }
         cnt += __popc(bb);
       }
       if (lane == 0) w.iscal[3] = cnt;
     }
-    __syncthreads();
+    ew_sync();
     const int nact = w.iscal[3];
     const int ngroups = (nact + slots - 1) / slots;
-    const int32_t* brow = single ? w.ref : prow;  // base row of this candidate
-    int32_t* orow = a.out + (size_t)lid * m;
-    const bool store = valid && !red;
+    // writes the left operand of group gi (blocks act[gi * slots ..]) and hands it to the control warp
+    auto build_a = [&](int gi) {
+      const int ga = gi * slots, gb = min(nact, ga + slots), gn = gb - ga;
+      uint4* A4 = reinterpret_cast<uint4*>(w.A);
+      for (int i = tid; i < gn * (kT5ABytes / 16); i += kT5M) A4[i] = make_uint4(0, 0, 0, 0);
+      ew_sync();
+      if (valid) {
+        if (single) {
+          t5_walk_delta(s, w, list_len, ref_len, t, [&](int rn, int ro, int) {
+            put_entry(w, tid, rn, true, ga, gb);
+            put_entry(w, tid, ro, false, ga, gb);
+          });
+        } else {
+          t5_walk_full(s, prow, t, [&](int r, uint32_t, int32_t, int) {
+            if (r >= 0) put_entry(w, tid, r, true, ga, gb);
+          });
+        }
+      }
+      fence_async_smem();
+      ew_sync();
+      if (tid == 0) bar_arrive(b.a_full);
+    };
+    if (ngroups <= 1) build_a(0);  // an empty tile hands over an empty operand
 
-    for (int nc = 0; nc < nchunks && !failed; ++nc) {
-      const int c0 = nc * kT5NC;
-      const int nc_cols = min(kT5NC, np - c0);
-      for (int gi = 0; gi < ngroups && !failed; ++gi) {
-        const int ga = gi * slots, gb = min(nact, ga + slots), gn = gb - ga;
-        if (nc == 0 || ngroups > 1) {  // left operand of this group of blocks
-          uint4* A4 = reinterpret_cast<uint4*>(w.A);
-          for (int i = tid; i < gn * (kT5ABytes / 16); i += blockDim.x) A4[i] = make_uint4(0, 0, 0, 0);
-          __syncthreads();
-          if (valid) {
-            if (single) {
-              t5_walk_delta(s, w, list_len, ref_len, t, [&](int rn, int ro, uint32_t) {
-                put_entry(w, tid, rn, true, ga, gb);
-                put_entry(w, tid, ro, false, ga, gb);
-              });
-            } else {
-              t5_walk_full(s, prow, t, [&](int r, uint32_t, int32_t, int) {
-                if (r >= 0) put_entry(w, tid, r, true, ga, gb);
-              });
+    const bool tma_rows = map != nullptr && lid0 + (uint64_t)warp * 32 + 32 <= (uint64_t)a.Q;
+    const bool store = valid && !red;
+    int32_t* orow = a.out + (size_t)lid * m;
+    for (int nc = 0; nc < nchunks && ok; ++nc) {
+      if (ngroups > 1) {
+        for (int gi = 0; gi < ngroups && ok; ++gi) {
+          if (nc > 0 || gi > 0) {
+            ok = bar_wait_or_stop(b.a_empty, ph_aempty, stop);
+            ph_aempty ^= 1u;
+            if (ew_sync_or(!ok)) {
+              ok = false;
+              break;
             }
           }
-          fence_async_smem();
-          __syncthreads();
+          build_a(gi);
         }
-        if (tid == 0) {  // M_Pi^T blocks of this column chunk, then the MMAs
-          const uint32_t bytes = (uint32_t)nc_cols * kT5K;
-          bar_expect_tx(bar_b, bytes * (uint32_t)gn);
-          for (int k = 0; k < gn; ++k) {
-            const uint8_t* src = a.MB + ((size_t)w.act[ga + k] * np + c0) * kT5K;
-            bulk_g2s(saddr(w.B + (size_t)k * ncmax * kT5K), src, bytes, bar_b);
-          }
-          if (!bar_wait(bar_b, ph_b)) atomicOr(&a.st->error, kErrTimeout);
-          ph_b ^= 1u;
-          fence_after_sync();
-          const uint32_t id = idesc_f8(kT5M, nc_cols);
-          for (int k = 0; k < gn; ++k) {
-            const uint64_t ad = smem_desc(saddr(w.A + (size_t)k * kT5ABytes), 128, 256);
-            const uint64_t bd = smem_desc(saddr(w.B + (size_t)k * ncmax * kT5K), 128, 256);
-            mma_f8(tmem, ad, bd, id, (gi > 0 || k > 0) ? 1u : 0u);
-          }
-          mma_commit(bar_m);
-        }
-        // every thread waits for the products (the operands are reused
-        // next); a wait that runs out stops the CTA, all threads together
-        const bool ok = bar_wait(bar_m, ph_m);
-        ph_m ^= 1u;
-        if (!ok) atomicOr(&a.st->error, kErrTimeout);
-        fence_after_sync();
-        if (__syncthreads_or(!ok)) failed = true;
+        if (!ok) break;
       }
-      if (failed) break;
-      // epilogue: C' = base + D for this chunk's columns
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+      ok = bar_wait_or_stop(b.acc_full[buf], ph_accfull[buf], stop);
+      ph_accfull[buf] ^= 1u;
+      if (ew_sync_or(!ok)) {
+        ok = false;
+        break;
+      }
+      fence_after_sync();
+      const int c0 = nc * kT5NC, nc_cols = min(kT5NC, np - c0);
+      const uint32_t acc = lane_tmem + (uint32_t)(buf * kT5NC);
       for (int c = 0; c < nc_cols; c += 32) {
         uint32_t r[32];
         const bool two = c + 32 <= nc_cols;
-        if (nact == 0) {
+        if (two) tmem_ld32(acc + (uint32_t)c, r);
+        else tmem_ld16(acc + (uint32_t)c, r);
+        tmem_wait_ld();
+        const int j0 = c0 + c;
+        const int cnt = min(two ? 32 : 16, m - j0);
+        if (cnt <= 0) continue;
+        // v = base + D = (base - bias) + bits(bias + D)
+        if (single) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) r[i] = 0u;
+          for (int i = 0; i < 32; i += 4) {
+            if (i < cnt) {
+              const int4 b4 = *reinterpret_cast<const int4*>(w.adj + j0 + i);
+              r[i] += (uint32_t)b4.x;
+              r[i + 1] += (uint32_t)b4.y;
+              r[i + 2] += (uint32_t)b4.z;
+              r[i + 3] += (uint32_t)b4.w;
+            }
+          }
         } else {
-          if (two) tmem_ld32(lane_addr + (uint32_t)c, r);
-          else tmem_ld16(lane_addr + (uint32_t)c, r);
-          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (i < cnt) r[i] += (uint32_t)__ldcg(prow + j0 + i) - kT5Bias;
         }
-        if (store) {
-          const int j0 = c0 + c;
-          const int cnt = min(two ? 32 : 16, m - j0);
+        if (tma_rows && two) {  // 32 rows x 32 columns through the swizzled staging buffer
+          uint8_t* sb = my_stg + (size_t)stg_i * 4096;
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(kT5Stg - 1) : "memory");
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            *reinterpret_cast<uint4*>(sb + lane * 128 + ((q ^ (lane & 7)) * 16)) =
+                make_uint4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+          fence_async_smem();
+          __syncwarp();
+          if (lane == 0) tma_store_2d(map, j0, (int)(a.store_row0 + lid0 + (uint64_t)warp * 32), saddr(sb));
+          stg_i = (stg_i + 1) % kT5Stg;
+        } else if (store) {
           if ((m & 3) == 0) {
 #pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              if (i < cnt) {
-                const int4 b4 = *reinterpret_cast<const int4*>(brow + j0 + i);
-                int4 v;
-                v.x = b4.x + __float2int_rn(__uint_as_float(r[i]));
-                v.y = b4.y + __float2int_rn(__uint_as_float(r[i + 1]));
-                v.z = b4.z + __float2int_rn(__uint_as_float(r[i + 2]));
-                v.w = b4.w + __float2int_rn(__uint_as_float(r[i + 3]));
-                __stcg(reinterpret_cast<int4*>(orow + j0 + i), v);
-              }
-            }
+            for (int i = 0; i < 32; i += 4)
+              if (i < cnt)
+                __stcg(reinterpret_cast<int4*>(orow + j0 + i),
+                       make_int4((int)r[i], (int)r[i + 1], (int)r[i + 2], (int)r[i + 3]));
           } else {
 #pragma unroll
             for (int i = 0; i < 32; ++i)
-              if (i < cnt) __stcg(orow + j0 + i, brow[j0 + i] + __float2int_rn(__uint_as_float(r[i])));
+              if (i < cnt) __stcg(orow + j0 + i, (int)r[i]);
           }
         }
       }
+      // the buffer back to the bias for its next chunk, then free
+#pragma unroll 1
+      for (int c = 0; c < kT5NC; c += 32) tmem_fill32(acc + (uint32_t)c, kT5Bias);
+      tmem_wait_st();
       fence_before_sync();
-      __syncthreads();
-      fence_after_sync();
+      __syncwarp();
+      if (lane == 0) bar_arrive(b.acc_empty[buf]);
+      buf ^= 1;
     }
+    ew_sync();
   }
-  // the products of a failed tile may still be in flight: wait once more
-  if (failed && tid == 0) (void)bar_wait(bar_m, ph_m ^ 1u);
+  if (!ok) {
+    atomicOr(&a.st->error, kErrTimeout);
+    *stop = 1;
+  }
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kT5Threads, 2) k_tc5_expand(Tc5Args a, const __grid_constant__ CUtensorMap map) {
+  if (a.ctr && __ldcg(a.ctr + 1) == 0) return;  // the depth is full: nothing to do
+  extern __shared__ unsigned char t5_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)t5_raw + 1023) & ~(uintptr_t)1023);
+  const int m = a.s.m, np = a.np;
+  Tc5Smem w = carve(base, m, np, a.nblocks, a.slots);
+  const Tc5Bars b = bars_of(w);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    bar_init(b.a_full, 1);
+    bar_init(b.a_empty, 1);
+    for (int i = 0; i < 2; ++i) {
+      bar_init(b.acc_full[i], 1);
+      bar_init(b.acc_empty[i], 4);
+    }
+    bar_init(b.drain, 1);
+    for (int i = 0; i < kT5Stages; ++i) {
+      bar_init(b.b_full + 8 * i, 1);
+      bar_init(b.b_empty + 8 * i, 1);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *w.cp = -1;
+    w.iscal[5] = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(w.tmem_slot)),
+                 "r"((uint32_t)(2 * kT5NC)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
   fence_before_sync();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kT5NC));
+  fence_after_sync();
+  const uint32_t tmem = *w.tmem_slot;
+  if (warp < 4) {  // both accumulator buffers start at the bias
+    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c = 0; c < 2 * kT5NC; c += 32) tmem_fill32(lane_tmem + (uint32_t)c, kT5Bias);
+    tmem_wait_st();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp < 4) {
+    t5_epilogue(a, w, b, tmem, a.use_map ? &map : nullptr);
+  } else {
+    if ((tid & 31) == 0) t5_control(a, w, b, tmem);
+    __syncwarp();
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * kT5NC)));
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
 }
 
 }  // namespace
 
 int tc5_slots(int m, int nblocks) {
-  // two CTAs per SM (each holds 256 TMEM columns): shared memory per CTA <= 113 KB
+  // two CTAs per SM (256 TMEM columns each): at most 113 KB of shared memory each
   int slots = kT5MaxSlots;
   while (slots > 1 && tc5_smem_bytes(m, nblocks, slots) > (113u << 10)) --slots;
   return slots;
 }
 
-void launch_tc5(const Tc5Args& a, cudaStream_t st, int nsm) {
-  // at least 80 KB of shared memory so that no more than two CTAs (512 TMEM columns) share an SM
+bool tc5_store_map(CUtensorMap* map, int32_t* pool, int m, uint64_t rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc || (m & 3) != 0 || m < 32 || rows == 0 || rows > 0x7FFFFFFFull) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)m * 4};
+  const cuuint32_t box[2] = {32, 32}, es[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_INT32, 2, pool, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_tc5(const Tc5Args& a, const CUtensorMap& map, cudaStream_t st, int nsm) {
+  // more than a third of an SM's shared memory: two CTAs (256 TMEM columns each) per SM
   const size_t smem = std::max<size_t>(tc5_smem_bytes(a.s.m, a.nblocks, a.slots), 80u << 10);
   cudaFuncSetAttribute(k_tc5_expand, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const uint64_t ntiles = ((uint64_t)a.Q + kT5M - 1) / kT5M;
-  const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, (uint64_t)nsm * 2));
-  k_tc5_expand<<<blocks, kT5M, smem, st>>>(a);
+  const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, 2ull * nsm));
+  k_tc5_expand<<<blocks, kT5Threads, smem, st>>>(a, map);
 }
 
 }  // namespace snp
