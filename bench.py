@@ -1,16 +1,23 @@
 #!/usr/bin/env python3
 """Benchmark: new configurations per second of the breadth-first exploration.
 
-Workload (default "random64"): the seeded 64-neuron random SNP system
-(seed 1; 2-3 rules per neuron, regexes a^i(a^j)*, out-degree 4, initial spikes
-U[0,6]) explored to depth 8 with the frontier capped at 2^20 configurations
-and at most 2^24 candidates examined per depth, sparse int32 transition.
+Workload (default "dense1024"): the seeded 1024-neuron random SNP system
+(seed 3; 4 rules per neuron, R = 4096, out-degree 64, c U[1,8], i U[c,8],
+j U{0,1,2}, p U[1,8], C0 U[0,16]) explored to depth 4 with the frontier capped
+at 2^22 configurations and at most 2^26 candidates examined per depth.  The
+line's value is the plain int32 (sparse) transition; the metric's comparison,
+the exact tensor-core forms on the same GPU (fp8 on tcgen05, int8 on
+mma.sync), is timed after it and reported under "compare", each with its ratio
+to the int32 value.  --workload random64 gives the 64-neuron system (depth 8,
+cap 2^20, budget 2^24); batch4096 and serving the batch engine and the
+serving loop.
 
-One step = one complete snp_explore call (all 8 depths, steps (a)-(d) on the
+One step = one complete snp_explore call (all depths, steps (a)-(d) on the
 GPU) with the system already resident.  value = new configurations found over
 all timed steps (and all ranks) / the max over ranks of the device time of the
 timed region (CUDA events on the exploration's stream).  The working set of a
-step (2.1 GB of configurations, 128 MB table) exceeds L2, so no flush is added.
+step (68.7 GB of configurations at dense1024, 2.1 GB at random64) exceeds L2,
+so no flush is added.  Each form's handle is freed before the next form runs.
 
 e2e: the same metric through the C ABI with host buffers: every step loads the
 system from host arrays, explores, and copies every configuration back to
@@ -52,7 +59,8 @@ WORKLOADS = {
     "dense1024": dict(seed=3, depth=4, cap=1 << 22, budget=1 << 26,
                       desc="random SNP system seed 3: m=1024, 4 rules/neuron (R=4096), out-degree 64, c U[1,8], "
                            "i U[c,8], j U{0,1,2}, p U[1,8], C0 U[0,16]; BFS depth 4, frontier cap 2^22, candidate "
-                           "budget 2^26, passes of up to 2^21 spiking vectors (65536 in the tensor-core form)",
+                           "budget 2^26, passes of up to 2^21 spiking vectors (2^20 in the fp8 tensor-core form, 65536 in the "
+                           "int8 one)",
                       cpu_sample=dict(depth=1, cap=1 << 12, budget=1 << 14),
                       ref_sample=dict(depth=1, cap=1 << 11, budget=1 << 13)),
     # rate frozen at 0.8 x the measured batched capacity (125.8 requests/s, --calibrate, 2000 requests)
@@ -69,6 +77,10 @@ WORKLOADS = {
                       cpu_sample=dict(systems=2, depth=6, cap=1 << 12, budget=1 << 16),
                       ref_sample=dict(systems=1, depth=4, cap=1 << 12, budget=1 << 16)),
 }
+
+
+# timed steps by default: a timed region of at least 2 s
+DEFAULT_STEPS = {"dense1024": 80, "random64": 300, "batch4096": 5, "serving": 1}
 
 
 def rank_info():
@@ -205,10 +217,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per launch of the expand kernel from the committed ncu summary,
-    or None when the summary is missing or was taken on other kernel sources."""
-    path = os.path.join(ROOT, "profiles", f"expand_kernel_{workload}.txt")
+def profiled_traffic(workload: str, kernel: str = "expand"):
+    """DRAM bytes per candidate of a form's dominant kernel from the committed
+    ncu summary (profiles/<kernel>_kernel_<workload>.txt), or None when the
+    summary is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_kernel_{workload}.txt")
     if not os.path.exists(path):
         return None
     vals = {}
@@ -243,6 +256,88 @@ def transition_code(snp, name: str) -> int:
     return {"sparse": snp.SNP_T_SPARSE_I32, "tc": snp.SNP_T_TC_I8, "f8": snp.SNP_T_TC_F8}[name]
 
 
+TRANSITION_NAMES = {"sparse": "sparse_i32", "tc": "tc_i8", "f8": "tc_f8"}
+
+
+def time_form(args, system, w, snp, torch, dist, dev, world, local, transition: str, steps: int, warmup: int):
+    """Times `steps` explorations of the workload in one transition form on a
+    side stream (CUDA events around the whole timed region, after `warmup`
+    untimed ones); the handle, and its store, is freed afterwards."""
+    s = snp.System(system)
+    stream = torch.cuda.Stream(device=dev)
+    kw = dict(cap=w["cap"], budget=w["budget"], stream=stream, chunk=w.get("chunk", 0),
+              transition=transition_code(snp, transition))
+    for _ in range(warmup):
+        s.explore(w["depth"], **kw)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    r = dict(total_new=0, expand_bytes=0, expand_ms=0.0, launches=0, candidates=0, chunks=0)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(steps):
+            s.explore(w["depth"], kernel_timing=True, **kw)
+            st = s.depth_stats()
+            r["total_new"] += sum(d.new for d in st[1:])
+            r["expand_bytes"] += sum(d.expand_bytes for d in st)
+            r["expand_ms"] += sum(d.expand_ms for d in st)
+            r["launches"] += sum(d.launches for d in st)
+            r["candidates"] += sum(d.examined for d in st[1:])
+            r["chunks"] += sum(d.chunks for d in st)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    r["clocks"] = clocks.stop()
+    r["ms"] = ev0.elapsed_time(ev1)
+    r["per_depth"] = [{"depth": d, "new": x.new, "examined": x.examined, "chunks": x.chunks, "ms": round(x.ms, 4),
+                       "new_per_s": round(x.new / (x.ms * 1e-3)) if x.ms > 0 else None}
+                      for d, x in enumerate(st) if d > 0]
+    s.close()
+    torch.cuda.synchronize()
+    return r
+
+
+def roofline_of(args, system, snp, transition: str, r):
+    """Roofline object of the form's dominant kernel (the
+    algorithmic bytes per candidate and per configuration)."""
+    ms = r["ms"]
+    nlaunch = max(1, r["chunks"])
+    if transition == "tc":
+        # the int8 tensor-core pass: dense 2 * R * m int8 operations per candidate
+        peak = snp.snp_tc_peak_tops(20000)
+        ops = 2.0 * system.R * system.m * r["candidates"]
+        achieved = ops / (r["expand_ms"] * 1e-3) / 1e12 if r["expand_ms"] > 0 else None
+        return {
+            "kernel": "k_tc_digits + k_tc_rows (mma.sync m16n8k32 s8) + k_resolve_rows, per pass",
+            "bound": "tensor", "achieved": round(achieved, 2) if achieved else None, "peak": round(peak, 1),
+            "peak_kind": "measured mma.sync m16n8k32 s8 rate on this GPU (snp_tc_peak_tops)", "unit": "TOPS",
+            "frac": round(achieved / peak, 4) if achieved else None,
+            "algorithmic_ops_per_launch": int(ops / nlaunch),
+            "avg_launch_ms": round(r["expand_ms"] / nlaunch, 4), "traffic": None,
+            "expand_share_of_step": round(r["expand_ms"] / ms, 4) if ms > 0 else None,
+        }
+    peak, peak_kind = measured_peaks()
+    achieved = r["expand_bytes"] / (r["expand_ms"] * 1e-3) / 1e9 if r["expand_ms"] > 0 else None
+    if transition == "f8":
+        kernel = "k_tc5_expand (tcgen05 kind::f8f6f4, TMEM, TMA row stores) + k_resolve_rows, per pass"
+        traffic = profiled_traffic(args.workload, "tc5")
+    else:
+        kernel = ("k_expand_wide" if system.m > 128 else "k_expand") + " (decode, C' = C + S.M, hash, probe/compare/claim)"
+        traffic = profiled_traffic(args.workload)
+    return {
+        "kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+        "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+        "frac": round(achieved / peak, 4) if achieved else None,
+        "algorithmic_bytes_per_launch": int(r["expand_bytes"] / nlaunch),
+        "avg_launch_ms": round(r["expand_ms"] / nlaunch, 4),
+        "traffic": (int(traffic["bytes_per_candidate"] * r["candidates"] / nlaunch) if traffic else None),
+        "expand_share_of_step": round(r["expand_ms"] / ms, 4) if ms > 0 else None,
+    }
+
+
 def bench_ours(args):
     import numpy as np
     import torch
@@ -263,76 +358,29 @@ def bench_ours(args):
     system = make_system(args.workload, rank)
     if args.workload == "batch4096":
         return bench_batch(args, w, system, snp, torch, dist, dev, rank, world, local)
-    s = snp.System(system)
-    stream = torch.cuda.Stream(device=dev)
-    tc = args.transition == "tc"
-    kw = dict(cap=w["cap"], budget=w["budget"], stream=stream, chunk=w.get("chunk", 0),
-              transition=transition_code(snp, args.transition))
-    for _ in range(args.warmup):
-        s.explore(w["depth"], **kw)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    total_new = 0
-    expand_bytes = 0
-    expand_ms = 0.0
-    launches = 0
-    candidates = 0
-    with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for _ in range(args.steps):
-            s.explore(w["depth"], kernel_timing=True, **kw)
-            st = s.depth_stats()
-            total_new += sum(d.new for d in st[1:])
-            expand_bytes += sum(d.expand_bytes for d in st)
-            expand_ms += sum(d.expand_ms for d in st)
-            launches += sum(d.launches for d in st)
-            candidates += sum(d.examined for d in st[1:])
-        ev1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    per_depth = [{"depth": d, "new": x.new, "examined": x.examined, "chunks": x.chunks, "ms": round(x.ms, 4),
-                  "new_per_s": round(x.new / (x.ms * 1e-3)) if x.ms > 0 else None} for d, x in enumerate(st) if d > 0]
-    ms_max, (total_all, launches_all) = aggregate_ranks(ms, [total_new, launches], dist if world > 1 else None, dev)
+    main_form = args.transition or "sparse"
+    r = time_form(args, system, w, snp, torch, dist, dev, world, local, main_form, args.steps, args.warmup)
+    ms_max, (total_all, launches_all) = aggregate_ranks(r["ms"], [r["total_new"], r["launches"]],
+                                                        dist if world > 1 else None, dev)
     total_all, launches_all = int(total_all), int(launches_all)
     value = total_all / (ms_max * 1e-3)
+    roofline = roofline_of(args, system, snp, main_form, r)
 
-    nlaunch_expand = sum(x.chunks for x in st) * args.steps
-    if tc:
-        # the tensor-core pass: dense 2 * R * m int8 operations per candidate
-        peak = snp.snp_tc_peak_tops(20000)
-        ops = 2.0 * system.R * system.m * candidates
-        achieved = ops / (expand_ms * 1e-3) / 1e12 if expand_ms > 0 else None
-        roofline = {
-            "kernel": "k_tc_digits + k_tc_rows (mma.sync m16n8k32 s8) + k_resolve_rows, per pass",
-            "bound": "tensor", "achieved": round(achieved, 2) if achieved else None, "peak": round(peak, 1),
-            "peak_kind": "measured mma.sync m16n8k32 s8 rate on this GPU (snp_tc_peak_tops)", "unit": "TOPS",
-            "frac": round(achieved / peak, 4) if achieved else None,
-            "algorithmic_ops_per_launch": int(ops / max(1, nlaunch_expand)),
-            "avg_launch_ms": round(expand_ms / max(1, nlaunch_expand), 4), "traffic": None,
-            "expand_share_of_step": round(expand_ms / ms, 4) if ms > 0 else None,
-        }
-    else:
-        # the expand kernel: steps (b)-(d) per candidate
-        peak, peak_kind = measured_peaks()
-        achieved = expand_bytes / (expand_ms * 1e-3) / 1e9 if expand_ms > 0 else None
-        traffic = profiled_traffic(args.workload)
-        roofline = {
-            "kernel": ("k_expand_wide" if system.m > 128 else "k_expand") +
-                      " (decode, C' = C + S.M, hash, probe/compare/claim)",
-            "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
-            "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
-            "frac": round(achieved / peak, 4) if achieved else None,
-            "algorithmic_bytes_per_launch": int(expand_bytes / max(1, nlaunch_expand)),
-            "avg_launch_ms": round(expand_ms / max(1, nlaunch_expand), 4),
-            "traffic": (int(traffic["bytes_per_candidate"] * candidates / max(1, nlaunch_expand)) if traffic else None),
-            "expand_share_of_step": round(expand_ms / ms, 4) if ms > 0 else None,
-        }
+    # the metric's comparison: the tensor-core forms against the plain int32 form on the same GPU
+    compare = {}
+    if args.transition is None and args.workload == "dense1024" and not args.no_compare:
+        for form, steps, warm in (("f8", args.steps, args.warmup), ("tc", 1, 1)):
+            rf = time_form(args, system, w, snp, torch, dist, dev, world, local, form, steps, warm)
+            msf, (tot_f,) = aggregate_ranks(rf["ms"], [rf["total_new"]], dist if world > 1 else None, dev)
+            vf = tot_f / (msf * 1e-3)
+            compare[TRANSITION_NAMES[form]] = {
+                "value": round(vf, 1), "unit": UNIT, "steps": steps, "warmup": warm,
+                "ms_per_step": round(msf / steps, 4), "ratio_to_sparse_i32": round(vf / value, 4),
+                "dtype": "fp8 e4m3 operands, fp32 accumulation (exact)" if form == "f8" else "int8, int32 accumulation",
+                "new_per_step": rf["total_new"] // steps, "per_depth": rf["per_depth"],
+                "roofline": roofline_of(args, system, snp, form, rf), "clocks": rf["clocks"],
+                "gpu_launches": rf["launches"],
+            }
 
     e2e = None
     if not args.no_e2e:
@@ -346,23 +394,27 @@ def bench_ours(args):
                          f"{new} new configurations in {dt:.2f} s, single-threaded C++ oracle",
                "seconds": round(dt, 2)}
     if rank == 0:
+        nps = r["total_new"] // args.steps
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int8" if tc else "int32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"sparse": "int32", "tc": "int8", "f8": "fp8"}[main_form],
+            "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w['desc']}", "depth": w["depth"], "frontier_cap": w["cap"],
-                       "candidate_budget": w["budget"], "transition": "tc_i8" if tc else "sparse_i32",
-                       "new_per_step": total_new // args.steps,
-                       "l2": f"inputs larger than L2 ({total_new // args.steps * system.m * 4 / 1e9:.1f} GB of "
-                             "configurations written per step)",
+                       "candidate_budget": w["budget"], "transition": TRANSITION_NAMES[main_form],
+                       "new_per_step": nps,
+                       "l2": f"inputs larger than L2 ({nps * system.m * 4 / 1e9:.1f} GB of configurations written "
+                             "per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "per_depth": per_depth,
+            "per_depth": r["per_depth"],
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches_all,
-            "clocks": clk,
+            "clocks": r["clocks"],
         }
+        if compare:
+            line["compare"] = compare
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
@@ -571,7 +623,7 @@ def bench_e2e(args, system, w, snp, torch, dev):
         o = snp.snp_explore_opts_init()
         o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
         o.chunk = w.get("chunk", 0)
-        o.transition = transition_code(snp, args.transition)
+        o.transition = transition_code(snp, args.transition or "sparse")
         snp.snp_explore(h, o)
         n = snp.snp_reachable_count(h)
         if host_out is None or host_out.shape[0] < n:
@@ -622,10 +674,11 @@ def bench_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: at least 2 s of them: dense1024 80, random64 300, batch4096 5)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="random64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense1024")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--depth", type=int, default=0, help="override the workload's depth (profiling cases)")
@@ -635,10 +688,14 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="serving: arrivals of the stream to run")
     ap.add_argument("--max-active", type=int, default=2048, help="serving: requests on the device at once")
     ap.add_argument("--calibrate", action="store_true", help="serving: submit all at once, report the capacity")
-    ap.add_argument("--transition", choices=["sparse", "tc", "f8"], default="sparse",
+    ap.add_argument("--transition", choices=["sparse", "tc", "f8"], default=None,
                     help="step (c): sparse int32 gather, the exact int8 tensor-core product (mma.sync), or the "
-                         "exact fp8 product on tcgen05")
+                         "exact fp8 product on tcgen05 (default: sparse; on dense1024 the two tensor-core forms are "
+                         "also timed and reported under 'compare')")
+    ap.add_argument("--no-compare", action="store_true", help="dense1024: time the sparse form only")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 5)
     if args.depth > 0:
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], depth=args.depth)
     if args.cap > 0:

@@ -47,6 +47,7 @@ extern "C" {
 #define SNP_E_OVERFLOW 7 /* a spike count could leave the int32 range */
 #define SNP_E_STATE 8    /* call out of order (e.g. results before an exploration) */
 #define SNP_E_INTERNAL 9 /* a device-side consistency check failed */
+#define SNP_E_CANCELLED 10 /* the caller's cancel flag was set (snp_explore_opts.cancel) */
 
 /* Transition forms for step (c). */
 #define SNP_T_SPARSE_I32 0 /* gather over M_Pi's nonzeros, int32 on the CUDA cores */
@@ -133,6 +134,15 @@ typedef struct {
  *                    candidates a warp builds together; <= 0: the largest
  *                    that shared memory holds.
  *  warps             warps per CTA of the batch engine (4 or 8); <= 0: automatic.
+ *  timeout_ms        > 0: bound, in milliseconds, on a lane's wait for a hash
+ *                    slot that another lane is claiming; past it the pass
+ *                    records SNP_E_TIMEOUT (the call returns it, the handle
+ *                    stays usable).  <= 0: the default bound of 2^22 polls.
+ *  cancel            host int32 polled before every depth and pass (NULL:
+ *                    none); once it is nonzero the passes in flight finish,
+ *                    the exploration is discarded and the call returns
+ *                    SNP_E_CANCELLED.
+ *  reserved          must be 0.
  * Candidate order ("canonical order"): parents in discovery order; for each,
  * its valid spiking vectors in mixed-radix order with neuron 0's choice most
  * significant and the last neuron's least; a neuron's choices are its
@@ -149,8 +159,9 @@ typedef struct {
   int32_t kernel_timing;
   int32_t tile;
   int32_t warps;
-  int32_t reserved0;
-  int64_t reserved[2];
+  int32_t timeout_ms;
+  const volatile int32_t* cancel;
+  int64_t reserved;
 } snp_explore_opts;
 
 /* Statistics of one BFS depth (index 0 is the root level). */
@@ -174,13 +185,17 @@ typedef struct {
 
 /* Fills *opts with defaults: depth 1, sparse int32, no cap, no budget,
  * max_expand_value -1, no parent records, automatic chunk, default stream,
- * no kernel timing. */
+ * no kernel timing, the default wait bound, no cancel flag. */
 void snp_explore_opts_init(snp_explore_opts* opts);
 
 /* Validates and copies a system (Definition 1, Definition 2) and uploads its
  * rule table and M_Pi to the current device.  On success *out is a new handle.
  * Errors: SNP_E_INVALID (see snp_system_desc), SNP_E_NOMEM, SNP_E_CUDA. */
 int snp_load_system(const snp_system_desc* desc, snp_handle* out);
+
+/* Shape of a loaded system (Definition 1: m neurons, R rules) and the CUDA
+ * device it lives on; any pointer may be NULL.  Errors: SNP_E_INVALID. */
+int snp_system_info(snp_handle h, int32_t* m, int32_t* R, int32_t* device);
 
 /* Releases a handle and all its device memory.  NULL is accepted. */
 int snp_free(snp_handle h);
@@ -312,9 +327,8 @@ int snp_server_destroy(void* srv);
 
 /* snp_explore without allocating memory: the paper has no counterpart; this
  * is for callers that may not allocate device memory at the moment they need
- * an exploration (a framework's caching allocator holds the free memory,
- * contexts such as host callbacks where cudaMalloc may not be called, loops
- * that must not block on the allocator).  It runs the same search as
+ * an exploration (a framework's caching allocator holds the free memory, or a
+ * loop must not block on the allocator).  It runs the same search as
  * snp_explore and writes the same configurations in the same order, but
  * allocates neither device nor host memory: the configurations go straight
  * into the caller's device buffer out[capacity * m], which also serves as the
@@ -323,20 +337,25 @@ int snp_server_destroy(void* srv);
  * the process exits.  All calls share that array and each leaves its contents
  * behind; a call clears what must start empty, and calls whose work overlaps
  * on the GPU (other streams or threads) race on it.  The first call on a
- * device looks up the array's address; make that first call before any
- * stream capture.
+ * device (and the first after its context was recreated) looks up the
+ * array's address.  The call launches kernels on opts->stream and waits for
+ * that stream once per pass, so it may not be made from a stream callback or
+ * on a stream that is being captured.  The caller's current device is the
+ * same on return.
  *  opts           as for snp_explore; transition must be SNP_T_SPARSE_I32
  *                 and record_parents 0.  Uses opts->stream.
- *  out            device memory, capacity rows of m int32.
+ *  out            device memory on the handle's device, capacity rows of m
+ *                 int32.
  *  capacity       1 <= capacity <= 2^20 configurations (the array's limit);
  *                 larger values are refused with SNP_E_INVALID.
  *  *n             configurations written (C0 first, discovery order).
  *  depth_reached  (host, may be NULL) as for snp_explore.
  *  per_depth_new  (host, [opts->depth + 1], may be NULL) new configurations
  *                 per depth, index 0 being C0's level.
- * The handle's own exploration state is not touched.  Errors: SNP_E_INVALID,
- * SNP_E_BUFFER (capacity reached while candidates remain), SNP_E_OVERFLOW,
- * SNP_E_TIMEOUT, SNP_E_INTERNAL, SNP_E_CUDA. */
+ * The handle's exploration results are not touched (the handle's pinned
+ * staging words are reused).  Errors: SNP_E_INVALID, SNP_E_BUFFER (capacity
+ * reached while candidates remain), SNP_E_OVERFLOW, SNP_E_TIMEOUT,
+ * SNP_E_INTERNAL, SNP_E_CUDA. */
 int snp_explore_static(snp_handle h, const snp_explore_opts* opts, int32_t* out, int64_t capacity, int64_t* n,
                        int32_t* depth_reached, int64_t* per_depth_new);
 
@@ -357,6 +376,13 @@ const char* snp_last_error(void);
  * without exhausting the device; k <= 0 turns it off.  The failing call
  * returns SNP_E_NOMEM and leaves every handle usable.  Process-wide. */
 int snp_debug_fail_allocation(int64_t k);
+
+/* Testing hook (no counterpart in the paper): the next snp_explore (on any
+ * handle) leaves C0's hash-table slot in the "being claimed" state instead of
+ * publishing it, so a candidate equal to C0 waits until the wait bound runs
+ * out and the call returns SNP_E_TIMEOUT, without any fault.  One-shot,
+ * process-wide; on = 0 withdraws it. */
+int snp_debug_hold_root_slot(int32_t on);
 
 /* SNP_ABI_VERSION of the loaded library. */
 int snp_abi_version(void);

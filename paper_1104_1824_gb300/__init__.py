@@ -31,6 +31,7 @@ SNP_E_BUFFER = 6
 SNP_E_OVERFLOW = 7
 SNP_E_STATE = 8
 SNP_E_INTERNAL = 9
+SNP_E_CANCELLED = 10
 SNP_T_SPARSE_I32 = 0
 SNP_T_TC_I8 = 1
 SNP_T_TC_F8 = 2
@@ -38,12 +39,12 @@ SNP_PSI_SAT = (1 << 64) - 1
 
 ERROR_NAMES = {0: "SNP_OK", 1: "SNP_E_INVALID", 2: "SNP_E_RANGE", 3: "SNP_E_NOMEM", 4: "SNP_E_CUDA",
                5: "SNP_E_TIMEOUT", 6: "SNP_E_BUFFER", 7: "SNP_E_OVERFLOW", 8: "SNP_E_STATE",
-               9: "SNP_E_INTERNAL"}
+               9: "SNP_E_INTERNAL", 10: "SNP_E_CANCELLED"}
 
 # Every symbol include/snp.h declares.
 EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "snp_explore", "snp_reachable",
            "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
-           "snp_explore_resume", "snp_debug_fail_allocation",
+           "snp_explore_resume", "snp_debug_fail_allocation", "snp_system_info", "snp_debug_hold_root_slot",
            "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune", "snp_server_create",
            "snp_server_submit", "snp_server_poll", "snp_server_wait", "snp_server_stats", "snp_server_destroy"]
 
@@ -66,8 +67,8 @@ class snp_explore_opts(ctypes.Structure):
                 ("frontier_cap", ctypes.c_int64), ("candidate_budget", ctypes.c_int64),
                 ("max_expand_value", ctypes.c_int32), ("record_parents", ctypes.c_int32),
                 ("chunk", ctypes.c_int64), ("stream", ctypes.c_void_p), ("kernel_timing", ctypes.c_int32),
-                ("tile", ctypes.c_int32), ("warps", ctypes.c_int32), ("reserved0", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 2)]
+                ("tile", ctypes.c_int32), ("warps", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
+                ("cancel", ctypes.c_void_p), ("reserved", ctypes.c_int64)]
 
 
 class snp_depth_info(ctypes.Structure):
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH):
     lib.snp_explore_opts_init.restype = None
     lib.snp_load_system.argtypes = [ctypes.POINTER(snp_system_desc), ctypes.POINTER(vp)]
     lib.snp_free.argtypes = [vp]
+    lib.snp_debug_hold_root_slot.argtypes = [i32]
+    lib.snp_system_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.snp_step.argtypes = [vp, vp, i64, vp, ctypes.POINTER(u64)]
     lib.snp_explore.argtypes = [vp, ctypes.POINTER(snp_explore_opts), ctypes.POINTER(i32), vp]
     lib.snp_reachable.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
@@ -200,6 +203,12 @@ def snp_debug_fail_allocation(k: int) -> None:
     _check(load_library().snp_debug_fail_allocation(ctypes.c_int64(int(k))))
 
 
+def snp_debug_hold_root_slot(on: bool = True) -> None:
+    """Testing hook: the next exploration leaves C0's table slot being claimed
+    (a candidate equal to C0 then waits until the wait bound runs out)."""
+    _check(load_library().snp_debug_hold_root_slot(ctypes.c_int32(1 if on else 0)))
+
+
 def snp_explore_resume(h, rows: np.ndarray, stats, opts: snp_explore_opts,
                        truncated_flags: Optional[np.ndarray] = None) -> int:
     """rows: [n, m] int32 (host array or a torch device tensor); stats: a ctypes array of snp_depth_info."""
@@ -235,10 +244,41 @@ def snp_parents(h, parent, index, capacity: int) -> int:
     return n.value
 
 
+def snp_system_info(h) -> Tuple[int, int, int]:
+    """(m, R, device) of a loaded system."""
+    m, r, dev = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load_library().snp_system_info(h, ctypes.byref(m), ctypes.byref(r), ctypes.byref(dev)))
+    return m.value, r.value, dev.value
+
+
+def snp_system_m(h) -> int:
+    return snp_system_info(h)[0]
+
+
+def snp_system_device(h) -> int:
+    return snp_system_info(h)[2]
+
+
 def snp_explore_static(h, opts: snp_explore_opts, out, capacity: int,
                        per_depth_new: Optional[np.ndarray] = None) -> Tuple[int, int]:
     """Exploration into the caller's device buffer `out`, allocating nothing.
-    Returns (configurations written, depth reached)."""
+    Returns (configurations written, depth reached).  `out` must be a
+    contiguous int32 device tensor on the handle's device with at least
+    capacity * m entries; `per_depth_new`, if given, an int64 array of at least
+    opts.depth + 1 entries."""
+    m = snp_system_m(h)
+    if not hasattr(out, "data_ptr") or not hasattr(out, "is_cuda") or not out.is_cuda:
+        raise SnpError(SNP_E_INVALID, "out must be a device (CUDA) tensor")
+    if str(out.dtype) != "torch.int32" or not out.is_contiguous():
+        raise SnpError(SNP_E_INVALID, "out must be a contiguous int32 tensor")
+    if int(capacity) < 0 or out.numel() < int(capacity) * m:
+        raise SnpError(SNP_E_INVALID, f"out holds {out.numel()} entries, capacity * m needs {int(capacity) * m}")
+    if out.device.index != snp_system_device(h):
+        raise SnpError(SNP_E_INVALID, f"out is on device {out.device.index}, the system on {snp_system_device(h)}")
+    if per_depth_new is not None:
+        if not isinstance(per_depth_new, np.ndarray) or per_depth_new.dtype != np.int64 or \
+                not per_depth_new.flags["C_CONTIGUOUS"] or per_depth_new.shape[0] < opts.depth + 1:
+            raise SnpError(SNP_E_INVALID, "per_depth_new must be a contiguous int64 array of depth + 1 entries")
     n = ctypes.c_int64()
     dr = ctypes.c_int32()
     _check(load_library().snp_explore_static(h, ctypes.byref(opts), _ptr(out), int(capacity), ctypes.byref(n),
@@ -379,8 +419,11 @@ class System:
 
     def explore(self, depth: int, cap: int = 0, budget: int = 0, transition: int = SNP_T_SPARSE_I32,
                 max_expand: int = -1, record_parents: bool = False, chunk: int = 0, stream=None,
-                kernel_timing: bool = False) -> int:
+                kernel_timing: bool = False, timeout_ms: int = 0, cancel=None) -> int:
+        """cancel: a host int32 array of one element, polled between passes."""
         o = snp_explore_opts_init()
+        o.timeout_ms = int(timeout_ms)
+        o.cancel = _ptr(cancel) or None
         o.depth = int(depth)
         o.transition = int(transition)
         o.frontier_cap = int(cap)

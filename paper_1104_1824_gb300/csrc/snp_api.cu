@@ -17,6 +17,7 @@ namespace snp {
 
 thread_local std::string g_err;
 std::atomic<long long> g_alloc_countdown{0};
+std::atomic<int> g_hold_root_slot{0};
 
 int fail(int code, const char* fmt, ...) {
   char buf[512];
@@ -232,6 +233,11 @@ int snp_debug_fail_allocation(int64_t k) {
   return SNP_OK;
 }
 
+int snp_debug_hold_root_slot(int32_t on) {
+  g_hold_root_slot.store(on ? 1 : 0);
+  return SNP_OK;
+}
+
 int snp_abi_version(void) { return SNP_ABI_VERSION; }
 
 int snp_load_system(const snp_system_desc* d, snp_handle* out) {
@@ -426,6 +432,15 @@ int snp_load_system(const snp_system_desc* d, snp_handle* out) {
   return SNP_OK;
 }
 
+int snp_system_info(snp_handle h, int32_t* m, int32_t* R, int32_t* device) {
+  g_err.clear();
+  if (!h) return fail(SNP_E_INVALID, "handle is NULL");
+  if (m) *m = h->m;
+  if (R) *R = h->R;
+  if (device) *device = h->device;
+  return SNP_OK;
+}
+
 int snp_free(snp_handle h) {
   if (!h) return SNP_OK;
   cudaSetDevice(h->device);
@@ -512,6 +527,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   }
   if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_I8 && o->transition != SNP_T_TC_F8)
     return fail(SNP_E_INVALID, "unknown transition %d", o->transition);
+  if (o->reserved != 0) return fail(SNP_E_INVALID, "opts->reserved must be 0");
   if (o->transition == SNP_T_TC_I8 && h->max_abs_m > 127)
     return fail(SNP_E_RANGE, "int8 transition refused: |M_Pi| reaches %d > 127", h->max_abs_m);
   if (o->transition == SNP_T_TC_F8 && h->max_abs_m > 16)
@@ -626,7 +642,15 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     const uint64_t want =
         (uint64_t)((long double)(rows_plan + (int64_t)std::min<uint64_t>(qmax, 1 << 16)) * 4.0L / 3.0L / kBucket) + 1;
     TRY(rebuild_table(h, pow2_at_least(want), st));
+    if (!rs && g_hold_root_slot.exchange(0)) {  // testing hook: C0's slot stays "being claimed"
+      const uint64_t nslots = h->nbuckets * kBucket;
+      k_hold_slot_of_row<<<grid_for((int64_t)nslots, 256, nsm * 8), 256, 0, st>>>(h->d_slots.as<unsigned long long>(),
+                                                                                nslots, 0u);
+      CK(cudaGetLastError());
+    }
   }
+  const uint64_t wait_ns = o->timeout_ms > 0 ? (uint64_t)o->timeout_ms * 1000000ull : 0ull;
+  auto cancelled = [&]() { return o->cancel && *o->cancel != 0; };
   if (rs) {
     h->stats.assign(rs->stats, rs->stats + rs->nstats);
     for (int d = 0; d < rs->nstats; ++d)
@@ -643,6 +667,10 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   double rate = 1.0;  // new configurations per candidate, for chunk sizing
 
   for (int d = d_start; d <= o->depth; ++d) {
+    if (cancelled()) {
+      CK(cudaStreamSynchronize(st));
+      return fail(SNP_E_CANCELLED, "cancelled before depth %d", d);
+    }
     snp_depth_info sd;
     std::memset(&sd, 0, sizeof sd);
     const int64_t P = level_hi - level_lo;
@@ -756,6 +784,13 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
       return SNP_OK;
     };
     for (;;) {
+      if (cancelled()) {  // the passes in flight finish first
+        while (nfl > 0) {
+          const int rc = retire();
+          if (rc != SNP_OK) return rc;
+        }
+        return fail(SNP_E_CANCELLED, "cancelled at depth %d", d);
+      }
       // what the depth may still accept once the passes in flight are done, as expected from the last rate
       const double left = cap > 0 ? (double)remaining - rate * (double)pend_q : 1.0;
       if (nfl < 2 && g0 < T && !capped && remaining > 0 && (nfl == 0 || o->chunk > 0 || left > 0)) {
@@ -832,6 +867,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
           a.prec = with_records ? h->d_prec.as<ParentRec>() : nullptr;
           a.ctr = h->d_ctr.as<unsigned long long>();
           a.st = h->d_st.as<ChunkState>();
+          a.wait_ns = wait_ns;
           if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][0], st));
           if (tc5) {
             Tc5Args t;
@@ -1020,20 +1056,22 @@ int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out) {
 //
 // Some callers cannot allocate device memory when they need an exploration:
 // code that runs while a framework's caching allocator owns all free device
-// memory, host callbacks and other contexts where cudaMalloc may not be
-// called, and latency-critical loops that must never block on the allocator.
+// memory, and latency-critical loops that must never block on the allocator.
 // For them, snp_explore_static takes the output buffer from the caller (it
 // doubles as the configuration pool) and carves every other buffer it needs
 // (hash table, staging rows, first-occurrence bitmap, Psi prefix sums, scan
-// temporaries, counters) out of one array compiled into this library.
+// temporaries, counters) out of one array compiled into this library.  It
+// still launches kernels, copies counters to the host and waits on the
+// caller's stream once per pass, so it cannot be called from a stream
+// callback or on a stream that is being captured.
 //
 // The array is fixed at kStaticScratchBytes; every GPU that loads the library
 // holds it until the process exits.  Calls share it and each call leaves its
 // contents behind: a call clears what must start empty (table, bitmap,
 // counters) before use, and two calls whose work overlaps on the GPU (other
-// streams, other threads) race on it.  The first call on a device looks up the
-// array's device address (cudaGetSymbolAddress) with that device current; make
-// that first call before any stream capture.
+// streams, other threads) race on it.  The first call on a device (and the
+// first after the device's context was recreated) looks up the array's device
+// address (cudaGetSymbolAddress) with that device current.
 
 namespace {
 
@@ -1047,21 +1085,53 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 std::mutex g_static_mu;
 void* g_static_addr[kStaticMaxDevices] = {};
+void* g_static_ctx[kStaticMaxDevices] = {};  // the context each address was looked up in
 
-// Device address of g_static_scratch on the current device (looked up once).
+// The current CUDA context (cuCtxGetCurrent through the runtime's driver entry
+// point), or nullptr when it cannot be told.
+void* current_context() {
+  using Fn = int (*)(void**);
+  static Fn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<Fn>(p);
+  }();
+  void* ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
+
+// Device address of g_static_scratch on the current device: looked up once
+// per device and context (a recreated context maps the array anew).
 int static_scratch(int device, unsigned char** out) {
   if (device < 0 || device >= kStaticMaxDevices) return fail(SNP_E_INVALID, "device %d out of range", device);
+  void* ctx = current_context();
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[device]) {
+  if (!g_static_addr[device] || !ctx || g_static_ctx[device] != ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess || !p)
       return fail(SNP_E_CUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
     g_static_addr[device] = p;
+    g_static_ctx[device] = ctx;
   }
   *out = static_cast<unsigned char*>(g_static_addr[device]);
   return SNP_OK;
 }
+
+// Restores the caller's current device on scope exit.
+struct DeviceRestore {
+  int prev = -1;
+  DeviceRestore() {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+  }
+  ~DeviceRestore() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 struct StaticLayout {
   ChunkState* st;
@@ -1113,7 +1183,18 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
   if (capacity > kStaticMaxRows)
     return fail(SNP_E_INVALID, "capacity %lld exceeds the static scratch limit of %lld configurations",
                 (long long)capacity, (long long)kStaticMaxRows);
-  if (!is_device_ptr(out)) return fail(SNP_E_INVALID, "out must be device memory");
+  {
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, out) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SNP_E_INVALID, "out must be device memory");
+    }
+    if (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)
+      return fail(SNP_E_INVALID, "out must be device memory");
+    if (pa.type == cudaMemoryTypeDevice && pa.device != h->device)
+      return fail(SNP_E_INVALID, "out is on device %d, the system on device %d", pa.device, h->device);
+  }
+  DeviceRestore keep_device;
   CK(cudaSetDevice(h->device));
   unsigned char* base = nullptr;
   TRY(static_scratch(h->device, &base));
@@ -1206,6 +1287,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
       a.sidx_of = nullptr;
       a.store_cap = 0;
       a.st = L.st;
+      a.wait_ns = o->timeout_ms > 0 ? (uint64_t)o->timeout_ms * 1000000ull : 0ull;
       launch_expand(a, st, nsm);
       CK(cudaGetLastError());
       const uint32_t nwords = (uint32_t)((Q + 31) / 32);

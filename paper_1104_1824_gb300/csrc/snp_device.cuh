@@ -24,8 +24,28 @@ constexpr uint32_t kErrStaging = 4u;
 constexpr uint32_t kErrOverflow = 8u;
 constexpr uint32_t kErrInternal = 16u;
 
-// Bound on the wait for a reserved slot to be published.
+// Bound on the wait for a reserved slot to be published: this many polls,
+// and (when the caller gave one) a time limit.
 constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Warp-uniform: true once a retry loop has run kSpinLimit polls or, with
+// wait_ns > 0, wait_ns nanoseconds since its first poll (lane 0's clock).
+__device__ __forceinline__ bool wait_expired(int pass, uint64_t wait_ns, uint64_t& t0) {
+  if (pass >= kSpinLimit) return true;
+  if (wait_ns == 0) return false;
+  uint64_t now = __shfl_sync(0xffffffffu, global_ns(), 0);
+  if (pass == 0) {
+    t0 = now;
+    return false;
+  }
+  return now - t0 > wait_ns;
+}
 
 struct NeuronInfo;
 struct ApplEntry;

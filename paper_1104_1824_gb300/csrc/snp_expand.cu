@@ -422,6 +422,7 @@ template <bool VEC>
 __device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                                   bool todo) {
   const int lane = threadIdx.x & 31;
+  uint64_t t0 = 0;
   for (int pass = 0;; ++pass) {
     unsigned long long* owned = nullptr;
     const int status = todo ? resolve_lane<VEC>(a, row, key, lid, owned) : kDone;
@@ -438,7 +439,7 @@ __device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int3
     if (status == kOwner) finish_owner<VEC>(a, row, key, lid, owned, sidx);
     todo = status == kRetry;
     if (__all_sync(0xffffffffu, !todo)) break;
-    if (pass >= kSpinLimit) {
+    if (wait_expired(pass, a.wait_ns, t0)) {
       if (todo) atomicOr(&a.st->error, kErrTimeout);
       break;
     }
@@ -837,6 +838,7 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
   uint32_t orf = 0;
   const int32_t* other = nullptr;
   unsigned long long* owned = nullptr;
+  uint64_t t0 = 0;
   for (int pass = 0;; ++pass) {
     if (st == kRetry) {
       st = kProbe;
@@ -959,7 +961,7 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
       if (!__any_sync(0xffffffffu, st == kProbe)) break;
     }
     if (__all_sync(0xffffffffu, st != kRetry)) break;
-    if (pass >= kSpinLimit) {
+    if (wait_expired(pass, a.wait_ns, t0)) {
       if (st == kRetry) atomicOr(&a.st->error, kErrTimeout);
       break;
     }
@@ -1259,6 +1261,7 @@ __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t
     const uint64_t lid = base + threadIdx.x;
     bool done = lid >= a.Q || redundant[lid];
     const uint64_t key = done ? 0ull : mix64(hash[lid]);
+    uint64_t t0 = 0;
     for (int pass = 0;; ++pass) {
       if (!done) {
         unsigned long long* owned = nullptr;
@@ -1273,7 +1276,7 @@ __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t
         done = status != kRetry;
       }
       if (__all_sync(0xffffffffu, done)) break;
-      if (pass >= kSpinLimit) {
+      if (wait_expired(pass, a.wait_ns, t0)) {
         if (!done) atomicOr(&a.st->error, kErrTimeout);
         break;
       }

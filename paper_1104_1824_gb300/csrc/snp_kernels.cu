@@ -408,6 +408,13 @@ void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, in
 
 // Clears the first-occurrence bitmap; with ctr, one thread then moves the
 // device counters past the chunk's accepted configurations.
+__global__ void k_hold_slot_of_row(unsigned long long* slots, uint64_t n, uint32_t row) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    const unsigned long long v = slots[i];
+    if (v != kEmpty && (uint32_t)v == row) slots[i] = (v & 0xFFFFFFFF00000000ull) | kRowReserved;
+  }
+}
+
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x) bits[i] = 0;
   if (ctr && blockIdx.x == 0 && threadIdx.x == 0) {

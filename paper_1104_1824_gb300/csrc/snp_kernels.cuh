@@ -35,6 +35,7 @@ struct ClaimArgs {
   // lid's row to store row inplace_base + lid): an owner publishes it there.
   int32_t inplace = 0;
   uint64_t inplace_base = 0;
+  uint64_t wait_ns = 0;       // > 0: time limit of a wait for a slot being claimed
 };
 
 struct CommitArgs {
@@ -177,6 +178,8 @@ __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, 
 __global__ void k_commit(CommitArgs a);
 void launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t st);
 void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out, cudaStream_t st);
+// Testing hook: marks the slot holding store row `row` as being claimed.
+__global__ void k_hold_slot_of_row(unsigned long long* slots, uint64_t n, uint32_t row);
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st);
 __global__ void k_insert_rows(DevSys s, const int32_t* pool, const uint32_t* perm, int64_t r0, int64_t r1, DevTable t,
                               ChunkState* st);

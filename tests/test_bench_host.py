@@ -50,7 +50,7 @@ def test_e2e_steps_load_explore_and_read_back_every_time():
     calls = []
 
     class FakeLibrary:
-        SNP_T_TC_I8, SNP_T_SPARSE_I32 = 1, 0
+        SNP_T_TC_I8, SNP_T_SPARSE_I32, SNP_T_TC_F8 = 1, 0, 2
 
         def snp_load_system(self, m, *arrays):
             calls.append("load")

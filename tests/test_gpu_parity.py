@@ -390,6 +390,30 @@ def test_overflow_is_reported(gpu):
     assert s.count() == 3
 
 
+def test_overflow_bound_against_the_oracle(gpu):
+    """The device refuses to expand a configuration from which some column
+    could leave int32 in one step (the per-column bound: the sum over neurons
+    of their largest entry in that column, whatever fires); the oracle, in
+    int64, flags only a child that does leave it.  They agree on an actual
+    overflow and differ, by design, where the bound fires and no child
+    overflows (the oracle pins use the same two systems)."""
+    big = 2 ** 31 - 3
+    actual = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 0], [[1], [0]], [1, big])
+    assert oracle.Oracle(actual).explore(3).error == 1
+    s = gpu.System(actual)
+    for t in (gpu.SNP_T_SPARSE_I32, gpu.SNP_T_TC_I8, gpu.SNP_T_TC_F8):
+        with pytest.raises(gpu.SnpError) as ei:
+            s.explore(3, transition=t)
+        assert ei.value.code == gpu.SNP_E_OVERFLOW
+    bound_only = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 0], [[1], [0]], [0, big])
+    e = oracle.Oracle(bound_only).explore(3)
+    assert e.error == 0 and e.configs.shape[0] == 4
+    s = gpu.System(bound_only)
+    with pytest.raises(gpu.SnpError) as ei:
+        s.explore(3)
+    assert ei.value.code == gpu.SNP_E_OVERFLOW
+
+
 def test_state_and_buffer_errors(gpu):
     s = gpu.System(snp_synth.paper_example())
     with pytest.raises(gpu.SnpError) as ei:

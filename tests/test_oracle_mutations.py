@@ -29,6 +29,7 @@ MUTATIONS = {
     "psi_without_max1": ("p = sat_mul(p, l.empty() ? 1 : l.size());", "p = sat_mul(p, l.size());"),
     "parents_lifo": ("std::memcpy(parent.data(), res->configs.data() + p * s.m",
                      "std::memcpy(parent.data(), res->configs.data() + (level_end - 1 - (p - level_begin)) * s.m"),
+    "no_overflow_check": ("if (acc[j] < INT32_MIN || acc[j] > INT32_MAX) return false;", "(void)0;"),
     "rule_order_reversed": ("if (applicable(s, C, r)) lists[s.rule_neuron[r]].push_back(r);",
                             "if (applicable(s, C, r)) lists[s.rule_neuron[r]].insert(lists[s.rule_neuron[r]].begin(), r);"),
 }
@@ -50,6 +51,12 @@ def pins_pass(lib_path: str) -> bool:
     e = o.explore(1000, max_expand=9)
     if ["-".join(str(int(x)) for x in r) for r in e.configs] != g["allGenCk"].split():
         return False
+    # an actual int32 overflow stops the exploration; a possible one does not
+    big = 2 ** 31 - 3
+    for c0, want_error in (([1, big], 1), ([0, big], 0)):
+        x = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 0], [[1], [0]], c0)
+        if oracle.Oracle(x, lib_path=lib_path).explore(3).error != want_error:
+            return False
     # a budget of B examines exactly B candidates when more are available
     e = oracle.Oracle(snp_synth.random_64(1), lib_path=lib_path).explore(1, budget=100)
     if e.depths[1].examined != 100 or e.depths[1].truncated != 1:

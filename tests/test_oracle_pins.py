@@ -315,3 +315,36 @@ def test_depth10_of_paper_example_matches_brute_force():
     levels = bf.bfs_levels(s, 10)
     assert e.per_depth_new == [len(l) for l in levels]
     assert e.per_depth_new == [1, 2, 4, 6, 6, 6, 5, 5, 5, 5, 5]
+
+
+def test_overflow_flag_on_actual_overflow():
+    """Eq. next-config in int64, flagged when an entry leaves int32: neuron 0
+    (one spike) sends 5 spikes to neuron 1, which holds 2^31 - 3 and consumes
+    one.  Both neurons have one applicable rule, so the only spiking vector is
+    S = (1, 1) and the only child is C + S . M = (0, 2^31 + 1) (Python
+    integers below); the oracle's step raises and its exploration stops with
+    the error set, keeping only C0."""
+    big = 2 ** 31 - 3
+    system = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 0], [[1], [0]], [1, big])
+    child = [1 + int(system.M[0][0]) + int(system.M[1][0]), big + int(system.M[0][1]) + int(system.M[1][1])]
+    assert child == [0, 2 ** 31 + 1]
+    o = oracle.Oracle(system)
+    C = np.array([1, big], dtype=np.int32)
+    assert o.psi(C) == 1
+    with pytest.raises(OverflowError):
+        o.step(C)
+    e = o.explore(3)
+    assert e.error == 1 and e.configs.shape[0] == 1
+
+
+def test_no_overflow_flag_when_no_child_overflows():
+    """The same system with neuron 0 empty: neuron 1 fires alone and drains
+    (its count only falls), so no child leaves int32 and the oracle explores
+    normally, although neuron 1's column could still gain 5 in one step if
+    neuron 0 fired (the GPU's per-column bound refuses this case; see the
+    GPU test of the same system)."""
+    big = 2 ** 31 - 3
+    system = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [5, 0], [[1], [0]], [0, big])
+    e = oracle.Oracle(system).explore(3)
+    assert e.error == 0
+    assert e.configs.tolist() == [[0, big], [0, big - 1], [0, big - 2], [0, big - 3]]
