@@ -421,22 +421,22 @@ def bench_ours(args):
         dist.destroy_process_group()
 
 
-def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
-    """Each rank explores its own block of n independent systems (seeds
-    batch_seed_base(w, rank) ...): weak scaling, no exchange between ranks."""
+def time_batch(args, w, systems, handles, snp, torch, dist, dev, world, local, form: str, steps: int, warmup: int):
+    """Times `steps` batch explorations (one launch per depth for all systems)
+    in one transition form; returns the timing, plan and per-step counts."""
     import numpy as np
-    handles = [snp.System(x) for x in systems]
     hs = [h.h for h in handles]
     stream = torch.cuda.Stream(device=dev)
     o = snp.snp_explore_opts_init()
     o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
     o.stream = stream.cuda_stream
+    o.transition = transition_code(snp, form)
     t0 = time.perf_counter()
     chunk, tile, warps = snp.snp_batch_autotune(hs, o) if args.autotune else (2048, 0, 8)
     tune_s = time.perf_counter() - t0
     o.chunk, o.tile, o.warps = chunk, tile, warps
     statuses = np.zeros(len(hs), dtype=np.int32)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         snp.snp_explore_batch(hs, o, statuses)
     if world > 1:
         dist.barrier()
@@ -446,7 +446,7 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         snp.snp_explore_batch(hs, o, statuses)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -465,11 +465,49 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
             bytes_step += a.examined * 8 + dups * row + a.new * (row + 8) + a.new * 2 * row + a.parents * row
             per_depth.setdefault(d, 0)
             per_depth[d] += a.new
+    return dict(ms=ms, clocks=clk, new_step=new_step, bytes_step=bytes_step, per_depth=per_depth,
+                plan={"chunk": chunk, "tile": tile, "warps": warps, "autotuned": bool(args.autotune),
+                      "autotune_s": round(tune_s, 2)})
+
+
+def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
+    """Each rank explores its own block of n independent systems (seeds
+    batch_seed_base(w, rank) ...): weak scaling, no exchange between ranks.
+    Without --transition the fp8 tensor-core batch is timed after the sparse
+    one and reported under "compare"."""
+    import numpy as np
+    handles = [snp.System(x) for x in systems]
+    main_form = args.transition or "sparse"
+    r = time_batch(args, w, systems, handles, snp, torch, dist, dev, world, local, main_form, args.steps, args.warmup)
+    ms, clk, new_step, bytes_step, per_depth = r["ms"], r["clocks"], r["new_step"], r["bytes_step"], r["per_depth"]
     ms_max, (total_all,) = aggregate_ranks(ms, [new_step * args.steps], dist if world > 1 else None, dev)
     total_all = int(total_all)
     value = total_all / (ms_max * 1e-3)
     peak, peak_kind = measured_peaks()
     achieved = bytes_step * args.steps / (ms * 1e-3) / 1e9
+    compare = {}
+    if args.transition is None and not args.no_compare:
+        rf = time_batch(args, w, systems, handles, snp, torch, dist, dev, world, local, "f8", args.steps, args.warmup)
+        msf, (tot_f,) = aggregate_ranks(rf["ms"], [rf["new_step"] * args.steps], dist if world > 1 else None, dev)
+        vf = tot_f / (msf * 1e-3)
+        compare["tc_f8"] = {
+            "value": round(vf, 1), "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(msf / args.steps, 3), "ratio_to_sparse_i32": round(vf / value, 4),
+            "dtype": "fp8 e4m3 operands, fp32 accumulation (exact)", "plan": rf["plan"],
+            "roofline": {"kernel": "k_batch_depth<tensor-core form> (tcgen05 tiles of 128 candidates per system, "
+                                   "one launch per depth)", "bound": "hbm",
+                         "achieved": round(rf["bytes_step"] * args.steps / (rf["ms"] * 1e-3) / 1e9, 1),
+                         "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+                         "frac": round(rf["bytes_step"] * args.steps / (rf["ms"] * 1e-3) / 1e9 / peak, 4),
+                         "traffic": None},
+            "clocks": rf["clocks"],
+        }
+    chunk, tile, warps = r["plan"]["chunk"], r["plan"]["tile"], r["plan"]["warps"]
+    tune_s = r["plan"]["autotune_s"]
+    o = snp.snp_explore_opts_init()
+    o.depth, o.frontier_cap, o.candidate_budget = w["depth"], w["cap"], w["budget"]
+    o.chunk, o.tile, o.warps = chunk, tile, warps
+    o.transition = transition_code(snp, main_form)
     e2e = None
     if not args.no_e2e:
         arrays = [[np.ascontiguousarray(a, dtype=np.int32) for a in (x.rule_neuron, x.rule_i, x.rule_j, x.M, x.c0)]
@@ -502,9 +540,11 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
         line = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": {"sparse": "int32", "tc": "int8", "f8": "fp8"}[main_form],
+            "data": "synthetic",
             "config": {"workload": f"batch4096: {w['desc']}", "systems": len(systems), "depth": w["depth"],
-                       "frontier_cap": w["cap"], "candidate_budget": w["budget"], "transition": "sparse_i32",
+                       "frontier_cap": w["cap"], "candidate_budget": w["budget"],
+                       "transition": TRANSITION_NAMES[main_form],
                        "plan": {"chunk": chunk, "tile": tile, "warps": warps, "autotuned": bool(args.autotune),
                                 "autotune_s": round(tune_s, 2)},
                        "new_per_step": new_step, "per_depth_new": [per_depth[d] for d in sorted(per_depth)],
@@ -518,6 +558,8 @@ def bench_batch(args, w, systems, snp, torch, dist, dev, rank, world, local):
                          "avg_launch_ms": round(ms / args.steps / w["depth"], 3), "traffic": None},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (w["depth"] + 2) * args.steps, "clocks": clk,
         }
+        if compare:
+            line["compare"] = compare
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -318,9 +318,10 @@ def snp_batch_autotune(handles, opts: snp_explore_opts) -> Tuple[int, int, int]:
 
 
 def explore_batch(systems, depth: int, cap: int, budget: int = 0, max_expand: int = -1, chunk: int = 0,
-                  tile: int = 0, warps: int = 0, stream=None) -> np.ndarray:
+                  tile: int = 0, warps: int = 0, stream=None, transition: int = SNP_T_SPARSE_I32) -> np.ndarray:
     """Convenience: snp_explore_batch over System objects; returns the statuses."""
     o = snp_explore_opts_init()
+    o.transition = int(transition)
     o.depth, o.frontier_cap, o.candidate_budget, o.max_expand_value = int(depth), int(cap), int(budget), int(max_expand)
     o.chunk, o.tile, o.warps, o.stream = int(chunk), int(tile), int(warps), _stream_handle(stream)
     st = np.zeros(len(systems), dtype=np.int32)

@@ -38,6 +38,51 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// e4m3 byte of an integer v with |v| <= 16 (exact: 1 sign, 4 exponent bits
+// with bias 7, 3 mantissa bits).
+uint8_t e4m3_of_int(int v) {
+  if (v == 0) return 0;
+  const int a = std::abs(v);
+  int e = 0;
+  while ((2 << e) <= a) ++e;
+  const int mant = ((a << 3) >> e) - 8;
+  return (uint8_t)((v < 0 ? 0x80 : 0) | ((e + 7) << 3) | mant);
+}
+
+// fp8 tensor-core form: M_Pi^T in e4m3 for the tcgen05 B operand, uploaded on
+// first use.  Block b holds rules 32b .. 32b + 31 (zero past R) for every
+// column (zero past m, np = m rounded up to 16) as 8-column x 16-rule core
+// matrices (128 contiguous bytes: 8 columns of 16 rules), the two 16-rule
+// halves 128 bytes apart and the 8-column groups 256 bytes apart, so any run
+// of columns starting at a multiple of 8 is one contiguous copy.
+// Per-candidate hash and repeat buffers for q candidates.
+int tc5_prepare(snp_system* h, uint64_t q) {
+  if (!h->d_MB.p) {
+    const int m = h->m, R = h->R;
+    const int np = (m + 15) / 16 * 16, nblocks = (R + 31) / 32;
+    std::vector<uint8_t> mb((size_t)nblocks * np * 32, 0);
+    for (int b = 0; b < nblocks; ++b)
+      for (int j = 0; j < m; ++j) {
+        for (int k = 0; k < 32; ++k) {
+          const int r = b * 32 + k;
+          if (r >= R) break;
+          const size_t o = ((size_t)b * np + (j & ~7)) * 32 + (size_t)((k >> 4) * 128 + (j & 7) * 16 + (k & 15));
+          mb[o] = e4m3_of_int(h->M[(size_t)r * m + j]);
+        }
+      }
+    TRY(h->d_MB.reserve(mb.size()));
+    CK(cudaMemcpy(h->d_MB.p, mb.data(), mb.size(), cudaMemcpyHostToDevice));
+    h->t5_np = np;
+    h->t5_nblocks = nblocks;
+  }
+  if (h->tc_cap < q) {
+    TRY(h->d_hash.reserve(sizeof(unsigned long long) * q));
+    TRY(h->d_red.reserve(q));
+    h->tc_cap = q;
+  }
+  return SNP_OK;
+}
+
 }  // namespace snp
 
 namespace {
@@ -103,51 +148,6 @@ int tc_prepare(snp_system* h, uint64_t q, cudaStream_t st) {
     TRY(h->d_loc.reserve((size_t)q * h->mp));
     TRY(h->d_pidx.reserve(sizeof(uint32_t) * q));
     TRY(h->d_rows.reserve(sizeof(int32_t) * (size_t)q * h->m));
-    TRY(h->d_hash.reserve(sizeof(unsigned long long) * q));
-    TRY(h->d_red.reserve(q));
-    h->tc_cap = q;
-  }
-  return SNP_OK;
-}
-
-// e4m3 byte of an integer v with |v| <= 16 (exact: 1 sign, 4 exponent bits
-// with bias 7, 3 mantissa bits).
-uint8_t e4m3_of_int(int v) {
-  if (v == 0) return 0;
-  const int a = std::abs(v);
-  int e = 0;
-  while ((2 << e) <= a) ++e;
-  const int mant = ((a << 3) >> e) - 8;
-  return (uint8_t)((v < 0 ? 0x80 : 0) | ((e + 7) << 3) | mant);
-}
-
-// fp8 tensor-core form: M_Pi^T in e4m3 for the tcgen05 B operand, uploaded on
-// first use.  Block b holds rules 32b .. 32b + 31 (zero past R) for every
-// column (zero past m, np = m rounded up to 16) as 8-column x 16-rule core
-// matrices (128 contiguous bytes: 8 columns of 16 rules), the two 16-rule
-// halves 128 bytes apart and the 8-column groups 256 bytes apart, so any run
-// of columns starting at a multiple of 8 is one contiguous copy.
-// Per-candidate hash and repeat buffers for q candidates.
-int tc5_prepare(snp_system* h, uint64_t q) {
-  if (!h->d_MB.p) {
-    const int m = h->m, R = h->R;
-    const int np = (m + 15) / 16 * 16, nblocks = (R + 31) / 32;
-    std::vector<uint8_t> mb((size_t)nblocks * np * 32, 0);
-    for (int b = 0; b < nblocks; ++b)
-      for (int j = 0; j < m; ++j) {
-        for (int k = 0; k < 32; ++k) {
-          const int r = b * 32 + k;
-          if (r >= R) break;
-          const size_t o = ((size_t)b * np + (j & ~7)) * 32 + (size_t)((k >> 4) * 128 + (j & 7) * 16 + (k & 15));
-          mb[o] = e4m3_of_int(h->M[(size_t)r * m + j]);
-        }
-      }
-    TRY(h->d_MB.reserve(mb.size()));
-    CK(cudaMemcpy(h->d_MB.p, mb.data(), mb.size(), cudaMemcpyHostToDevice));
-    h->t5_np = np;
-    h->t5_nblocks = nblocks;
-  }
-  if (h->tc_cap < q) {
     TRY(h->d_hash.reserve(sizeof(unsigned long long) * q));
     TRY(h->d_red.reserve(q));
     h->tc_cap = q;

@@ -19,7 +19,7 @@ struct BatchArena {
   // shape the buffers and the captured graph were made for
   std::vector<snp_system*> handles;
   int64_t cap = 0, budget = 0;
-  int32_t max_expand = 0, blocks = 0, warps = 0, B = 0;
+  int32_t max_expand = 0, blocks = 0, warps = 0, B = 0, tc = 0;
   uint32_t qc = 0;
   uint64_t nslots = 0;
   size_t scratch_stride = 0, pool_bytes = 0;
@@ -41,7 +41,10 @@ struct BatchPlan {
 int batch_setup(snp_handle* hs, int32_t n, const snp_explore_opts* o) {
   if (!hs || n < 1 || !o) return fail(SNP_E_INVALID, "bad arguments");
   if (o->depth < 0) return fail(SNP_E_INVALID, "depth = %d < 0", o->depth);
-  if (o->transition != SNP_T_SPARSE_I32) return fail(SNP_E_INVALID, "the batch engine runs the sparse transition");
+  if (o->transition == SNP_T_TC_I8)
+    return fail(SNP_E_INVALID, "the batch engine's tensor-core form is SNP_T_TC_F8 (tcgen05 has no int8 kind on this GPU)");
+  if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_F8)
+    return fail(SNP_E_INVALID, "unknown transition %d", o->transition);
   if (o->record_parents) return fail(SNP_E_INVALID, "the batch engine keeps no parent records");
   if (o->frontier_cap < 1 || o->frontier_cap > (1 << 20))
     return fail(SNP_E_INVALID, "the batch engine needs 1 <= frontier_cap <= 2^20 (got %lld)", (long long)o->frontier_cap);
@@ -50,6 +53,12 @@ int batch_setup(snp_handle* hs, int32_t n, const snp_explore_opts* o) {
   for (int32_t i = 0; i < n; ++i) {
     if (!hs[i]) return fail(SNP_E_INVALID, "handle %d is NULL", i);
     if (hs[i]->device != dev) return fail(SNP_E_INVALID, "handle %d lives on device %d, not %d", i, hs[i]->device, dev);
+    if (o->transition == SNP_T_TC_F8) {
+      if (hs[i]->max_abs_m > 16)
+        return fail(SNP_E_RANGE, "fp8 transition refused: |M_Pi| of system %d reaches %d > 16", i, hs[i]->max_abs_m);
+      if ((hs[i]->R + 31) / 32 > 1024) return fail(SNP_E_INVALID, "system %d has more than 32768 rules", i);
+      TRY(tc5_prepare(hs[i], 0));
+    }
   }
   return SNP_OK;
 }
@@ -64,6 +73,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   const int nsm = sm_count(dev);
   const int64_t cap = o->frontier_cap;
   const int depth = o->depth;
+  const bool tc = o->transition == SNP_T_TC_F8;
   int m_max = 1;
   for (int32_t i = 0; i < n; ++i) m_max = std::max(m_max, hs[i]->m);
   const int64_t rows_per = 1 + (int64_t)depth * cap;
@@ -72,17 +82,20 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   // tile rows and warps
   int ts = 0;
   int B = plan.tile > 0 ? plan.tile : 32;  // shrunk below to what the shared memory holds
-  const int warps = plan.warps == 4 ? 4 : 8;
+  const int warps = (tc || plan.warps == 4) ? 4 : 8;
   size_t warp_smem = expand_smem_bytes(m_max, B, &ts);
   while (B > 1 && warp_smem * warps > (200u << 10)) warp_smem = expand_smem_bytes(m_max, --B, &ts);
-  if (warp_smem * warps > (220u << 10)) return fail(SNP_E_INVALID, "rows of %d neurons do not fit the batch tile", m_max);
+  if (!tc && warp_smem * warps > (220u << 10))
+    return fail(SNP_E_INVALID, "rows of %d neurons do not fit the batch tile", m_max);
   int blocks_per_sm = 1;
   {
     int nb = 0;
-    // one CTA per SM is always resident; two when registers and shared memory allow
-    nb = (warps == 4 && warp_smem * warps * 2 <= (200u << 10)) ? 2 : 1;
+    // one CTA per SM is always resident; two when registers and shared memory allow (the
+    // tensor-core form: two CTAs of 128 TMEM columns each)
+    nb = tc ? 2 : (warps == 4 && warp_smem * warps * 2 <= (200u << 10)) ? 2 : 1;
     blocks_per_sm = nb;
   }
+  if (tc) B = 0;
   const int blocks = std::max(1, std::min<int>(nsm * blocks_per_sm, n));
   const size_t scratch_stride = (batch_scratch_bytes(cap, plan.qc, m_max) + 255) & ~size_t(255);
 
@@ -98,7 +111,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
               arena->budget == (o->candidate_budget > 0 ? o->candidate_budget : 0) &&
               arena->max_expand == o->max_expand_value && arena->blocks == blocks && arena->warps == warps &&
               arena->B == B && arena->qc == plan.qc && arena->nslots == nslots && arena->pool_bytes == pool_bytes &&
-              arena->scratch_stride == scratch_stride;
+              arena->scratch_stride == scratch_stride && arena->tc == (tc ? 1 : 0);
   for (int32_t i = 0; same && i < n; ++i) same = arena->handles[i] == hs[i] && hs[i]->batch == arena;
   if (!same) {
     arena = std::make_shared<BatchArena>();
@@ -115,6 +128,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     arena->nslots = nslots;
     arena->pool_bytes = pool_bytes;
     arena->scratch_stride = scratch_stride;
+    arena->tc = tc ? 1 : 0;
     for (int32_t i = 0; i < n; ++i) {  // release older arenas before allocating
       hs[i]->batch.reset();
       hs[i]->result_pool = nullptr;
@@ -151,6 +165,9 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     b.cap = cap;
     b.budget = o->candidate_budget > 0 ? o->candidate_budget : 0;
     b.stats = arena->stats.as<BatchDepthStat>() + (size_t)i * (depth + 1);
+    b.MB = tc ? h->d_MB.as<uint8_t>() : nullptr;
+    b.np = h->t5_np;
+    b.nblocks = h->t5_nblocks;
   }
   TRY(arena->c0.reserve(sizeof(int32_t) * c0.size()));
   TRY(arena->c0_off.reserve(sizeof(int64_t) * n));
@@ -181,6 +198,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
   a.scratch_stride = scratch_stride;
   a.pmax = cap;
   a.m_max = m_max;
+  a.tc = tc ? 1 : 0;
 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (ms) {
@@ -282,11 +300,13 @@ extern "C" int snp_batch_autotune(snp_handle* hs, int32_t n, const snp_explore_o
   const uint32_t qcs[] = {1024, 2048, 4096};
   const int tiles[] = {8, 16, 32};
   const int ws[] = {4, 8};
+  const bool tc = o->transition == SNP_T_TC_F8;  // the tensor-core form: tile and warps are fixed
   float best = 1e30f;
   BatchPlan bestp;
   for (uint32_t qc : qcs)
     for (int tl : tiles)
       for (int w : ws) {
+        if (tc && (tl != tiles[0] || w != ws[0])) continue;
         BatchPlan p;
         p.qc = qc;
         p.tile = tl;

@@ -33,6 +33,7 @@
 // row (to the next store row; the batch engine and the allocation-free path
 // use staging row lid) and publish the slot.
 #include "snp_kernels.cuh"
+#include "snp_tcgen05.cuh"
 
 namespace snp {
 
@@ -1354,6 +1355,8 @@ struct BatchScratch {
   int32_t* staging;
   uint32_t *gmin, *slot_of, *srow, *own, *bits, *wbase;
   ChunkState* st;
+  unsigned long long* hash;  // [qc] tensor-core form: linear hash of each candidate's row
+  uint8_t* red;              // [qc] tensor-core form: the candidate repeats an earlier one
 };
 
 __device__ __forceinline__ BatchScratch batch_scratch(unsigned char* base, int64_t pmax, uint32_t qc, int m_max) {
@@ -1375,6 +1378,8 @@ __device__ __forceinline__ BatchScratch batch_scratch(unsigned char* base, int64
   b.bits = reinterpret_cast<uint32_t*>(take((qc / 32 + 1) * 4));
   b.wbase = reinterpret_cast<uint32_t*>(take((qc / 32 + 1) * 4));
   b.st = reinterpret_cast<ChunkState*>(take(sizeof(ChunkState)));
+  b.hash = reinterpret_cast<unsigned long long*>(take((size_t)qc * 8));
+  b.red = reinterpret_cast<uint8_t*>(take(qc));
   return b;
 }
 
@@ -1412,6 +1417,206 @@ __device__ void block_scan_sat(uint64_t* v, int64_t n, uint64_t* wsum) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core form of a batch pass (SNP_T_TC_F8): the rows of candidates
+// g0 .. g0 + Q - 1 of the CTA's current system, C' = C_p + S . M_Pi
+// (Eq. next-config) with the 0/1 spiking vector S of every firing neuron, by
+// tcgen05.mma kind::f8f6f4 over tiles of 128 candidates (one thread and one
+// TMEM lane per candidate), into the CTA's staging rows, with their linear
+// hashes and repeat flags; the pass then resolves them like the sparse form.
+// The MMA waits synchronously (the batch's CTAs overlap one another).
+
+constexpr int kBtcSlots = 8;  // rule blocks of the left operand held at once
+
+struct BatchTcSmem {
+  uint8_t* A;          // [kBtcSlots][4096] left operand
+  uint8_t* B;          // [kBtcSlots][128 * 32] M_Pi^T blocks of one 128-column chunk
+  uint32_t* bitmap;    // [32] active rule blocks (at most 1024 blocks)
+  uint16_t* slot_of;   // [1024]
+  uint16_t* act;       // [1024]
+  int* nact;
+  unsigned long long* bars;  // operand arrival, MMA completion
+  uint32_t* tmem_slot;
+};
+
+__host__ __device__ inline size_t batch_tc_smem_bytes() {
+  return (size_t)kBtcSlots * t5::kT5ABytes * 2 + 32 * 4 + 1024 * 2 * 2 + 16 + 16 + 16 + 256;
+}
+
+__device__ __forceinline__ BatchTcSmem batch_tc_smem(unsigned char* raw) {
+  unsigned char* p = reinterpret_cast<unsigned char*>(((uintptr_t)raw + 1023) & ~(uintptr_t)1023);
+  BatchTcSmem w;
+  w.A = p;
+  p += (size_t)kBtcSlots * t5::kT5ABytes;
+  w.B = p;
+  p += (size_t)kBtcSlots * t5::kT5ABytes;
+  w.bitmap = reinterpret_cast<uint32_t*>(p);
+  p += 32 * 4;
+  w.slot_of = reinterpret_cast<uint16_t*>(p);
+  p += 1024 * 2;
+  w.act = reinterpret_cast<uint16_t*>(p);
+  p += 1024 * 2;
+  w.nact = reinterpret_cast<int*>(p);
+  p += 16;
+  w.bars = reinterpret_cast<unsigned long long*>(p);
+  p += 16;
+  w.tmem_slot = reinterpret_cast<uint32_t*>(p);
+  return w;
+}
+
+// Chosen rule of every neuron of parent row prow for candidate t (last
+// neuron least significant): f(rule or -1, mask, spikes, neuron).  Returns
+// false if t is not a valid index.
+template <typename F>
+__device__ __forceinline__ bool batch_walk(const DevSys& s, const int32_t* prow, uint64_t t, F&& f) {
+  uint64_t q = t;
+  for (int n = s.m - 1; n >= 0; --n) {
+    const int32_t x = prow[n];
+    const uint32_t mask = (uint32_t)appl(s, n, x);
+    if (!mask) {
+      f(-1, 0u, x, n);
+      continue;
+    }
+    const uint32_t radix = (uint32_t)__popc(mask);
+    uint32_t d = 0;
+    if (radix > 1) {
+      d = (uint32_t)(q % radix);
+      q /= radix;
+    }
+    f(__ldg(s.first_rule + n) + nth_set_bit(mask, (int)d), mask, x, n);
+  }
+  return q == 0;
+}
+
+// Rows of the pass by tensor core; returns false when an mbarrier wait ran
+// out (the CTA then stops: products may still be in flight).
+__device__ bool batch_tc_rows(const ClaimArgs& a, const BatchSys* bs, const BatchTcSmem& w, uint32_t tmem,
+                              unsigned long long* hash, uint8_t* red_out, uint32_t& ph_b, uint32_t& ph_m) {
+  using namespace t5;
+  const DevSys& s = a.sys;
+  const int m = s.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int np = bs->np, nblocks = bs->nblocks;
+  const int nbw = (nblocks + 31) / 32, nchunks = (np + kT5NC - 1) / kT5NC;
+  const uint32_t bar_b = saddr(w.bars), bar_m = saddr(w.bars + 1);
+  const uint32_t ntiles = (a.Q + kT5M - 1) / kT5M;
+  for (uint32_t tile = 0; tile < ntiles; ++tile) {
+    const uint32_t lid = tile * kT5M + tid;
+    const bool valid = lid < a.Q;
+    const uint64_t g = a.g0 + (valid ? lid : tile * kT5M);
+    // parent: largest p with off[p] <= g
+    int64_t lo = 0, hi = a.P;
+    while (hi - lo > 1) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (__ldcg(a.off + mid) <= g) lo = mid;
+      else hi = mid;
+    }
+    const int32_t* prow = a.parents + (size_t)lo * m;
+    const uint64_t t = g - __ldcg(a.off + lo);
+    for (int i = tid; i < nbw; i += kT5M) w.bitmap[i] = 0u;
+    __syncthreads();
+    uint64_t h = 0;
+    bool red = false;
+    if (valid) {
+      const bool ok = batch_walk(s, prow, t, [&](int r, uint32_t mask, int32_t x, int n) {
+        h += col_hash(s, n, x);
+        if (r < 0) return;
+        atomicOr(w.bitmap + (r >> 10), 1u << ((r >> 5) & 31));
+        h += __ldg(s.rowkey + r);
+        red |= redundant_choice(s, mask, r);
+      });
+      if (!ok) atomicOr(&a.st->error, kErrInternal);
+      hash[lid] = h;
+      red_out[lid] = red ? 1 : 0;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      int cnt = 0;
+      for (int b0 = 0; b0 < nblocks; b0 += 32) {
+        const int bk = b0 + lane;
+        const bool on = bk < nblocks && ((w.bitmap[bk >> 5] >> (bk & 31)) & 1u);
+        const uint32_t bb = __ballot_sync(0xffffffffu, on);
+        if (on) {
+          const int pos = cnt + __popc(bb & ((1u << lane) - 1u));
+          w.act[pos] = (uint16_t)bk;
+          w.slot_of[bk] = (uint16_t)pos;
+        }
+        cnt += __popc(bb);
+      }
+      if (lane == 0) *w.nact = cnt;
+    }
+    __syncthreads();
+    const int nact = *w.nact;
+    const int ngroups = (nact + kBtcSlots - 1) / kBtcSlots;
+    for (int nc = 0; nc < nchunks; ++nc) {
+      const int c0 = nc * kT5NC, nc_cols = min(kT5NC, np - c0);
+      for (int gi = 0; gi < ngroups; ++gi) {
+        const int ga = gi * kBtcSlots, gb = min(nact, ga + kBtcSlots), gn = gb - ga;
+        if (nc == 0 || ngroups > 1) {  // left operand of this group of blocks
+          uint4* A4 = reinterpret_cast<uint4*>(w.A);
+          for (int i = tid; i < gn * (kT5ABytes / 16); i += kT5M) A4[i] = make_uint4(0, 0, 0, 0);
+          __syncthreads();
+          if (valid)
+            batch_walk(s, prow, t, [&](int r, uint32_t, int32_t, int) {
+              if (r < 0) return;
+              const int pos = w.slot_of[r >> 5];
+              if (pos >= ga && pos < gb) w.A[(size_t)(pos - ga) * kT5ABytes + a_off(tid, r & 31)] = kF8PlusOne;
+            });
+          fence_async_smem();
+          __syncthreads();
+        }
+        bool ok = true;
+        if (tid == 0) {
+          const uint32_t bytes = (uint32_t)nc_cols * kT5K;
+          bar_expect_tx(bar_b, bytes * (uint32_t)gn);
+          for (int k = 0; k < gn; ++k)
+            bulk_g2s(saddr(w.B + (size_t)k * kT5ABytes), bs->MB + ((size_t)w.act[ga + k] * np + c0) * kT5K, bytes,
+                     bar_b);
+          ok = bar_wait(bar_b, ph_b);
+          ph_b ^= 1u;
+          fence_after_sync();
+          const uint32_t id = idesc_f8(kT5M, nc_cols);
+          for (int k = 0; k < gn; ++k)
+            mma_f8(tmem, smem_desc(saddr(w.A + (size_t)k * kT5ABytes), 128, 256),
+                   smem_desc(saddr(w.B + (size_t)k * kT5ABytes), 128, 256), id, (gi > 0 || k > 0) ? 1u : 0u);
+          mma_commit(bar_m);
+        }
+        ok = bar_wait(bar_m, ph_m) && ok;
+        ph_m ^= 1u;
+        fence_after_sync();
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) atomicOr(&a.st->error, kErrTimeout);
+          return false;
+        }
+      }
+      // C' = C_p + D for this chunk's columns, to staging row lid
+      const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16);
+      for (int c = 0; c < nc_cols; c += 32) {
+        uint32_t r[32];
+        const bool two = c + 32 <= nc_cols;
+        if (nact == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) r[i] = 0u;
+        } else {
+          if (two) tmem_ld32(acc + (uint32_t)c, r);
+          else tmem_ld16(acc + (uint32_t)c, r);
+          tmem_wait_ld();
+        }
+        const int j0 = c0 + c, cnt = min(two ? 32 : 16, m - j0);
+        if (valid && !red) {
+          int32_t* dst = a.staging + (size_t)lid * m + j0;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (i < cnt) __stcg(dst + i, prow[j0 + i] + __float2int_rn(__uint_as_float(r[i])));
+        }
+      }
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+    }
+  }
+  return true;
+}
+
 }  // namespace
 
 __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n) {
@@ -1431,20 +1636,44 @@ __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0
   }
 }
 
-template <int kThreads>
+template <int kThreads, bool TC>
 __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ unsigned int s_next;
   __shared__ uint64_t s_wsum[kThreads / 32];
-  __shared__ unsigned int s_cnt, s_stop, s_capped, s_last;
+  __shared__ unsigned int s_cnt, s_stop, s_capped, s_last, s_broken;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = kThreads / 32;
   BatchScratch sc = batch_scratch(ba.scratch + (size_t)blockIdx.x * ba.scratch_stride, ba.pmax, ba.qc, ba.m_max);
+  // tensor-core form: operands in shared memory, 128 TMEM columns, two mbarriers
+  BatchTcSmem tw{};
+  uint32_t tmem = 0, ph_b = 0, ph_m = 0;
+  if constexpr (TC) {
+    tw = batch_tc_smem(smem_raw);
+    if (tid == 0) {
+      t5::bar_init(t5::saddr(tw.bars), 1);
+      t5::bar_init(t5::saddr(tw.bars + 1), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      s_broken = 0;
+    }
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(t5::saddr(tw.tmem_slot)),
+                   "r"((uint32_t)t5::kT5NC));
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    t5::fence_before_sync();
+    __syncthreads();
+    t5::fence_after_sync();
+    tmem = *tw.tmem_slot;
+  }
   for (;;) {
     if (tid == 0) s_next = atomicAdd(ba.queue + ba.launch, 1u);
     __syncthreads();
     const int32_t si = (int32_t)s_next;
     __syncthreads();
-    if (si >= ba.n) return;
+    if (si >= ba.n) break;
+    if constexpr (TC) {
+      if (s_broken) break;
+    }
     BatchSys* bs = ba.sys + si;
     const int32_t d = bs->cur_depth + 1;
     if (bs->done || d > bs->target_depth) continue;
@@ -1516,10 +1745,34 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
       a.sidx_of = nullptr;
       a.store_cap = 0;
       a.st = sc.st;
-      if ((m & 3) == 0)
-        expand_warp<true, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
-      else
-        expand_warp<false, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+      if constexpr (TC) {
+        if (!batch_tc_rows(a, bs, tw, tmem, sc.hash, sc.red, ph_b, ph_m)) {
+          if (tid == 0) {
+            s_broken = 1;
+            atomicOr(&bs->error, kErrTimeout);
+          }
+          __syncthreads();
+          break;
+        }
+        __threadfence();
+        __syncthreads();
+        // step (d) for the pass's rows, 32 candidates per warp at a time
+        for (uint32_t b0 = (uint32_t)warp * 32u; b0 < Q; b0 += (uint32_t)nwarps * 32u) {
+          const uint32_t lid = b0 + (uint32_t)lane;
+          const bool todo = lid < Q && !sc.red[lid];
+          const uint64_t key = todo ? mix64(sc.hash[lid]) : 0ull;
+          const int32_t* row = sc.staging + (size_t)(lid < Q ? lid : 0) * m;
+          if ((m & 3) == 0)
+            resolve_warp<true, 1>(a, row, key, lid, todo);
+          else
+            resolve_warp<false, 1>(a, row, key, lid, todo);
+        }
+      } else {
+        if ((m & 3) == 0)
+          expand_warp<true, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+        else
+          expand_warp<false, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+      }
       __threadfence();
       __syncthreads();
       // first-occurrence marks
@@ -1618,13 +1871,23 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
     }
     __syncthreads();
   }
+  if constexpr (TC) {
+    // products of a pass whose wait ran out may still be in flight
+    if (s_broken && tid == 0) (void)t5::bar_wait(t5::saddr(tw.bars + 1), ph_m ^ 1u);
+    t5::fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)t5::kT5NC));
+  }
 }
+
+size_t batch_tc_smem_bytes_host() { return batch_tc_smem_bytes() + 1024; }
 
 size_t batch_scratch_bytes(int64_t pmax, uint32_t qc, int m_max) {
   auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
   return r((size_t)std::max<int64_t>(pmax + 1, qc / 32 + 1) * 8) + r((pmax + 1) * 8) + r((size_t)qc * m_max * 4) +
          3 * r(qc * 4) + 3 * r((qc / 32 + 1) * 4) +
-         r(sizeof(ChunkState));
+         r(sizeof(ChunkState)) + r((size_t)qc * 8) + r(qc);
 }
 
 size_t expand_smem_bytes(int m_max, int B, int* ts) {
@@ -1633,13 +1896,19 @@ size_t expand_smem_bytes(int m_max, int B, int* ts) {
 }
 
 void launch_batch_depth(const BatchArgs& a, int blocks, int warps, cudaStream_t st) {
+  if (a.tc) {  // four warps: the 128 TMEM lanes of a tile
+    const size_t smem = batch_tc_smem_bytes_host();
+    cudaFuncSetAttribute(k_batch_depth<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch_depth<128, true><<<blocks, 128, smem, st>>>(a);
+    return;
+  }
   const size_t smem = a.warp_smem * warps;
   if (warps == 4) {
-    cudaFuncSetAttribute(k_batch_depth<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_batch_depth<128><<<blocks, 128, smem, st>>>(a);
+    cudaFuncSetAttribute(k_batch_depth<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch_depth<128, false><<<blocks, 128, smem, st>>>(a);
   } else {
-    cudaFuncSetAttribute(k_batch_depth<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_batch_depth<256><<<blocks, 256, smem, st>>>(a);
+    cudaFuncSetAttribute(k_batch_depth<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_batch_depth<256, false><<<blocks, 256, smem, st>>>(a);
   }
 }
 

@@ -217,3 +217,8 @@ struct snp_system {
   snp::DevTable table() const { return snp::DevTable{d_slots.as<unsigned long long>(), nbuckets - 1}; }
 };
 
+namespace snp {
+// fp8 tensor-core form: uploads M_Pi^T in e4m3 on first use (the operand of
+// tcgen05.mma); hash and repeat buffers for q candidates (snp_api.cu).
+int tc5_prepare(snp_system* h, uint64_t q);
+}  // namespace snp

@@ -85,6 +85,9 @@ struct BatchSys {
   int32_t max_expand;
   int64_t cap, budget;         // per-depth frontier cap (>= 1) and candidate budget (<= 0: none)
   struct BatchDepthStat* stats;  // [target_depth + 1]
+  // fp8 tensor-core form: M_Pi^T in e4m3 (tc5_pack_mt layout), columns rounded to 16, rule blocks
+  const uint8_t* MB;
+  int32_t np, nblocks;
 };
 
 struct BatchDepthStat {
@@ -109,6 +112,7 @@ struct BatchArgs {
   size_t scratch_stride;
   int64_t pmax;                // largest frontier a system may have (largest cap)
   int32_t m_max;
+  int32_t tc;                  // 1: rows by the fp8 tensor-core form (four warps per CTA)
 };
 
 // Bytes of per-CTA scratch for frontiers of up to pmax rows and passes of qc candidates.
@@ -116,6 +120,8 @@ size_t batch_scratch_bytes(int64_t pmax, uint32_t qc, int m_max);
 // Per-warp shared memory of the expand loop for rows of up to m_max neurons.
 size_t expand_smem_bytes(int m_max, int B, int* ts);
 void launch_batch_depth(const BatchArgs& a, int blocks, int warps, cudaStream_t st);
+// Dynamic shared memory of the batch kernel's tensor-core form.
+size_t batch_tc_smem_bytes_host();
 __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n);
 
 // Step (a) and Psi for P frontier rows; returns the launches made.

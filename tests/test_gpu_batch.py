@@ -100,3 +100,61 @@ def test_batch_rejects_bad_options(gpu):
     with pytest.raises(gpu.SnpError) as ei:
         gpu.snp_explore_batch([x.h for x in h], o)
     assert ei.value.code == gpu.SNP_E_INVALID
+
+
+# --- the fp8 tensor-core form in the batch engine ---
+
+def test_batch_tc_systems_match_oracle(gpu):
+    systems = snp_synth.batch_systems(24)
+    handles = [gpu.System(x) for x in systems]
+    st = gpu.explore_batch(handles, 4, cap=512, budget=8192, transition=gpu.SNP_T_TC_F8)
+    assert (st == 0).all()
+    for h, x in zip(handles, systems):
+        assert_matches_oracle(h, x, 4, 512, 8192)
+
+
+@pytest.mark.parametrize("cap,budget,chunk", [(1, 0, 0), (3, 7, 32), (50, 0, 100), (7, 40, 0)])
+def test_batch_tc_tiny_systems(gpu, cap, budget, chunk):
+    rng = np.random.default_rng(4000 + cap * 17 + budget)
+    systems = [bf.tiny_system(rng, m_max=4, r_max=9) for _ in range(40)]
+    handles = [gpu.System(x) for x in systems]
+    st = gpu.explore_batch(handles, 5, cap=cap, budget=budget, chunk=chunk, transition=gpu.SNP_T_TC_F8)
+    assert (st == 0).all()
+    for h, x in zip(handles, systems):
+        assert_matches_oracle(h, x, 5, cap, budget)
+
+
+def test_batch_tc_wide_and_many_rule_systems(gpu):
+    """Rows of 129 to 700 neurons (several 128-column chunks) and a system of
+    16 rules per neuron (more rule blocks than the operand holds at once)."""
+    systems = [snp_synth.random_system(60 + k, m, (1, 3), (2, 6), (0, 5), "sparse")
+               for k, m in enumerate((129, 300, 700))]
+    systems.append(snp_synth.random_system(77, 128, (16, 16), (2, 4), (0, 6), "sparse"))
+    handles = [gpu.System(x) for x in systems]
+    st = gpu.explore_batch(handles, 3, cap=400, budget=4000, transition=gpu.SNP_T_TC_F8)
+    assert (st == 0).all()
+    for h, x in zip(handles, systems):
+        assert_matches_oracle(h, x, 3, 400, 4000)
+
+
+def test_batch_tc_equals_sparse_at_batch_settings(gpu):
+    systems = snp_synth.batch_systems(64)
+    a = [gpu.System(x) for x in systems]
+    b = [gpu.System(x) for x in systems]
+    assert (gpu.explore_batch(a, 6, cap=1 << 12, budget=1 << 16) == 0).all()
+    assert (gpu.explore_batch(b, 6, cap=1 << 12, budget=1 << 16, transition=gpu.SNP_T_TC_F8) == 0).all()
+    for x, y in zip(a, b):
+        assert (x.reachable() == y.reachable()).all()
+        assert [(p.new, p.examined) for p in x.depth_stats()] == [(p.new, p.examined) for p in y.depth_stats()]
+
+
+def test_batch_tc_refusals(gpu):
+    systems = snp_synth.batch_systems(2)
+    handles = [gpu.System(x) for x in systems]
+    with pytest.raises(gpu.SnpError) as ei:
+        gpu.explore_batch(handles, 2, cap=16, transition=gpu.SNP_T_TC_I8)
+    assert ei.value.code == gpu.SNP_E_INVALID
+    big = snp_synth.make_system(2, [0, 1], [1, 1], [1, 1], [1, 1], [17, 1], [[1], [0]], [3, 3])
+    with pytest.raises(gpu.SnpError) as ei:
+        gpu.explore_batch([gpu.System(big)], 2, cap=16, transition=gpu.SNP_T_TC_F8)
+    assert ei.value.code == gpu.SNP_E_RANGE

@@ -11,8 +11,8 @@
   recorded child of their recorded parent (the oracle recomputes it); the
   per-depth records follow the cap and budget rule.
 * All 4096 systems of the batch workload (depth 6, cap 2^12, budget 2^16) in
-  one snp_explore_batch call, each against its oracle digest
-  (tests/golden/batch4096_digests.json).
+  one snp_explore_batch call, sparse and fp8 tensor-core forms, each against
+  its oracle digest (tests/golden/batch4096_digests.json).
 * The serving loop on 200 requests of the serving stream's own ranges (m up
   to 512, depth up to 32, cap 2^12, budget 2^16): each result alone equals
   the result in the mix.
@@ -107,12 +107,14 @@ def _system_digest(rows: np.ndarray, per_depth) -> str:
 
 
 @pytest.mark.slow
-def test_batch4096_every_system(gpu):
+@pytest.mark.parametrize("form", ["sparse", "f8"])
+def test_batch4096_every_system(gpu, form):
     with open(os.path.join(GOLDEN, "batch4096_digests.json")) as f:
         g = json.load(f)
     systems = snp_synth.batch_systems(g["n"], g["base_seed"])
     handles = [gpu.System(x) for x in systems]
-    st = gpu.explore_batch(handles, g["depth"], cap=g["cap"], budget=g["budget"])
+    t = gpu.SNP_T_SPARSE_I32 if form == "sparse" else gpu.SNP_T_TC_F8
+    st = gpu.explore_batch(handles, g["depth"], cap=g["cap"], budget=g["budget"], transition=t)
     assert (st == 0).all()
 
     def check(k):
