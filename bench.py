@@ -49,6 +49,12 @@ METRIC = "new configurations/sec per BFS depth (bit-exact), int8-TC batched vs p
 UNIT = "new configurations/s"
 
 WORKLOADS = {
+    "paper": dict(depth=10, cap=0, budget=0,
+                  desc="the paper's 3-neuron, 5-rule system generating N - {1} (C0 = (2,1,1), M_Pi of Section 2.2, "
+                       "rules a^k -> a read as 'at least k spikes'); BFS to depth 10, no cap, no budget "
+                       "(50 configurations)",
+                  cpu_sample=dict(depth=10, cap=0, budget=0),
+                  ref_sample=dict(depth=10, cap=0, budget=0)),
     "random64": dict(seed=1, depth=8, cap=1 << 20, budget=1 << 24,
                      desc="random SNP system seed 1: m=64, 2-3 rules/neuron, a^i(a^j)* with i U[1,4], j U{0,1,2}, "
                           "c U[1,i], p U{1,2} (15% forgetting), out-degree 4, C0 U[0,6]; BFS depth 8, "
@@ -80,7 +86,7 @@ WORKLOADS = {
 
 
 # timed steps by default: a timed region of at least 2 s
-DEFAULT_STEPS = {"dense1024": 80, "random64": 300, "batch4096": 5, "serving": 1}
+DEFAULT_STEPS = {"dense1024": 80, "random64": 300, "batch4096": 5, "serving": 1, "paper": 2000}
 
 
 def rank_info():
@@ -114,6 +120,8 @@ def make_system(name, rank: int = 0):
     w = WORKLOADS[name]
     if name == "batch4096":
         return snp_synth.batch_systems(w["n"], batch_seed_base(w, rank))
+    if name == "paper":
+        return snp_synth.paper_example()
     return snp_synth.random_64(w["seed"]) if name == "random64" else snp_synth.dense_1024(w["seed"])
 
 
@@ -636,6 +644,8 @@ def bench_serving(args, w, snp, torch, rank):
         "ms_per_step": round(info.span_ms, 1), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": f"serving: {w['desc']}", "requests": n, "of_stream": w["requests"],
+                   "subset": f"the first {n} arrivals of the {w['requests']}-request stream (its whole length would "
+                             f"take {w['requests'] / rate / 60:.0f} minutes of arrivals at {rate:g}/s)",
                    "rate_per_s": None if args.calibrate else rate, "calibration": bool(args.calibrate),
                    "max_active": args.max_active, "hbm_budget_gb": round(budget / 2 ** 30, 1),
                    "system_generation_s": round(gen_s, 1)},
@@ -717,7 +727,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None,
-                    help="timed steps (default: at least 2 s of them: dense1024 80, random64 300, batch4096 5)")
+                    help="timed steps (default: dense1024 80, random64 300 (at least 2 s), batch4096 5, paper 2000)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dense1024")

@@ -72,7 +72,7 @@ struct Tc5Smem {
   uint8_t* A;          // [slots][4096] left operand, one block per slot
   uint8_t* B;          // [kT5Stages][ncmax * 32] right operand ring
   uint8_t* stg;        // [4 warps][kT5Stg][4096] store staging (128-byte swizzle)
-  int32_t* adj;        // [np] C_ref - kT5Bias (delta form)
+  int32_t* adj;        // [2][np] C_ref - kT5Bias (delta form): this tile's and the next tile's reference
   uint32_t* masks;     // [m] applicable rules of the cached parent
   uint16_t* list;      // [m] its neurons with >= 2 applicable rules, least significant first
   uint8_t* refd;       // [m] digits of t_ref over list
@@ -83,8 +83,9 @@ struct Tc5Smem {
   unsigned long long* bars;  // a_full, a_empty, acc_full[2], acc_empty[2], drain, b_full[S], b_empty[S]
   uint32_t* tmem_slot;
   long long* cp;       // cached parent (frontier index), -1: none
-  unsigned long long* scal;  // [0] t_ref, [1] h_ref, [2] p_first
-  int* iscal;          // [0] list_len, [1] ref_len, [2] ref_red, [3] nact, [4] single, [5] stop
+  unsigned long long* scal;  // [0] t_ref, [1] h_ref, [2] p_first, [3] first candidate a chained tile must start at,
+                             // [4] next h_ref
+  int* iscal;          // [0] list_len, [1] ref buffer, [2] ref_red, [3] nact, [4] single, [5] stop, [6] next ref_red
 };
 
 }  // namespace
@@ -96,7 +97,7 @@ size_t tc5_smem_bytes(int m, int nblocks, int slots) {
   b += (size_t)slots * kT5ABytes;
   b += (size_t)kT5Stages * ncmax * kT5K;
   b += (size_t)4 * kT5Stg * 4096;
-  b += (size_t)np * 4;
+  b += (size_t)np * 4 * 2;
   b += (size_t)((m + 3) / 4 * 4) * 4;
   b += (size_t)((m + 7) / 8 * 8) * 2;
   b += (size_t)((m + 15) / 16 * 16);
@@ -120,7 +121,7 @@ __device__ __forceinline__ Tc5Smem carve(unsigned char* base, int m, int np, int
   w.B = p;
   p += (size_t)kT5Stages * ncmax * kT5K;
   w.adj = reinterpret_cast<int32_t*>(p);
-  p += (size_t)np * 4;
+  p += (size_t)np * 4 * 2;
   w.masks = reinterpret_cast<uint32_t*>(p);
   p += (size_t)((m + 3) / 4 * 4) * 4;
   w.list = reinterpret_cast<uint16_t*>(p);
@@ -144,7 +145,7 @@ __device__ __forceinline__ Tc5Smem carve(unsigned char* base, int m, int np, int
   w.cp = reinterpret_cast<long long*>(p);
   p += 8;
   w.scal = reinterpret_cast<unsigned long long*>(p);
-  p += 32;
+  p += 48;
   w.iscal = reinterpret_cast<int*>(p);
   return w;
 }
@@ -204,24 +205,26 @@ __device__ __forceinline__ uint32_t digit_of(uint64_t& q, uint32_t radix) {
 
 // Walks the nonzero entries of the candidate's left-operand row.  Delta form:
 // f(rule of t, rule of t_ref, change in the count of repeated-row choices) for
-// each neuron whose digit differs from t_ref's.  Full form: f(chosen rule or -1, mask, spikes, neuron) for every
+// each neuron whose digit differs from t_ref's (t and t_ref of one parent).  Full form: f(chosen rule or -1, mask, spikes, neuron) for every
 // neuron of parent row prow (applicability evaluated on the way).  Returns
 // false if t is not a valid index.
 template <typename F>
-__device__ __forceinline__ bool t5_walk_delta(const DevSys& s, const Tc5Smem& w, int list_len, int ref_len, uint64_t t,
-                                              F&& f) {
-  uint64_t q = t;
+__device__ __forceinline__ bool t5_walk_delta(const DevSys& s, const Tc5Smem& w, int list_len, uint64_t t,
+                                              uint64_t t_ref, F&& f) {
+  // digits of t and t_ref, least significant first, until the remaining
+  // quotients agree (every more significant digit is then the same)
+  uint64_t q = t, qr = t_ref;
   const int lim = min(list_len, kT5Ent);
-  for (int e = 0; e < lim && (q != 0 || e < ref_len); ++e) {
+  for (int e = 0; e < lim && q != qr; ++e) {
     const uint4 en = w.ent[e];  // mask, repeated-row choices, first rule, radix
     const uint32_t d = digit_of(q, en.w);
-    const uint32_t dr = e < ref_len ? w.refd[e] : 0u;
+    const uint32_t dr = digit_of(qr, en.w);
     if (d != dr) {
       const int fr = (int)en.z;
       f(fr + nth_set_bit(en.x, (int)d), fr + nth_set_bit(en.x, (int)dr), (int)((en.y >> d) & 1u) - (int)((en.y >> dr) & 1u));
     }
   }
-  return q == 0;
+  return q == qr;
 }
 
 template <typename F>
@@ -257,7 +260,7 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
   const DevSys& s = a.s;
   const int m = s.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t* prow = t5_parent_row(a, p);
-  int32_t* ref = w.adj;  // C_ref while it is built, then C_ref - kT5Bias
+  int32_t* ref = w.adj;  // buffer 0: C_ref while it is built, then C_ref - kT5Bias
   ew_sync();
   for (int n = tid; n < m; n += kT5M) {
     const int32_t x = __ldcg(prow + n);
@@ -287,7 +290,7 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
       for (; e < cnt && q != 0; ++e) w.refd[e] = (uint8_t)digit_of(q, (uint32_t)__popc(w.masks[w.list[e]]));
       if (q != 0) atomicOr(&a.st->error, kErrInternal);  // t_ref >= Psi
       w.iscal[0] = cnt;
-      w.iscal[1] = e;
+      w.iscal[6] = e;  // digits of t_ref that may be nonzero
     }
     for (int e = lane; e < min(cnt, kT5Ent); e += 32) {  // the walk's per-entry constants
       const int n = w.list[e];
@@ -299,7 +302,7 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
     }
   }
   ew_sync();
-  const int ref_len = w.iscal[1];
+  const int ref_len = w.iscal[6];
   // C_ref: every firing neuron's first applicable rule, then the swaps of the
   // neurons whose reference digit is not 0
   int red = 0;
@@ -345,6 +348,7 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
   if (tid == 0) {
     *w.cp = p;
     w.scal[0] = t_ref;
+    w.iscal[1] = 0;  // the reference row is in buffer 0
   }
   ew_sync();
 }
@@ -482,7 +486,12 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
     ew_sync();
     const int64_t p_first = (int64_t)w.scal[2];
     const bool single = w.iscal[4] != 0;
-    if (single && *w.cp != p_first) t5_load_parent(a, w, p_first, g_first - __ldcg(a.off + p_first));
+    // The reference of a tile that follows a full tile of the same parent is
+    // the candidate just before it, whose row, hash and repeat count the last
+    // thread kept from that tile; otherwise the parent's state is rebuilt with
+    // the tile's first candidate as reference.
+    if (single && !(*w.cp == p_first && w.scal[3] == g_first))
+      t5_load_parent(a, w, p_first, g_first - __ldcg(a.off + p_first));
 
     // this thread's candidate
     const uint64_t lid = lid0 + tid;
@@ -494,7 +503,11 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
     if (tile == 0 && tid == 0) a.st->p_first = (unsigned long long)p;
     if (tile + 1 == ntiles && tid + 1 == (int)nrows) a.st->p_last = (unsigned long long)p;
     const int32_t* prow = t5_parent_row(a, p);
-    const int list_len = w.iscal[0], ref_len = w.iscal[1];
+    const int list_len = w.iscal[0];
+    const uint64_t t_ref = w.scal[0];
+    const int32_t* adj = w.adj + (size_t)w.iscal[1] * np;          // this tile's reference row - bias
+    int32_t* adj_next = w.adj + (size_t)(w.iscal[1] ^ 1) * np;    // the next tile's
+    const bool keep_last = single && nrows == (uint32_t)kT5M && tid == kT5M - 1;
 
     // pass 1: active blocks, hash, repeated-row choices
     uint64_t h = 0;
@@ -504,13 +517,17 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
       if (single) {
         h = w.scal[1];
         int rc = w.iscal[2];
-        good = t5_walk_delta(s, w, list_len, ref_len, t, [&](int rn, int ro, int dred) {
+        good = t5_walk_delta(s, w, list_len, t, t_ref, [&](int rn, int ro, int dred) {
           mark_block(w, rn);
           mark_block(w, ro);
           h += __ldg(s.rowkey + rn) - __ldg(s.rowkey + ro);
           rc += dred;
         });
         red = rc > 0;
+        if (keep_last) {  // the next tile's reference
+          w.scal[4] = h;
+          w.iscal[6] = rc;
+        }
       } else {
         good = t5_walk_full(s, prow, t, [&](int r, uint32_t mask, int32_t x, int n) {
           h += col_hash(s, n, x);
@@ -557,7 +574,7 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
       ew_sync();
       if (valid) {
         if (single) {
-          t5_walk_delta(s, w, list_len, ref_len, t, [&](int rn, int ro, int) {
+          t5_walk_delta(s, w, list_len, t, t_ref, [&](int rn, int ro, int) {
             put_entry(w, tid, rn, true, ga, gb);
             put_entry(w, tid, ro, false, ga, gb);
           });
@@ -614,12 +631,20 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
 #pragma unroll
           for (int i = 0; i < 32; i += 4) {
             if (i < cnt) {
-              const int4 b4 = *reinterpret_cast<const int4*>(w.adj + j0 + i);
+              const int4 b4 = *reinterpret_cast<const int4*>(adj + j0 + i);
               r[i] += (uint32_t)b4.x;
               r[i + 1] += (uint32_t)b4.y;
               r[i + 2] += (uint32_t)b4.z;
               r[i + 3] += (uint32_t)b4.w;
             }
+          }
+          if (keep_last) {  // this row, less the bias, is the next tile's reference
+#pragma unroll
+            for (int i = 0; i < 32; i += 4)
+              if (i < cnt)
+                *reinterpret_cast<int4*>(adj_next + j0 + i) =
+                    make_int4((int)(r[i] - kT5Bias), (int)(r[i + 1] - kT5Bias), (int)(r[i + 2] - kT5Bias),
+                              (int)(r[i + 3] - kT5Bias));
           }
         } else {
 #pragma unroll
@@ -662,6 +687,17 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
       buf ^= 1;
     }
     ew_sync();
+    if (tid == 0) {  // the chain of references: the next tile may start from this one's last candidate
+      if (single && nrows == (uint32_t)kT5M) {
+        w.scal[3] = g_first + kT5M;
+        w.scal[0] = t + (kT5M - 1);
+        w.scal[1] = w.scal[4];
+        w.iscal[2] = w.iscal[6];
+        w.iscal[1] ^= 1;
+      } else {
+        w.scal[3] = ~0ull;
+      }
+    }
   }
   if (!ok) {
     atomicOr(&a.st->error, kErrTimeout);
@@ -693,6 +729,7 @@ __global__ void __launch_bounds__(kT5Threads, 2) k_tc5_expand(Tc5Args a, const _
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *w.cp = -1;
+    w.scal[3] = ~0ull;
     w.iscal[5] = 0;
   }
   if (warp == 0) {
