@@ -5,10 +5,11 @@
 //
 // Exactness.  Entries of M_Pi are integers with |M| <= 16 and the left
 // operand holds 0, +1 or -1, all exact in e4m3.  Every product sum D is an
-// integer with |D| <= 2 * 16 * 1024 < 2^15.  The accumulator starts at
-// 1.5 * 2^23, so every partial sum stays in [2^23, 2^24), where fp32 holds
-// every integer: the result's bits are 0x4B400000 + D exactly, and the row is
-// C' = base + D in int32, one integer add per entry.
+// integer with |D| <= 2 * 16 * 1024 < 2^15, and so is every partial sum, which
+// fp32 holds exactly whatever order the tensor core adds in.  The epilogue
+// adds 1.5 * 2^23 in fp32 (exact: the sum stays in [2^23, 2^24), where fp32
+// holds every integer), so the bits are 0x4B400000 + D, and the row is
+// C' = (base - 0x4B400000) + bits in int32: two full-rate adds per entry.
 //
 // Work unit: a tile of 128 consecutive candidates (the MMA's M, one TMEM lane
 // and one epilogue thread per candidate).  Two forms of the left operand:
@@ -311,9 +312,14 @@ __device__ void t5_load_parent(const Tc5Args& a, const Tc5Smem& w, int64_t p, ui
     if (!mask) continue;
     const int r = __ldg(s.first_rule + n) + __ffs(mask) - 1;
     const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
-    for (int e = e0; e < e1; ++e) {
-      const int2 cv = __ldg(s.csr + e);
-      atomicAdd(ref + cv.x, cv.y);
+    for (int e = e0; e < e1; e += 8) {  // eight loads in flight, then their adds
+      int2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e + u < e1) v[u] = __ldg(s.csr + e + u);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (e + u < e1) atomicAdd(ref + v[u].x, v[u].y);
     }
   }
   for (int e = tid; e < ref_len; e += kT5M) {
@@ -426,7 +432,7 @@ __device__ void t5_control(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b,
           fence_after_sync();
           const uint64_t ad = smem_desc(saddr(w.A + (size_t)k * kT5ABytes), 128, 256);
           const uint64_t bd = smem_desc(saddr(w.B + (size_t)sI * ncmax * kT5K), 128, 256);
-          mma_f8(d, ad, bd, id, 1u);  // accumulates onto the bias
+          mma_f8(d, ad, bd, id, (gi > 0 || k > 0) ? 1u : 0u);  // the chunk's first product overwrites
           mma_commit(b.b_empty + 8 * sI);
         }
         stage = (st0 + gn) % kT5Stages;
@@ -620,12 +626,20 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
       for (int c = 0; c < nc_cols; c += 32) {
         uint32_t r[32];
         const bool two = c + 32 <= nc_cols;
-        if (two) tmem_ld32(acc + (uint32_t)c, r);
-        else tmem_ld16(acc + (uint32_t)c, r);
-        tmem_wait_ld();
+        if (nact == 0) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) r[i] = 0u;
+        } else {
+          if (two) tmem_ld32(acc + (uint32_t)c, r);
+          else tmem_ld16(acc + (uint32_t)c, r);
+          tmem_wait_ld();
+        }
         const int j0 = c0 + c;
         const int cnt = min(two ? 32 : 16, m - j0);
         if (cnt <= 0) continue;
+        // bits(D + 1.5 * 2^23) = kT5Bias + D exactly (|D| < 2^22)
+#pragma unroll
+        for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(__uint_as_float(r[i]) + 12582912.0f);
         // v = base + D = (base - bias) + bits(bias + D)
         if (single) {
 #pragma unroll
@@ -677,10 +691,7 @@ __device__ void t5_epilogue(const Tc5Args& a, const Tc5Smem& w, const Tc5Bars& b
           }
         }
       }
-      // the buffer back to the bias for its next chunk, then free
-#pragma unroll 1
-      for (int c = 0; c < kT5NC; c += 32) tmem_fill32(acc + (uint32_t)c, kT5Bias);
-      tmem_wait_st();
+      // the buffer is free again
       fence_before_sync();
       __syncwarp();
       if (lane == 0) bar_arrive(b.acc_empty[buf]);
@@ -741,15 +752,7 @@ __global__ void __launch_bounds__(kT5Threads, 2) k_tc5_expand(Tc5Args a, const _
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *w.tmem_slot;
-  if (warp < 4) {  // both accumulator buffers start at the bias
-    const uint32_t lane_tmem = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-    for (int c = 0; c < 2 * kT5NC; c += 32) tmem_fill32(lane_tmem + (uint32_t)c, kT5Bias);
-    tmem_wait_st();
-  }
-  fence_before_sync();
-  __syncthreads();
-  fence_after_sync();
+
   if (warp < 4) {
     t5_epilogue(a, w, b, tmem, a.use_map ? &map : nullptr);
   } else {

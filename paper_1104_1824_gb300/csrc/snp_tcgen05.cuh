@@ -112,6 +112,13 @@ __device__ __forceinline__ void tmem_fill32(uint32_t addr, uint32_t v) {
       : "memory");
 }
 
+// Copies 128 lanes x 256 bits (8 columns) from shared memory (matrix
+// descriptor desc) into TMEM at addr; ordered before the tcgen05.mma the same
+// thread issues after it, and tracked by its tcgen05.commit.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t addr, uint64_t desc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(addr), "l"(desc) : "memory");
+}
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Byte offset of (row, k) in one 128 x 32 block of the left operand.
@@ -147,7 +154,7 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int 
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-constexpr uint32_t kT5Bias = 0x4B400000u;  // bits of 1.5 * 2^23: bits(1.5 * 2^23 + v) = kT5Bias + v for |v| < 2^22
+constexpr uint32_t kT5Bias = 0x4B400000u;  // bits of 1.5 * 2^23: bits(1.5 * 2^23 + v) = kT5Bias + v for integers |v| < 2^22
 
 }  // namespace t5
 }  // namespace snp
