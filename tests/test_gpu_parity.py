@@ -390,6 +390,18 @@ def test_overflow_is_reported(gpu):
     assert s.count() == 3
 
 
+@pytest.mark.parametrize("m,cap", [(64, 2000), (128, 3000), (256, 1500)])
+def test_psi_rows_with_large_counts(gpu, m, cap):
+    """Frontier rows that hold spike counts of 64 or more in some neurons (the
+    direct applicability table stops at 63): such rows leave the fast Psi loop
+    for the general one; with small caps the parent records are built too."""
+    system = snp_synth.random_system(4400 + m, m, (2, 3), (2, 4), (0, 6), "sparse")
+    rng = np.random.default_rng(m)
+    system.c0[:] = np.where(rng.random(m) < 0.2, rng.integers(60, 300, size=m), rng.integers(0, 7, size=m))
+    s, e = explore_both(gpu, system, 3, cap=cap, budget=20 * cap)
+    assert_same(s, e)
+
+
 def test_overflow_bound_against_the_oracle(gpu):
     """The device refuses to expand a configuration from which some column
     could leave int32 in one step (the per-column bound: the sum over neurons
