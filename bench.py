@@ -737,6 +737,7 @@ def main():
     ap.add_argument("--cap", type=int, default=0, help="override the workload's frontier cap (profiling cases)")
     ap.add_argument("--chunk", type=int, default=0, help="override the pass size (profiling cases)")
     ap.add_argument("--autotune", action="store_true", help="batch4096: pick pass size, tile and warps first")
+    ap.add_argument("--systems", type=int, default=0, help="batch4096: override the number of systems (profiling cases)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: arrivals of the stream to run")
     ap.add_argument("--max-active", type=int, default=2048, help="serving: requests on the device at once")
     ap.add_argument("--calibrate", action="store_true", help="serving: submit all at once, report the capacity")
@@ -754,6 +755,8 @@ def main():
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], cap=args.cap)
     if args.chunk > 0:
         WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], chunk=args.chunk)
+    if args.systems > 0 and args.workload == "batch4096":
+        WORKLOADS[args.workload] = dict(WORKLOADS[args.workload], n=args.systems)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
