@@ -318,13 +318,15 @@ def roofline_of(args, system, snp, transition: str, r):
         peak = snp.snp_tc_peak_tops(20000)
         ops = 2.0 * system.R * system.m * r["candidates"]
         achieved = ops / (r["expand_ms"] * 1e-3) / 1e12 if r["expand_ms"] > 0 else None
+        traffic = profiled_traffic(args.workload, "tc_rows")
         return {
             "kernel": "k_tc_digits + k_tc_rows (mma.sync m16n8k32 s8) + k_resolve_rows, per pass",
             "bound": "tensor", "achieved": round(achieved, 2) if achieved else None, "peak": round(peak, 1),
             "peak_kind": "measured mma.sync m16n8k32 s8 rate on this GPU (snp_tc_peak_tops)", "unit": "TOPS",
             "frac": round(achieved / peak, 4) if achieved else None,
             "algorithmic_ops_per_launch": int(ops / nlaunch),
-            "avg_launch_ms": round(r["expand_ms"] / nlaunch, 4), "traffic": None,
+            "avg_launch_ms": round(r["expand_ms"] / nlaunch, 4),
+            "traffic": (int(traffic["bytes_per_candidate"] * r["candidates"] / nlaunch) if traffic else None),
             "expand_share_of_step": round(r["expand_ms"] / ms, 4) if ms > 0 else None,
         }
     peak, peak_kind = measured_peaks()
