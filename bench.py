@@ -267,14 +267,16 @@ def transition_code(snp, name: str) -> int:
 TRANSITION_NAMES = {"sparse": "sparse_i32", "tc": "tc_i8", "f8": "tc_f8"}
 
 
-def time_form(args, system, w, snp, torch, dist, dev, world, local, transition: str, steps: int, warmup: int):
+def time_form(args, system, w, snp, torch, dist, dev, world, local, transition: str, steps: int, warmup: int,
+              packed: bool = False):
     """Times `steps` explorations of the workload in one transition form on a
     side stream (CUDA events around the whole timed region, after `warmup`
-    untimed ones); the handle, and its store, is freed afterwards."""
+    untimed ones); the handle, and its store, is freed afterwards.  packed:
+    the store keeps counts in 1 or 2 bytes where the bound allows."""
     s = snp.System(system)
     stream = torch.cuda.Stream(device=dev)
     kw = dict(cap=w["cap"], budget=w["budget"], stream=stream, chunk=w.get("chunk", 0),
-              transition=transition_code(snp, transition))
+              transition=transition_code(snp, transition), packed=packed)
     for _ in range(warmup):
         s.explore(w["depth"], **kw)
     if world > 1:
@@ -303,12 +305,13 @@ def time_form(args, system, w, snp, torch, dist, dev, world, local, transition: 
     r["per_depth"] = [{"depth": d, "new": x.new, "examined": x.examined, "chunks": x.chunks, "ms": round(x.ms, 4),
                        "new_per_s": round(x.new / (x.ms * 1e-3)) if x.ms > 0 else None}
                       for d, x in enumerate(st) if d > 0]
+    r["row_width"] = s.row_width()
     s.close()
     torch.cuda.synchronize()
     return r
 
 
-def roofline_of(args, system, snp, transition: str, r):
+def roofline_of(args, system, snp, transition: str, r, packed: bool = False):
     """Roofline object of the form's dominant kernel (the
     algorithmic bytes per candidate and per configuration)."""
     ms = r["ms"]
@@ -336,7 +339,9 @@ def roofline_of(args, system, snp, transition: str, r):
         traffic = profiled_traffic(args.workload, "tc5")
     else:
         kernel = ("k_expand_wide" if system.m > 128 else "k_expand") + " (decode, C' = C + S.M, hash, probe/compare/claim)"
-        traffic = profiled_traffic(args.workload)
+        if packed:
+            kernel += f", rows of {r['row_width']} byte(s) per count"
+        traffic = profiled_traffic(args.workload, "expand_packed" if packed else "expand")
     return {
         "kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1) if achieved else None, "peak": peak,
         "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
@@ -369,12 +374,13 @@ def bench_ours(args):
     if args.workload == "batch4096":
         return bench_batch(args, w, system, snp, torch, dist, dev, rank, world, local)
     main_form = args.transition or "sparse"
-    r = time_form(args, system, w, snp, torch, dist, dev, world, local, main_form, args.steps, args.warmup)
+    r = time_form(args, system, w, snp, torch, dist, dev, world, local, main_form, args.steps, args.warmup,
+                  packed=args.packed)
     ms_max, (total_all, launches_all) = aggregate_ranks(r["ms"], [r["total_new"], r["launches"]],
                                                         dist if world > 1 else None, dev)
     total_all, launches_all = int(total_all), int(launches_all)
     value = total_all / (ms_max * 1e-3)
-    roofline = roofline_of(args, system, snp, main_form, r)
+    roofline = roofline_of(args, system, snp, main_form, r, packed=args.packed)
 
     # the metric's comparison: the tensor-core forms against the plain int32 form on the same GPU
     compare = {}
@@ -391,6 +397,20 @@ def bench_ours(args):
                 "roofline": roofline_of(args, system, snp, form, rf), "clocks": rf["clocks"],
                 "gpu_launches": rf["launches"],
             }
+    # packed configurations: the same sparse form with the store's counts in 1 or 2 bytes
+    if args.transition is None and not args.packed and not args.no_compare:
+        rp = time_form(args, system, w, snp, torch, dist, dev, world, local, "sparse", args.steps, args.warmup,
+                       packed=True)
+        msp, (tot_p,) = aggregate_ranks(rp["ms"], [rp["total_new"]], dist if world > 1 else None, dev)
+        vp = tot_p / (msp * 1e-3)
+        compare["sparse_packed"] = {
+            "value": round(vp, 1), "unit": UNIT, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(msp / args.steps, 4), "ratio_to_sparse_i32": round(vp / value, 4),
+            "dtype": {1: "uint8", 2: "uint16", 4: "int32"}[rp["row_width"]] + " store, int32 arithmetic",
+            "row_bytes": rp["row_width"] * system.m, "new_per_step": rp["total_new"] // args.steps,
+            "per_depth": rp["per_depth"], "roofline": roofline_of(args, system, snp, "sparse", rp, packed=True),
+            "clocks": rp["clocks"], "gpu_launches": rp["launches"],
+        }
 
     e2e = None
     if not args.no_e2e:
@@ -412,9 +432,10 @@ def bench_ours(args):
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {w['desc']}", "depth": w["depth"], "frontier_cap": w["cap"],
                        "candidate_budget": w["budget"], "transition": TRANSITION_NAMES[main_form],
+                       "row_bytes": r["row_width"] * system.m,
                        "new_per_step": nps,
-                       "l2": f"inputs larger than L2 ({nps * system.m * 4 / 1e9:.1f} GB of configurations written "
-                             "per step)",
+                       "l2": f"inputs larger than L2 ({nps * system.m * r['row_width'] / 1e9:.1f} GB of configurations "
+                             "written per step)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "per_depth": r["per_depth"],
             "roofline": roofline,
@@ -747,7 +768,9 @@ def main():
                     help="step (c): sparse int32 gather, the exact int8 tensor-core product (mma.sync), or the "
                          "exact fp8 product on tcgen05 (default: sparse; on dense1024 the two tensor-core forms are "
                          "also timed and reported under 'compare')")
-    ap.add_argument("--no-compare", action="store_true", help="dense1024: time the sparse form only")
+    ap.add_argument("--no-compare", action="store_true", help="time the line's form only")
+    ap.add_argument("--packed", action="store_true",
+                    help="the line's form with a packed store (counts in 1 or 2 bytes where the bound allows)")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = DEFAULT_STEPS.get(args.workload, 5)

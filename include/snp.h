@@ -142,6 +142,22 @@ typedef struct {
  *                    none); once it is nonzero the passes in flight finish,
  *                    the exploration is discarded and the call returns
  *                    SNP_E_CANCELLED.
+ *  packed            1: keep the configurations in the store with the
+ *                    narrowest of 1, 2 or 4 bytes per spike count that holds
+ *                    every count the exploration can reach (packed
+ *                    configurations; exactness unchanged).  The bound: counts
+ *                    never go below 0 and one step adds at most gain[j] =
+ *                    sum over neurons of their largest entry in column j of
+ *                    M_Pi, so no count exceeds max(C0[j]) + depth * gain[j]
+ *                    (for a resumed exploration: the checkpoint's largest
+ *                    count + the depths still to run times the largest
+ *                    gain).  uint8 needs m % 16 == 0 and uint16 m % 8 == 0
+ *                    (rows of whole 16-byte pieces); the tensor-core forms
+ *                    keep int32, and so do snp_explore_batch, the server and
+ *                    snp_explore_static, which read no other value of this
+ *                    field.  snp_row_width reports the width used;
+ *                    snp_reachable returns int32 rows whatever it is.
+ *                    0: int32 (the default).
  *  reserved          must be 0.
  * Candidate order ("canonical order"): parents in discovery order; for each,
  * its valid spiking vectors in mixed-radix order with neuron 0's choice most
@@ -161,7 +177,8 @@ typedef struct {
   int32_t warps;
   int32_t timeout_ms;
   const volatile int32_t* cancel;
-  int64_t reserved;
+  int32_t packed;
+  int32_t reserved;
 } snp_explore_opts;
 
 /* Statistics of one BFS depth (index 0 is the root level). */
@@ -239,7 +256,9 @@ int snp_explore_resume(snp_handle h, const int32_t* rows, int64_t n, const snp_d
 
 /* Every configuration found by the last snp_explore, C0 first, in discovery
  * order (depth by depth, each depth in canonical candidate order), into
- * out[capacity * m] (host or device).  *n receives the count.  With
+ * out[capacity * m] (host or device): the set the paper's simulator collects
+ * as allGenCk (Section 5; Algorithm 2 adds every new C_k to it), here as
+ * int32 rows whatever the store's width.  *n receives the count.  With
  * capacity < *n nothing is written and SNP_E_BUFFER is returned (out may then
  * be NULL).  per_depth_new (host, may be NULL) receives depth_reached + 1
  * counts, index 0 being C0's level.  Errors: SNP_E_STATE, SNP_E_BUFFER, SNP_E_CUDA. */
@@ -253,8 +272,18 @@ int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int6
 int snp_parents(snp_handle h, int64_t* parent, uint64_t* index, int64_t capacity, int64_t* n);
 
 /* Statistics of depth d (0 <= d <= depth_reached + 1) of the last
- * exploration.  Errors: SNP_E_STATE, SNP_E_INVALID. */
+ * exploration: the frontier expanded at that depth of the computation tree
+ * (Section 4.1: each level's configurations are the parents of the next), the
+ * sum of Psi over it (Eq. psi), the candidates examined and the new
+ * configurations kept; a depth with none new is where the search stopped by
+ * the second stopping criterion (Section 4.1).  Errors: SNP_E_STATE,
+ * SNP_E_INVALID. */
 int snp_depth_stats(snp_handle h, int32_t d, snp_depth_info* out);
+
+/* Bytes per spike count of the store of the last exploration: 1 (uint8),
+ * 2 (uint16) or 4 (int32) -- see snp_explore_opts.packed.  Errors:
+ * SNP_E_STATE (no exploration), SNP_E_INVALID. */
+int snp_row_width(snp_handle h, int32_t* bytes_per_count);
 
 /* Breadth-first exploration of n independent systems at once (the batch
  * engine): every system runs exactly what snp_explore would run on it with

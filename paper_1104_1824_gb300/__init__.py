@@ -46,7 +46,8 @@ EXPORTS = ["snp_explore_opts_init", "snp_load_system", "snp_free", "snp_step", "
            "snp_parents", "snp_depth_stats", "snp_last_error", "snp_abi_version", "snp_explore_static",
            "snp_explore_resume", "snp_debug_fail_allocation", "snp_system_info", "snp_debug_hold_root_slot",
            "snp_tc_peak_tops", "snp_explore_batch", "snp_batch_autotune", "snp_server_create",
-           "snp_server_submit", "snp_server_poll", "snp_server_wait", "snp_server_stats", "snp_server_destroy"]
+           "snp_server_submit", "snp_server_poll", "snp_server_wait", "snp_server_stats", "snp_server_destroy",
+           "snp_row_width"]
 
 
 class SnpError(RuntimeError):
@@ -68,7 +69,7 @@ class snp_explore_opts(ctypes.Structure):
                 ("max_expand_value", ctypes.c_int32), ("record_parents", ctypes.c_int32),
                 ("chunk", ctypes.c_int64), ("stream", ctypes.c_void_p), ("kernel_timing", ctypes.c_int32),
                 ("tile", ctypes.c_int32), ("warps", ctypes.c_int32), ("timeout_ms", ctypes.c_int32),
-                ("cancel", ctypes.c_void_p), ("reserved", ctypes.c_int64)]
+                ("cancel", ctypes.c_void_p), ("packed", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class snp_depth_info(ctypes.Structure):
@@ -109,6 +110,7 @@ def load_library(path: str = LIB_PATH):
     lib.snp_reachable.argtypes = [vp, vp, i64, ctypes.POINTER(i64), vp]
     lib.snp_parents.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
     lib.snp_depth_stats.argtypes = [vp, i32, ctypes.POINTER(snp_depth_info)]
+    lib.snp_row_width.argtypes = [vp, ctypes.POINTER(i32)]
     lib.snp_explore_static.argtypes = [vp, ctypes.POINTER(snp_explore_opts), vp, i64, ctypes.POINTER(i64),
                                        ctypes.POINTER(i32), vp]
     lib.snp_tc_peak_tops.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -372,6 +374,13 @@ def snp_depth_stats(h, d: int) -> snp_depth_info:
     return info
 
 
+def snp_row_width(h) -> int:
+    """Bytes per spike count of the last exploration's store (1, 2 or 4)."""
+    w = ctypes.c_int32()
+    _check(load_library().snp_row_width(h, ctypes.byref(w)))
+    return int(w.value)
+
+
 # --- convenience wrapper ------------------------------------------------------------------
 
 @dataclass
@@ -420,9 +429,12 @@ class System:
 
     def explore(self, depth: int, cap: int = 0, budget: int = 0, transition: int = SNP_T_SPARSE_I32,
                 max_expand: int = -1, record_parents: bool = False, chunk: int = 0, stream=None,
-                kernel_timing: bool = False, timeout_ms: int = 0, cancel=None) -> int:
-        """cancel: a host int32 array of one element, polled between passes."""
+                kernel_timing: bool = False, timeout_ms: int = 0, cancel=None, packed: bool = False) -> int:
+        """cancel: a host int32 array of one element, polled between passes;
+        packed: store counts in 1 or 2 bytes where the bound allows
+        (row_width() tells which)."""
         o = snp_explore_opts_init()
+        o.packed = 1 if packed else 0
         o.timeout_ms = int(timeout_ms)
         o.cancel = _ptr(cancel) or None
         o.depth = int(depth)
@@ -455,7 +467,7 @@ class System:
         return rows, np.frombuffer(bytes(arr), dtype=np.uint8).copy()
 
     def resume(self, checkpoint, depth: int, cap: int = 0, budget: int = 0, transition: int = SNP_T_SPARSE_I32,
-               max_expand: int = -1, chunk: int = 0, stream=None) -> int:
+               max_expand: int = -1, chunk: int = 0, stream=None, packed: bool = False) -> int:
         """Continues the exploration a checkpoint() was taken from up to `depth`."""
         rows, raw = checkpoint
         raw = np.ascontiguousarray(raw, dtype=np.uint8)
@@ -464,12 +476,17 @@ class System:
         o = snp_explore_opts_init()
         o.depth, o.transition, o.frontier_cap, o.candidate_budget = int(depth), int(transition), int(cap), int(budget)
         o.max_expand_value, o.chunk, o.stream = int(max_expand), int(chunk), _stream_handle(stream)
+        o.packed = 1 if packed else 0
         self.truncated = np.zeros(int(depth) + 1, dtype=np.int32)
         self.depth_reached = snp_explore_resume(self.h, rows, stats, o, self.truncated)
         return self.depth_reached
 
     def count(self) -> int:
         return snp_reachable_count(self.h)
+
+    def row_width(self) -> int:
+        """Bytes per spike count of the last exploration's store (1, 2 or 4)."""
+        return snp_row_width(self.h)
 
     def reachable(self) -> np.ndarray:
         n = self.count()

@@ -165,8 +165,8 @@ int rebuild_table(snp_system* h, uint64_t nbuckets, cudaStream_t st) {
                                                                        kEmpty);
   CK(cudaGetLastError());
   if (h->n_rows > 0) {
-    k_insert_rows<<<grid_for(h->n_rows, kWarpsPerBlock, 152 * 64), kThreads, 0, st>>>(
-        h->dev(), h->d_pool.as<int32_t>(), h->d_perm.as<uint32_t>(), 0, h->n_rows, h->table(), h->d_st.as<ChunkState>());
+    launch_insert_rows(h->dev(), h->d_pool.as<int32_t>(), h->row_w, h->d_perm.as<uint32_t>(), 0, h->n_rows, h->table(),
+                       h->d_st.as<ChunkState>(), grid_for(h->n_rows, kWarpsPerBlock, 152 * 64), st);
     CK(cudaGetLastError());
   }
   return SNP_OK;
@@ -471,7 +471,7 @@ int snp_step(snp_handle h, const int32_t* C, int64_t capacity, int32_t* out, uin
   uint64_t* dpsi = reinterpret_cast<uint64_t*>(h->d_tmp.as<char>() + ((sizeof(int32_t) * m + 15) / 16) * 16);
   CK(cudaMemcpy(dC, c.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice));
   CK(cudaMemset(h->d_st.p, 0, sizeof(ChunkState)));
-  launch_psi(h->dev(), dC, nullptr, 1, -1, dpsi, nullptr, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
+  launch_psi(h->dev(), dC, 4, nullptr, 1, -1, dpsi, nullptr, h->d_st.as<ChunkState>(), nullptr, sm_count(h->device));
   CK(cudaGetLastError());
   uint64_t ps = 0;
   CK(cudaMemcpy(&ps, dpsi, sizeof ps, cudaMemcpyDeviceToHost));
@@ -508,6 +508,21 @@ struct ResumeFrom {
 // Frontier rows whose Psi goes first when the last depth's Psi sum saturated.
 constexpr int64_t kPsiHead = 8192;
 
+// Bytes per spike count of a packed store.  Counts never go below 0 (a rule
+// applies only to at least the spikes it consumes) and one step adds at most
+// gain[j] to column j (at most one rule per neuron fires), so after `depths`
+// more steps no count of column j exceeds cmax[j] + depths * gain[j].  The
+// narrowest of uint8 (m % 16 == 0) and uint16 (m % 8 == 0) that holds every
+// column's bound, else 4 (int32).
+int packed_width(const snp_system* h, const std::vector<int64_t>& cmax, int64_t depths) {
+  long double b = 0.0L;
+  for (int j = 0; j < h->m; ++j)
+    b = std::max(b, (long double)cmax[j] + (long double)depths * (long double)h->gain[j]);
+  if (b <= 255.0L && h->m % 16 == 0) return 1;
+  if (b <= 65535.0L && h->m % 8 == 0) return 2;
+  return 4;
+}
+
 int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached, int32_t* truncated_flags,
                  const ResumeFrom* rs) {
   g_err.clear();
@@ -528,6 +543,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   if (o->transition != SNP_T_SPARSE_I32 && o->transition != SNP_T_TC_I8 && o->transition != SNP_T_TC_F8)
     return fail(SNP_E_INVALID, "unknown transition %d", o->transition);
   if (o->reserved != 0) return fail(SNP_E_INVALID, "opts->reserved must be 0");
+  if (o->packed != 0 && o->packed != 1) return fail(SNP_E_INVALID, "opts->packed = %d: expected 0 or 1", o->packed);
   if (o->transition == SNP_T_TC_I8 && h->max_abs_m > 127)
     return fail(SNP_E_RANGE, "int8 transition refused: |M_Pi| reaches %d > 127", h->max_abs_m);
   if (o->transition == SNP_T_TC_F8 && h->max_abs_m > 16)
@@ -541,6 +557,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   h->batch.reset();
   h->result_pool = nullptr;
   h->result_perm = nullptr;
+  h->result_w = 4;
   const int m = h->m;
   const int nsm = sm_count(h->device);
   const int64_t cap = o->frontier_cap > 0 ? o->frontier_cap : 0;
@@ -570,6 +587,33 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     qmax = std::min<uint64_t>(qmax, 1ull << 20);
     TRY(tc5_prepare(h, qmax));
   }
+  // Packed store: uint8 or uint16 counts where asked for, in the sparse form,
+  // for rows of whole 16-byte pieces, and where the bound on every count the
+  // exploration can reach allows it (packed_width); int32 otherwise.
+  int W = 4;
+  const int32_t* rs_rows = rs ? rs->rows : nullptr;  // a resumed exploration's rows (device copy when packed)
+  if (o->packed && !tc && !tc5 && m % 8 == 0) {
+    std::vector<int64_t> cmax(h->c0.begin(), h->c0.end());
+    int64_t depths = o->depth;
+    if (rs) {  // the checkpoint's largest count, for every column
+      if (!is_device_ptr(rs->rows)) {
+        TRY(h->d_tmp.reserve(sizeof(int32_t) * (size_t)m * rs->n));
+        CK(cudaMemcpyAsync(h->d_tmp.p, rs->rows, sizeof(int32_t) * (size_t)m * rs->n, cudaMemcpyHostToDevice, st));
+        rs_rows = h->d_tmp.as<int32_t>();
+      }
+      TRY(h->d_ctr.reserve(3 * sizeof(unsigned long long)));
+      CK(cudaMemsetAsync(h->d_ctr.p, 0, sizeof(int32_t), st));
+      launch_count_max(rs_rows, (int64_t)m * rs->n, h->d_ctr.as<int32_t>(), st);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(h->pin.u64, h->d_ctr.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      cmax.assign(m, *reinterpret_cast<const int32_t*>(h->pin.u64));
+      depths = o->depth - (rs->nstats - 1);
+    }
+    W = packed_width(h, cmax, depths);
+  }
+  h->row_w = W;
+  h->pool_rows = (int64_t)(h->d_pool.bytes / ((size_t)W * m));  // the store's capacity in rows of this width
   // Pool: exact when capped, growing otherwise.
   int64_t rows_plan = 1 << 12;
   if (cap > 0) {
@@ -600,7 +644,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
         (long double)qmax * (cap > 0 ? (long double)std::max(o->depth, 1) * (tc5 ? 2.0L : 1.0L) : 1.0L);
     const int64_t store_plan = (int64_t)std::min<long double>(2147483632.0L, (long double)rows_plan + extra);
     if (h->pool_rows < store_plan) {
-      TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * store_plan));
+      TRY(h->d_pool.reserve((size_t)W * m * store_plan));
       h->pool_rows = store_plan;
     }
   }
@@ -619,7 +663,12 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   if (rs) {  // the checkpoint's rows become store rows 0 .. n-1, in discovery order
     h->n_rows = rs->n;
     h->n_store = rs->n;
-    CK(cudaMemcpyAsync(h->d_pool.p, rs->rows, sizeof(int32_t) * (size_t)m * rs->n, cudaMemcpyDefault, st));
+    if (W == 4) {
+      CK(cudaMemcpyAsync(h->d_pool.p, rs->rows, sizeof(int32_t) * (size_t)m * rs->n, cudaMemcpyDefault, st));
+    } else {
+      launch_pack_rows(rs_rows, rs->n, m, W, h->d_pool.as<int32_t>(), st);
+      CK(cudaGetLastError());
+    }
     launch_iota_u32(h->d_perm.as<uint32_t>(), rs->n, st);
     CK(cudaGetLastError());
     level_hi = rs->n;
@@ -628,7 +677,18 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   } else {  // root level: C0, store row 0
     h->n_rows = 1;
     h->n_store = 1;
-    CK(cudaMemcpyAsync(h->d_pool.p, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    if (W == 4) {
+      CK(cudaMemcpyAsync(h->d_pool.p, h->c0.data(), sizeof(int32_t) * m, cudaMemcpyHostToDevice, st));
+    } else {  // C0 in the store's width (within range: packed_width bounds C0 too)
+      std::vector<uint8_t>& b = h->c0_packed;
+      b.resize((size_t)W * m);
+      for (int j = 0; j < m; ++j) {
+        const uint16_t v = (uint16_t)h->c0[j];
+        if (W == 1) b[j] = (uint8_t)v;
+        else std::memcpy(&b[2 * (size_t)j], &v, 2);
+      }
+      CK(cudaMemcpyAsync(h->d_pool.p, b.data(), b.size(), cudaMemcpyHostToDevice, st));
+    }
     CK(cudaMemsetAsync(h->d_perm.p, 0, sizeof(uint32_t), st));
   }
   if (o->record_parents) {
@@ -683,7 +743,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
       TRY(h->d_scan_tmp.reserve(scan_temp_bytes(P + 1, 8)));
       h->psi_cap = P + 1;
     }
-    const int32_t* parents = h->d_pool.as<int32_t>();            // the store
+    const int32_t* parents = h->d_pool.as<int32_t>();            // the store (W bytes per count)
     const uint32_t* pperm = h->d_perm.as<uint32_t>() + level_lo;  // its rows of this frontier
     CK(cudaMemsetAsync(h->d_st.p, 0, sizeof(ChunkState), st));
     uint64_t* psi = h->d_psi.as<uint64_t>();
@@ -692,10 +752,10 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     // hold 2^64 - 1 candidates: they go first, and if they do, the rest are
     // not read (no candidate and no statistic depends on them).
     const int64_t P0 = psi_saturated_before && P > 2 * kPsiHead ? kPsiHead : P;
-    launch_psi(h->dev(), parents, pperm, P0, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
+    launch_psi(h->dev(), parents, W, pperm, P0, o->max_expand_value, psi, nullptr, h->d_st.as<ChunkState>(), st, nsm);
     if (P0 < P) {
       launch_psi_head_check(psi, P0, h->d_st.as<ChunkState>(), st);
-      launch_psi(h->dev(), parents, pperm + P0, P - P0, o->max_expand_value, psi + P0, nullptr,
+      launch_psi(h->dev(), parents, W, pperm + P0, P - P0, o->max_expand_value, psi + P0, nullptr,
                  h->d_st.as<ChunkState>(), st, nsm);
       sd.launches += 2;
     }
@@ -712,7 +772,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     // candidates per parent they are worth a second pass over the frontier.
     const bool with_records = !tc && !tc5 && P > 0 && total <= 256ull * (uint64_t)P;
     if (with_records) {
-      launch_psi(h->dev(), parents, pperm, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(),
+      launch_psi(h->dev(), parents, W, pperm, P, o->max_expand_value, psi, h->d_prec.as<ParentRec>(),
                  h->d_st.as<ChunkState>(), st, nsm);
       CK(cudaGetLastError());
       sd.launches += 1;
@@ -763,7 +823,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
         // algorithmic bytes of the expand kernel (include/snp.h, snp_depth_info),
         // over the candidates examined (a pass that reaches the cap examines
         // its candidates up to the last one accepted)
-        const int64_t row = 4ll * m;
+        const int64_t row = (int64_t)W * m;
         const int64_t qx = cs.capped ? (int64_t)cs.last_lid + 1 : (int64_t)f.Q;
         const int64_t nparents = (int64_t)(cs.p_last - cs.p_first + 1);
         sd.expand_bytes += qx * 8 + (qx - (int64_t)acc) * row + (int64_t)acc * (row + 8) + nparents * row;
@@ -825,7 +885,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
           // uncapped: double; capped (the plan was exact up to one pass per depth): a few passes more
           const uint64_t grow = cap > 0 ? store_hi + 2 * qmax : std::max<uint64_t>(2ull * h->pool_rows, store_hi);
           const int64_t want = (int64_t)std::min<uint64_t>(0x7FFFFFF0ull, grow);
-          TRY(h->d_pool.reserve(sizeof(int32_t) * (size_t)m * want, st, true));
+          TRY(h->d_pool.reserve((size_t)W * m * want, st, true));
           h->pool_rows = want;
           parents = h->d_pool.as<int32_t>();
         }
@@ -868,6 +928,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
           a.ctr = h->d_ctr.as<unsigned long long>();
           a.st = h->d_st.as<ChunkState>();
           a.wait_ns = wait_ns;
+          a.w = W;
           if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][0], st));
           if (tc5) {
             Tc5Args t;
@@ -977,6 +1038,7 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   h->explored = true;
   h->result_pool = h->d_pool.as<int32_t>();
   h->result_perm = h->d_perm.as<uint32_t>();
+  h->result_w = W;
   h->have_parents = o->record_parents != 0;
   if (depth_reached) *depth_reached = h->depth_reached;
   if (truncated_flags)
@@ -1010,7 +1072,7 @@ int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int6
   if (!out) return fail(SNP_E_INVALID, "out is NULL");
   CK(cudaSetDevice(h->device));
   const size_t bytes = sizeof(int32_t) * (size_t)h->m * h->n_rows;
-  if (!h->result_perm) {
+  if (!h->result_perm && h->result_w == 4) {
     CK(cudaMemcpy(out, h->result_pool, bytes, cudaMemcpyDefault));
     return SNP_OK;
   }
@@ -1021,10 +1083,18 @@ int snp_reachable(snp_handle h, int32_t* out, int64_t capacity, int64_t* n, int6
     TRY(h->d_tmp.reserve(bytes));
     dst = h->d_tmp.as<int32_t>();
   }
-  launch_gather_rows(h->result_pool, h->result_perm, h->n_rows, h->m, dst, nullptr);
+  launch_gather_rows(h->result_pool, h->result_w, h->result_perm, h->n_rows, h->m, dst, nullptr);
   CK(cudaGetLastError());
   if (dst != out) CK(cudaMemcpy(out, dst, bytes, cudaMemcpyDeviceToHost));
   else CK(cudaDeviceSynchronize());
+  return SNP_OK;
+}
+
+int snp_row_width(snp_handle h, int32_t* bytes_per_count) {
+  g_err.clear();
+  if (!h || !bytes_per_count) return fail(SNP_E_INVALID, "bad arguments");
+  if (!h->explored) return fail(SNP_E_STATE, "no exploration to report");
+  *bytes_per_count = h->result_w;
   return SNP_OK;
 }
 
@@ -1217,8 +1287,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
   auto clear_and_insert = [&](int64_t rows) -> int {
     k_fill_u64<<<grid_for((int64_t)kStaticSlots, 256, nsm * 32), 256, 0, st>>>(L.slots, kStaticSlots, kEmpty);
     CK(cudaGetLastError());
-    k_insert_rows<<<grid_for(rows, kWarpsPerBlock, nsm * 64), kThreads, 0, st>>>(h->dev(), out, nullptr, 0, rows,
-                                                                                  table, L.st);
+    launch_insert_rows(h->dev(), out, 4, nullptr, 0, rows, table, L.st, grid_for(rows, kWarpsPerBlock, nsm * 64), st);
     CK(cudaGetLastError());
     return SNP_OK;
   };
@@ -1236,7 +1305,7 @@ extern "C" int snp_explore_static(snp_handle h, const snp_explore_opts* o, int32
     const int32_t* parents = out + (size_t)level_lo * m;
     CK(cudaMemsetAsync(L.st, 0, sizeof(ChunkState), st));
     CK(cudaMemsetAsync(L.psi + P, 0, sizeof(uint64_t), st));
-    launch_psi(h->dev(), parents, nullptr, P, o->max_expand_value, L.psi, nullptr, L.st, st, nsm);
+    launch_psi(h->dev(), parents, 4, nullptr, P, o->max_expand_value, L.psi, nullptr, L.st, st, nsm);
     CK(cudaGetLastError());
     scan_u64_sat(L.psi, L.off, P + 1, L.scan_tmp, st);
     CK(cudaMemcpyAsync(h->pin.u64, L.off + P, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));

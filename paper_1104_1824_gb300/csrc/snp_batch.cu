@@ -269,6 +269,7 @@ int batch_run(snp_handle* hs, int32_t n, const snp_explore_opts* o, const BatchP
     h->batch = arena;
     h->result_pool = b.pool;
     h->result_perm = nullptr;
+    h->result_w = 4;
     int code = SNP_OK;
     if (b.error & kErrOverflow) code = SNP_E_OVERFLOW;
     else if (b.error & kErrTimeout) code = SNP_E_TIMEOUT;

@@ -47,6 +47,81 @@ __device__ __forceinline__ bool wait_expired(int pass, uint64_t wait_ns, uint64_
   return now - t0 > wait_ns;
 }
 
+// How a configuration row lies in global memory: m spike counts of type T
+// (int32, or in a packed store uint16 / uint8, which the caller has shown wide
+// enough for every count the exploration can reach).  VEC: m % 4 == 0 and the
+// row is a whole number of 16-byte pieces (packed rows always are), so it
+// moves in pieces of PER16 counts.  Rows in shared memory are int32 in every
+// format.
+template <typename TT, bool V>
+struct RowFmt {
+  using T = TT;
+  static constexpr bool VEC = V;
+  static constexpr int W = (int)sizeof(TT);
+  static constexpr int PER16 = 16 / (int)sizeof(TT);
+};
+using RowI32 = RowFmt<int32_t, false>;
+using RowI32V = RowFmt<int32_t, true>;
+using RowU16 = RowFmt<uint16_t, true>;
+using RowU8 = RowFmt<uint8_t, true>;
+
+// Row j of a row array in format RF that the kernels' argument structs hold
+// as int32_t* whatever the format.
+template <class RF>
+__device__ __forceinline__ typename RF::T* row_at(int32_t* base, uint64_t j, int m) {
+  return reinterpret_cast<typename RF::T*>(base) + (size_t)j * m;
+}
+template <class RF>
+__device__ __forceinline__ const typename RF::T* row_at(const int32_t* base, uint64_t j, int m) {
+  return reinterpret_cast<const typename RF::T*>(base) + (size_t)j * m;
+}
+
+// Four counts (each within the row type's range) as the 4 * W bytes of the
+// packed row: one 32-bit word for uint8, two for uint16.
+__device__ __forceinline__ uint32_t pack4_u8(int4 v) {
+  return __byte_perm(__byte_perm(v.x, v.y, 0x0040), __byte_perm(v.z, v.w, 0x0040), 0x5410);
+}
+__device__ __forceinline__ uint2 pack4_u16(int4 v) {
+  return make_uint2(__byte_perm(v.x, v.y, 0x5410), __byte_perm(v.z, v.w, 0x5410));
+}
+__device__ __forceinline__ int4 unpack4_u8(uint32_t w) {
+  return make_int4((int)(w & 0xFFu), (int)((w >> 8) & 0xFFu), (int)((w >> 16) & 0xFFu), (int)(w >> 24));
+}
+__device__ __forceinline__ int4 unpack4_u16(uint2 w) {
+  return make_int4((int)(w.x & 0xFFFFu), (int)(w.x >> 16), (int)(w.y & 0xFFFFu), (int)(w.y >> 16));
+}
+
+// A row's 16-byte piece q unpacked into counts v[0 .. PER16).
+template <class RF>
+__device__ __forceinline__ void unpack_piece(uint4 x, int32_t* v) {
+  if constexpr (RF::W == 1) {
+    const int4 a = unpack4_u8(x.x), b = unpack4_u8(x.y), c = unpack4_u8(x.z), d = unpack4_u8(x.w);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+    v[8] = c.x, v[9] = c.y, v[10] = c.z, v[11] = c.w, v[12] = d.x, v[13] = d.y, v[14] = d.z, v[15] = d.w;
+  } else if constexpr (RF::W == 2) {
+    const int4 a = unpack4_u16(make_uint2(x.x, x.y)), b = unpack4_u16(make_uint2(x.z, x.w));
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  } else {
+    v[0] = (int32_t)x.x, v[1] = (int32_t)x.y, v[2] = (int32_t)x.z, v[3] = (int32_t)x.w;
+  }
+}
+
+// The 16-byte piece holding counts v[0 .. PER16) (v: int32 in shared memory,
+// 16-byte aligned).
+template <class RF>
+__device__ __forceinline__ uint4 pack_piece(const int32_t* v) {
+  const int4* v4 = reinterpret_cast<const int4*>(v);
+  if constexpr (RF::W == 1) {
+    return make_uint4(pack4_u8(v4[0]), pack4_u8(v4[1]), pack4_u8(v4[2]), pack4_u8(v4[3]));
+  } else if constexpr (RF::W == 2) {
+    const uint2 a = pack4_u16(v4[0]), b = pack4_u16(v4[1]);
+    return make_uint4(a.x, a.y, b.x, b.y);
+  } else {
+    const int4 a = v4[0];
+    return make_uint4((uint32_t)a.x, (uint32_t)a.y, (uint32_t)a.z, (uint32_t)a.w);
+  }
+}
+
 struct NeuronInfo;
 struct ApplEntry;
 
@@ -356,8 +431,9 @@ __device__ __forceinline__ void build_child(const DevSys& s, WarpParent& w, uint
   __syncwarp();
 }
 
-// Table key of the configuration in buf (warp-cooperative).
-__device__ __forceinline__ uint64_t fingerprint(const DevSys& s, const int32_t* buf, int lane) {
+// Table key of the configuration in buf (warp-cooperative; counts of type T).
+template <typename T>
+__device__ __forceinline__ uint64_t fingerprint(const DevSys& s, const T* buf, int lane) {
   uint64_t h = 0;
   for (int n = lane; n < s.m; n += 32) h += col_hash(s, n, buf[n]);
   return mix64(warp_sum_u64(h));

@@ -151,8 +151,9 @@ __device__ __forceinline__ void add_row_shared(const DevSys& s, int32_t* row, in
 // significant first), the block (the least significant of them whose choice
 // counts multiply to RL <= B) and, per lane, the mixed-radix place value of
 // the neurons owned by later lanes (neuron 0 most significant).
-__device__ __forceinline__ uint64_t parent_state(const DevSys& s, const int32_t* __restrict__ row, ExpandSmem& w,
-                                                 int B, int lane) {
+template <typename T>
+__device__ __forceinline__ uint64_t parent_state(const DevSys& s, const T* __restrict__ row, ExpandSmem& w, int B,
+                                                 int lane) {
   __syncwarp();
   for (int n = lane; n < s.m; n += 32) w.par[n] = row[n];
   __syncwarp();
@@ -261,9 +262,27 @@ __device__ __forceinline__ void copy_row(const int32_t* src, int32_t* dst, int m
 
 // Full-key compare; branch-free in groups of 8 loads so that the loads of a
 // group are in flight together.
-template <bool VEC>
-__device__ __forceinline__ bool row_equal_lane(const int32_t* row, const int32_t* other, int m) {
-  if (VEC) {
+template <class RF>
+__device__ __forceinline__ bool row_equal_lane(const int32_t* row, const typename RF::T* other, int m) {
+  if constexpr (RF::W < 4) {  // packed: the candidate is packed the same way, piece by piece
+    const uint4* b = reinterpret_cast<const uint4*>(other);
+    const int n16 = m / RF::PER16;
+    for (int j0 = 0; j0 < n16; j0 += 8) {
+      uint4 y[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < n16) y[u] = __ldcg(b + j0 + u);
+      uint32_t diff = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < n16) {
+          const uint4 x = pack_piece<RF>(row + (j0 + u) * RF::PER16);
+          diff |= (x.x ^ y[u].x) | (x.y ^ y[u].y) | (x.z ^ y[u].z) | (x.w ^ y[u].w);
+        }
+      if (diff) return false;
+    }
+    return true;
+  } else if constexpr (RF::VEC) {
     const int4* a = reinterpret_cast<const int4*>(row);
     const int4* b = reinterpret_cast<const int4*>(other);
     const int n4 = m >> 2;
@@ -282,30 +301,34 @@ __device__ __forceinline__ bool row_equal_lane(const int32_t* row, const int32_t
       if (diff) return false;
     }
     return true;
-  }
-  for (int j0 = 0; j0 < m; j0 += 8) {
-    int y[8];
+  } else {
+    for (int j0 = 0; j0 < m; j0 += 8) {
+      int y[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (j0 + u < m) y[u] = __ldcg(other + j0 + u);
-    int diff = 0;
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < m) y[u] = __ldcg(other + j0 + u);
+      int diff = 0;
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (j0 + u < m) diff |= row[j0 + u] ^ y[u];
-    if (diff) return false;
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < m) diff |= row[j0 + u] ^ y[u];
+      if (diff) return false;
+    }
+    return true;
   }
-  return true;
 }
 
-template <bool VEC>
-__device__ __forceinline__ void stage_row_lane(const int32_t* row, int32_t* dst, int m) {
-  if (VEC) {
+template <class RF>
+__device__ __forceinline__ void stage_row_lane(const int32_t* row, typename RF::T* dst, int m) {
+  if constexpr (RF::W < 4) {
+    uint4* b = reinterpret_cast<uint4*>(dst);
+    for (int j = 0; j < m / RF::PER16; ++j) __stcg(b + j, pack_piece<RF>(row + j * RF::PER16));
+  } else if constexpr (RF::VEC) {
     const int4* a = reinterpret_cast<const int4*>(row);
     int4* b = reinterpret_cast<int4*>(dst);
     for (int j = 0; j < (m >> 2); ++j) __stcg(b + j, a[j]);
-    return;
+  } else {
+    for (int j = 0; j < m; ++j) __stcg(dst + j, row[j]);
   }
-  for (int j = 0; j < m; ++j) __stcg(dst + j, row[j]);
 }
 
 // Step (d) for one candidate, by one lane, without waiting on any other lane:
@@ -314,11 +337,12 @@ __device__ __forceinline__ void stage_row_lane(const int32_t* row, int32_t* dst,
 constexpr int kRetry = 0, kDone = 1, kOwner = 2;
 
 // Frontier row p of the chunk (through the store's row map when there is one).
-__device__ __forceinline__ const int32_t* parent_row(const ClaimArgs& a, int64_t p) {
-  return a.parents + (size_t)(a.pperm ? __ldg(a.pperm + p) : (uint64_t)p) * a.sys.m;
+template <class RF>
+__device__ __forceinline__ const typename RF::T* parent_row(const ClaimArgs& a, int64_t p) {
+  return row_at<RF>(a.parents, a.pperm ? __ldg(a.pperm + p) : (uint64_t)p, a.sys.m);
 }
 
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ int resolve_lane(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                             unsigned long long*& owned) {
   // A bucket fills as a prefix (a slot is claimed only when every earlier
@@ -349,15 +373,15 @@ __device__ __forceinline__ int resolve_lane(const ClaimArgs& a, const int32_t* r
       const unsigned long long x = __ldcg(bs + j);
       const uint32_t rf = (uint32_t)x;
       if (rf == kRowReserved) return kRetry;  // published soon: try again later
-      const int32_t* other;
+      const typename RF::T* other;
       if (rf & kPending) {
         (void)ld_acquire(bs + j);  // orders the reads of the owner's row and records after the publish
         const uint32_t o = rf & ~kPending;
-        other = a.store_ctr ? a.pool + (size_t)__ldcg(a.sidx_of + o) * m : a.staging + (size_t)o * m;
+        other = a.store_ctr ? row_at<RF>(a.pool, __ldcg(a.sidx_of + o), m) : row_at<RF>(a.staging, o, m);
       } else {
-        other = a.pool + (size_t)rf * m;
+        other = row_at<RF>(a.pool, rf, m);
       }
-      if (row_equal_lane<VEC>(row, other, m)) {
+      if (row_equal_lane<RF>(row, other, m)) {
         if (rf & kPending) atomicMin(a.gmin + (rf & ~kPending), lid);
         return kDone;
       }
@@ -379,7 +403,7 @@ __device__ __forceinline__ int resolve_lane(const ClaimArgs& a, const int32_t* r
 
 // The owner's work: its row to staging row lid, or in store mode to store
 // row sidx (recorded in sidx_of), the claim records, then the publish.
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ void finish_owner(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                              unsigned long long* owned, uint64_t sidx) {
   const int m = a.sys.m;
@@ -388,10 +412,10 @@ __device__ __forceinline__ void finish_owner(const ClaimArgs& a, const int32_t* 
       atomicOr(&a.st->error, kErrStaging);
       return;
     }
-    stage_row_lane<VEC>(row, a.pool + (size_t)sidx * m, m);
+    stage_row_lane<RF>(row, row_at<RF>(a.pool, sidx, m), m);
     a.sidx_of[lid] = (uint32_t)sidx;
   } else {
-    stage_row_lane<VEC>(row, a.staging + (size_t)lid * m, m);
+    stage_row_lane<RF>(row, row_at<RF>(a.staging, lid, m), m);
   }
   a.gmin[lid] = lid;
   a.slot_of[lid] = (uint32_t)(owned - a.table.slots);
@@ -419,14 +443,14 @@ __device__ __forceinline__ void finish_owner_inplace(const ClaimArgs& a, uint64_
 // publish before anyone looks again.  KIND separates the out-of-line copies
 // of the single-system kernel (0) and the batch kernel (1), whose register
 // budgets differ.
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                                   bool todo) {
   const int lane = threadIdx.x & 31;
   uint64_t t0 = 0;
   for (int pass = 0;; ++pass) {
     unsigned long long* owned = nullptr;
-    const int status = todo ? resolve_lane<VEC>(a, row, key, lid, owned) : kDone;
+    const int status = todo ? resolve_lane<RF>(a, row, key, lid, owned) : kDone;
     uint64_t sidx = 0;
     if (a.store_ctr) {  // the warp's owners take consecutive store rows with one atomic
       const uint32_t ob = __ballot_sync(0xffffffffu, status == kOwner);
@@ -437,7 +461,7 @@ __device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int3
         sidx = __shfl_sync(0xffffffffu, base, leader) + __popc(ob & ((1u << lane) - 1u));
       }
     }
-    if (status == kOwner) finish_owner<VEC>(a, row, key, lid, owned, sidx);
+    if (status == kOwner) finish_owner<RF>(a, row, key, lid, owned, sidx);
     todo = status == kRetry;
     if (__all_sync(0xffffffffu, !todo)) break;
     if (wait_expired(pass, a.wait_ns, t0)) {
@@ -449,19 +473,19 @@ __device__ __forceinline__ void resolve_warp_body(const ClaimArgs& a, const int3
   __syncwarp();
 }
 
-template <bool VEC>
+template <class RF>
 __device__ __noinline__ void resolve_warp_call(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                                bool todo) {
-  resolve_warp_body<VEC>(a, row, key, lid, todo);
+  resolve_warp_body<RF>(a, row, key, lid, todo);
 }
 
-template <bool VEC, int KIND>
+template <class RF, int KIND>
 __device__ __forceinline__ void resolve_warp(const ClaimArgs& a, const int32_t* row, uint64_t key, uint32_t lid,
                                              bool todo) {
   if constexpr (KIND == 0)
-    resolve_warp_call<VEC>(a, row, key, lid, todo);
+    resolve_warp_call<RF>(a, row, key, lid, todo);
   else
-    resolve_warp_body<VEC>(a, row, key, lid, todo);
+    resolve_warp_body<RF>(a, row, key, lid, todo);
 }
 
 // Mixed-radix digit of a neuron with `radix` choices; q moves to the next
@@ -478,21 +502,43 @@ __device__ __forceinline__ uint32_t next_digit(uint64_t& q, uint32_t radix) {
   return d;
 }
 
+// Four counts of a row in global memory, from count 4 * j on (VEC rows).
+template <class RF>
+__device__ __forceinline__ int4 load4(const typename RF::T* row, int j) {
+  if constexpr (RF::W == 1)
+    return unpack4_u8(reinterpret_cast<const uint32_t*>(row)[j]);
+  else if constexpr (RF::W == 2)
+    return unpack4_u16(reinterpret_cast<const uint2*>(row)[j]);
+  else
+    return reinterpret_cast<const int4*>(row)[j];
+}
+
 // Calls f(n, x) for n = m - 1 down to 0 with x = row[n].
-template <bool VEC, typename F>
-__device__ __forceinline__ void for_each_neuron_desc(const int32_t* row, int m, F&& f) {
-  if (VEC) {
-    const int4* r4 = reinterpret_cast<const int4*>(row);
+template <class RF, typename F>
+__device__ __forceinline__ void for_each_neuron_desc(const typename RF::T* row, int m, F&& f) {
+  if constexpr (RF::VEC) {
     for (int n4 = (m >> 2) - 1; n4 >= 0; --n4) {
-      const int4 v = r4[n4];
+      const int4 v = load4<RF>(row, n4);
       f(4 * n4 + 3, v.w);
       f(4 * n4 + 2, v.z);
       f(4 * n4 + 1, v.y);
       f(4 * n4, v.x);
     }
-    return;
+  } else {
+    for (int n = m - 1; n >= 0; --n) f(n, (int32_t)row[n]);
   }
-  for (int n = m - 1; n >= 0; --n) f(n, row[n]);
+}
+
+// dst[0, m) = the counts of a row in global memory (one lane; dst int32 in
+// shared memory, 16-byte aligned for VEC rows).
+template <class RF>
+__device__ __forceinline__ void load_row(const typename RF::T* src, int32_t* dst, int m) {
+  if constexpr (RF::VEC) {
+    int4* b = reinterpret_cast<int4*>(dst);
+    for (int j = 0; j < (m >> 2); ++j) b[j] = load4<RF>(src, j);
+  } else {
+    for (int j = 0; j < m; ++j) dst[j] = src[j];
+  }
 }
 
 // One lane's candidate in a batch that crosses parents.
@@ -512,7 +558,7 @@ struct FlatLane {
 // row and the applicability table.  keep = the candidate picks no rule that
 // repeats an earlier applicable rule's row.  Returns nf, which shrinks when
 // parents without candidates push a parent beyond the 32 examined.
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int nf, int64_t p, uint64_t p_lo,
                                            int lane, FlatLane& f, bool& keep) {
   const DevSys& s = a.sys;
@@ -557,7 +603,7 @@ __device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int n
     f.h = h;
   } else {
     uint64_t h = 0;
-    for_each_neuron_desc<VEC>(parent_row(a, f.pc), s.m, [&](int n, int32_t x) {
+    for_each_neuron_desc<RF>(parent_row<RF>(a, f.pc), s.m, [&](int n, int32_t x) {
       h += col_hash(s, n, x);
       const uint64_t am = appl(s, n, x);
       const uint32_t mask = (uint32_t)am;
@@ -574,13 +620,13 @@ __device__ __forceinline__ int flat_decode(const ClaimArgs& a, uint64_t g, int n
 
 // Step (c) for a candidate of a crossing batch: C' = C + the chosen rules'
 // rows, built in a tile row (one lane).
-template <bool VEC, int KIND>
+template <class RF, int KIND>
 __device__ __forceinline__ void flat_build(const ClaimArgs& a, int64_t pc, uint64_t t, int32_t* trow) {
   const DevSys& s = a.sys;
-  const int32_t* prow = parent_row(a, pc);
-  copy_row<VEC>(prow, trow, s.m);
+  const typename RF::T* prow = parent_row<RF>(a, pc);
+  load_row<RF>(prow, trow, s.m);
   uint64_t q = t;
-  for_each_neuron_desc<VEC>(prow, s.m, [&](int n, int32_t x) {
+  for_each_neuron_desc<RF>(prow, s.m, [&](int n, int32_t x) {
     const uint32_t mask = (uint32_t)appl(s, n, x);
     if (!mask) return;
     const int kb = nth_set_bit(mask, (int)next_digit(q, __popc(mask)));
@@ -755,10 +801,10 @@ __device__ __forceinline__ void build_low_table(const DevSys& s, ExpandSmem& w, 
 // row: each lane decodes the digits of its own ceil(m / 32) neurons, whose
 // place value is the product of the choice counts of the later lanes' neurons
 // (last neuron least significant), and adds its chosen rules' rows.
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ void build_flat_row(const ClaimArgs& a, int32_t* row, int64_t pc, uint64_t t, int lane) {
   const DevSys& s = a.sys;
-  const int32_t* prow = parent_row(a, pc);
+  const typename RF::T* prow = parent_row<RF>(a, pc);
   __syncwarp();
   for (int n = lane; n < s.m; n += 32) row[n] = prow[n];
   const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
@@ -787,10 +833,21 @@ __device__ __forceinline__ void build_flat_row(const ClaimArgs& a, int32_t* row,
 }
 
 // Full-key compare of the scratch row with a stored row, by the whole warp.
-template <bool VEC>
-__device__ __forceinline__ bool warp_rows_equal(const int32_t* row, const int32_t* other, int m, int lane) {
+template <class RF>
+__device__ __forceinline__ bool warp_rows_equal(const int32_t* row, const typename RF::T* other, int m, int lane) {
   int diff = 0;
-  if (VEC) {
+  if constexpr (RF::W == 1) {  // lane j: counts 4j .. 4j + 3 (conflict-free 16-byte reads of the scratch row)
+    const int4* a = reinterpret_cast<const int4*>(row);
+    const uint32_t* b = reinterpret_cast<const uint32_t*>(other);
+    for (int j = lane; j < (m >> 2); j += 32) diff |= (int)(pack4_u8(a[j]) ^ __ldcg(b + j));
+  } else if constexpr (RF::W == 2) {
+    const int4* a = reinterpret_cast<const int4*>(row);
+    const uint2* b = reinterpret_cast<const uint2*>(other);
+    for (int j = lane; j < (m >> 2); j += 32) {
+      const uint2 x = pack4_u16(a[j]), y = __ldcg(b + j);
+      diff |= (int)((x.x ^ y.x) | (x.y ^ y.y));
+    }
+  } else if constexpr (RF::VEC) {
     const int4* a = reinterpret_cast<const int4*>(row);
     const int4* b = reinterpret_cast<const int4*>(other);
     for (int j = lane; j < (m >> 2); j += 32) {
@@ -804,9 +861,19 @@ __device__ __forceinline__ bool warp_rows_equal(const int32_t* row, const int32_
 }
 
 // The scratch row to global memory, by the whole warp (coalesced).
-template <bool VEC>
-__device__ __forceinline__ void warp_store_row(const int32_t* row, int32_t* dst, int m, int lane) {
-  if (VEC) {
+template <class RF>
+__device__ __forceinline__ void warp_store_row(const int32_t* row, typename RF::T* dst, int m, int lane) {
+  if constexpr (RF::W == 1) {
+    const int4* a = reinterpret_cast<const int4*>(row);
+    uint32_t* b = reinterpret_cast<uint32_t*>(dst);
+#pragma unroll 4
+    for (int j = lane; j < (m >> 2); j += 32) __stcg(b + j, pack4_u8(a[j]));
+  } else if constexpr (RF::W == 2) {
+    const int4* a = reinterpret_cast<const int4*>(row);
+    uint2* b = reinterpret_cast<uint2*>(dst);
+#pragma unroll 4
+    for (int j = lane; j < (m >> 2); j += 32) __stcg(b + j, pack4_u16(a[j]));
+  } else if constexpr (RF::VEC) {
     const int4* a = reinterpret_cast<const int4*>(row);
     int4* b = reinterpret_cast<int4*>(dst);
 #pragma unroll 4
@@ -826,7 +893,7 @@ constexpr int kProbe = 3, kCompare = 4;
 // lane waits inside a pass: a lane that meets a reserved slot with its
 // fingerprint starts over in a later pass, and owners publish before the pass
 // ends.
-template <bool VEC, typename Build>
+template <class RF, typename Build>
 __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* scratch, uint64_t key, uint32_t lid,
                                                   bool todo, int lane, Build&& build) {
   const int m = a.sys.m;
@@ -837,7 +904,7 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
   uint32_t match = 0, empty = 0;
   bool loaded = false;
   uint32_t orf = 0;
-  const int32_t* other = nullptr;
+  const typename RF::T* other = nullptr;
   unsigned long long* owned = nullptr;
   uint64_t t0 = 0;
   for (int pass = 0;; ++pass) {
@@ -882,9 +949,9 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
           if (orf & kPending) {
             (void)ld_acquire(bs + j);
             const uint32_t o = orf & ~kPending;
-            other = a.store_ctr ? a.pool + (size_t)__ldcg(a.sidx_of + o) * m : a.staging + (size_t)o * m;
+            other = a.store_ctr ? row_at<RF>(a.pool, __ldcg(a.sidx_of + o), m) : row_at<RF>(a.staging, o, m);
           } else {
-            other = a.pool + (size_t)orf * m;
+            other = row_at<RF>(a.pool, orf, m);
           }
           st = kCompare;
           break;
@@ -906,10 +973,10 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
       // compares, one lane's row at a time
       for (uint32_t cm = __ballot_sync(0xffffffffu, st == kCompare); cm; cm &= cm - 1) {
         const int L = __ffs(cm) - 1;
-        const int32_t* o = reinterpret_cast<const int32_t*>(
+        const typename RF::T* o = reinterpret_cast<const typename RF::T*>(
             __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(other), L));
         build(L);
-        const bool eq = warp_rows_equal<VEC>(scratch, o, m, lane);
+        const bool eq = warp_rows_equal<RF>(scratch, o, m, lane);
         if (lane == L) {
           if (eq) {
             if (orf & kPending) atomicMin(a.gmin + (orf & ~kPending), lid);
@@ -936,8 +1003,8 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
           const uint32_t ll = __shfl_sync(0xffffffffu, lid, L);
           if (a.store_ctr && sl >= a.store_cap) continue;  // reported by lane L below
           build(L);
-          warp_store_row<VEC>(scratch, a.store_ctr ? a.pool + (size_t)sl * m : a.staging + (size_t)ll * m, m,
-                              lane);
+          warp_store_row<RF>(scratch, a.store_ctr ? row_at<RF>(a.pool, sl, m) : row_at<RF>(a.staging, ll, m), m,
+                             lane);
         }
         __threadfence();
         __syncwarp();
@@ -972,17 +1039,17 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
 }
 
 // Resolves the queued crossing-batch candidates in the wide mode.
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ void flush_queue_wide(const ClaimArgs& a, ExpandSmem& w, int fill, int lane) {
   const bool mine = lane < fill;
-  resolve_warp_wide<VEC>(a, w.tile, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine, lane,
-                         [&](int L) { build_flat_row<VEC>(a, w.tile, w.dpc[L], w.dt[L], lane); });
+  resolve_warp_wide<RF>(a, w.tile, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine, lane,
+                        [&](int L) { build_flat_row<RF>(a, w.tile, w.dpc[L], w.dt[L], lane); });
 }
 
 // Block mode in the wide mode: lane k < RL owns candidate k of each block as
 // in block_run, but keeps only its hash; rows are built on demand from the
 // block base, to which the odometer applies its swaps directly.
-template <bool VEC>
+template <class RF>
 __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSmem& w, int64_t p, uint64_t p_lo,
                                                    uint64_t p_hi, uint64_t l, uint64_t lb, int64_t& cached_p,
                                                    uint64_t& after, int lane) {
@@ -990,7 +1057,7 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   const uint64_t g = a.g0 + l;
   const uint64_t gend = min(p_hi, a.g0 + lb);
   if (p != cached_p) {
-    after = parent_state(s, parent_row(a, p), w, kWideB, lane);
+    after = parent_state(s, parent_row<RF>(a, p), w, kWideB, lane);
     build_low_table(s, w, lane);
     cached_p = p;
   }
@@ -1018,8 +1085,8 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   for (;;) {
     const uint64_t c = gb + lane;
     const bool todo = lane < RL && c >= g && c < gend && !redk && w.hdr[kNred] == 0;
-    resolve_warp_wide<VEC>(a, w.tile, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo, lane,
-                           [&](int L) { build_block_row<VEC>(s, w, L, nlow, lane); });
+    resolve_warp_wide<RF>(a, w.tile, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo, lane,
+                          [&](int L) { build_block_row<RF::VEC>(s, w, L, nlow, lane); });
     gb += (uint64_t)RL;
     if (gb >= gend) break;
     // next block: the odometer, every lane following the same digits
@@ -1048,17 +1115,17 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
 }
 
 // Resolves the queued rows of crossing batches (building them first).
-template <bool VEC, int KIND>
+template <class RF, int KIND>
 __device__ __forceinline__ void flush_queue(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
   const bool mine = lane < fill;
-  if (mine && w.dpc[lane] >= 0) flat_build<VEC, KIND>(a, w.dpc[lane], w.dt[lane], w.tile + lane * ts);
+  if (mine && w.dpc[lane] >= 0) flat_build<RF, KIND>(a, w.dpc[lane], w.dt[lane], w.tile + lane * ts);
   __syncwarp();
-  resolve_warp<VEC, KIND>(a, w.tile + lane * ts, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine);
+  resolve_warp<RF, KIND>(a, w.tile + lane * ts, mine ? w.keys[lane] : 0ull, mine ? w.lids[lane] : 0u, mine);
 }
 
 // Block mode for parent p from candidate a.g0 + l to the end of the parent or
 // of the task; returns the new l.
-template <bool VEC, int KIND>
+template <class RF, int KIND>
 __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w, int B, int ts, int64_t p,
                                               uint64_t p_lo, uint64_t p_hi, uint64_t l, uint64_t lb,
                                               int64_t& cached_p, uint64_t& after, int lane) {
@@ -1067,7 +1134,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   const uint64_t g = a.g0 + l;
   const uint64_t gend = min(p_hi, a.g0 + lb);
   if (p != cached_p) {  // the warp's shared memory still holds the state of cached_p
-    after = parent_state(s, parent_row(a, p), w, B, lane);
+    after = parent_state(s, parent_row<RF>(a, p), w, B, lane);
     cached_p = p;
   }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
@@ -1078,7 +1145,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   uint64_t hk = 0;
   bool redk = true;
   if (lane < RL) {
-    copy_row<VEC>(w.buf, row, m);
+    copy_row<RF::VEC>(w.buf, row, m);
     redk = false;
     uint32_t q = (uint32_t)lane;
     for (int i = 0; i < nlow; ++i) {
@@ -1098,7 +1165,7 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   for (;;) {
     const uint64_t c = gb + lane;
     const bool todo = lane < RL && c >= g && c < gend && !redk && w.hdr[kNred] == 0;
-    resolve_warp<VEC, KIND>(a, row, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo);
+    resolve_warp<RF, KIND>(a, row, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo);
     gb += (uint64_t)RL;
     if (gb >= gend) break;
     // next block: the high digits move on by one (odometer, least significant first)
@@ -1133,18 +1200,18 @@ __device__ __forceinline__ uint64_t block_run(const ClaimArgs& a, ExpandSmem& w,
   return gend - a.g0;
 }
 
-template <bool VEC, int KIND>
+template <class RF, int KIND>
 __device__ __forceinline__ void flush_any(const ClaimArgs& a, ExpandSmem& w, int ts, int fill, int lane) {
   if constexpr (KIND == kWide)
-    flush_queue_wide<VEC>(a, w, fill, lane);
+    flush_queue_wide<RF>(a, w, fill, lane);
   else
-    flush_queue<VEC, KIND>(a, w, ts, fill, lane);
+    flush_queue<RF, KIND>(a, w, ts, fill, lane);
 }
 
 // Steps (b)-(d) for the tasks task0, task0 + tstride, ... of chunk a (a task
 // is a run of a.run consecutive candidates), by one warp: block mode while
 // the parent has 32 or more candidates left, else crossing batches.
-template <bool VEC, int KIND>
+template <class RF, int KIND>
 __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, ExpandSmem& w, uint64_t task0,
                                             uint64_t tstride, int lane) {
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
@@ -1174,14 +1241,14 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       const uint64_t g = a.g0 + l;
       if (done || p_hi - g >= 32) {
         if (fill > 0) {  // the tile is about to be reused, or the task ends
-          flush_any<VEC, KIND>(a, w, ts, fill, lane);
+          flush_any<RF, KIND>(a, w, ts, fill, lane);
           fill = 0;
         }
         if (done) break;
         if constexpr (KIND == kWide)
-          l = block_run_wide<VEC>(a, w, p, p_lo, p_hi, l, lb, cached_p, after, lane);
+          l = block_run_wide<RF>(a, w, p, p_lo, p_hi, l, lb, cached_p, after, lane);
         else
-          l = block_run<VEC, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, cached_p, after, lane);
+          l = block_run<RF, KIND>(a, w, B, ts, p, p_lo, p_hi, l, lb, cached_p, after, lane);
         const uint64_t gn = a.g0 + l;
         if (l < lb) {
           do {
@@ -1195,10 +1262,10 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
       // crossing batch
       FlatLane f;
       bool keep = false;
-      const int nb = flat_decode<VEC>(a, g, (int)min((uint64_t)B, lb - l), p, p_lo, lane, f, keep);
+      const int nb = flat_decode<RF>(a, g, (int)min((uint64_t)B, lb - l), p, p_lo, lane, f, keep);
       const uint32_t kept = __ballot_sync(0xffffffffu, keep);
       if (fill + __popc(kept) > B) {
-        flush_any<VEC, KIND>(a, w, ts, fill, lane);
+        flush_any<RF, KIND>(a, w, ts, fill, lane);
         fill = 0;
       }
       if (keep) {
@@ -1232,28 +1299,28 @@ __device__ __forceinline__ void expand_warp(const ClaimArgs& a, int B, int ts, E
   }
 }
 
-template <bool VEC>
+template <class RF>
 __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.ctr && __ldcg(a.ctr + 1) == 0) return;  // the depth is full: a chunk enqueued ahead has nothing to do
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   ExpandSmem w = expand_smem(smem_raw + (size_t)wib * expand_warp_bytes(a.sys.m, B, ts), a.sys.m, B, ts);
-  expand_warp<VEC, 0>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
+  expand_warp<RF, 0>(a, B, ts, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
 }
 
 // The wide mode of k_expand (rows of more than kWideM neurons).
-template <bool VEC>
+template <class RF>
 __global__ void __launch_bounds__(256, 1) k_expand_wide(ClaimArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.ctr && __ldcg(a.ctr + 1) == 0) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   ExpandSmem w = expand_smem_wide(smem_raw + (size_t)wib * expand_wide_bytes(a.sys.m), a.sys.m);
-  expand_warp<VEC, kWide>(a, kWideB, 0, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
+  expand_warp<RF, kWide>(a, kWideB, 0, w, (uint64_t)blockIdx.x * wpb + wib, (uint64_t)gridDim.x * wpb, lane);
 }
 
 // Step (d) for rows already built in global memory (the tensor-core form):
 // one lane per candidate, the same bounded wait-free passes as k_expand.
-template <bool VEC>
+template <class RF>
 __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t* rows,
                                                       const unsigned long long* hash, const uint8_t* redundant) {
   const int m = a.sys.m;
@@ -1266,12 +1333,12 @@ __global__ void __launch_bounds__(256) k_resolve_rows(ClaimArgs a, const int32_t
     for (int pass = 0;; ++pass) {
       if (!done) {
         unsigned long long* owned = nullptr;
-        const int status = resolve_lane<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned);
+        const int status = resolve_lane<RF>(a, rows + lid * m, key, (uint32_t)lid, owned);
         if (status == kOwner) {
           if (a.inplace)
             finish_owner_inplace(a, key, (uint32_t)lid, owned, a.inplace_base + lid);
           else
-            finish_owner<VEC>(a, rows + lid * m, key, (uint32_t)lid, owned,
+            finish_owner<RF>(a, rows + lid * m, key, (uint32_t)lid, owned,
                               a.store_ctr ? atomicAdd(a.store_ctr, 1ull) : 0ull);
         }
         done = status != kRetry;
@@ -1292,9 +1359,9 @@ void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long l
                          cudaStream_t st, int nsm) {
   const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(((uint64_t)a.Q + 255) / 256, (uint64_t)nsm * 8));
   if (a.sys.m % 4 == 0)
-    k_resolve_rows<true><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
+    k_resolve_rows<RowI32V><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
   else
-    k_resolve_rows<false><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
+    k_resolve_rows<RowI32><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
 }
 
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
@@ -1309,7 +1376,8 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
     a.run = (uint32_t)std::max<uint64_t>(8ull * kWideB, ((uint64_t)a.Q + warps - 1) / warps);
     const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
     const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm);
-    auto fn = (m % 4) == 0 ? k_expand_wide<true> : k_expand_wide<false>;
+    auto fn = a.w == 2 ? k_expand_wide<RowU16> : a.w == 1 ? k_expand_wide<RowU8>
+              : (m % 4) == 0 ? k_expand_wide<RowI32V> : k_expand_wide<RowI32>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     fn<<<blocks > 0 ? blocks : 1, wpb * 32, smem, st>>>(a);
     return 1;
@@ -1328,8 +1396,8 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   }
   const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
   const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm * per_sm);
-  const bool vec = (m % 4) == 0;
-  auto fn = vec ? k_expand<true> : k_expand<false>;
+  auto fn = a.w == 2 ? k_expand<RowU16> : a.w == 1 ? k_expand<RowU8>
+            : (m % 4) == 0 ? k_expand<RowI32V> : k_expand<RowI32>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   fn<<<blocks > 0 ? blocks : 1, wpb * 32, smem, st>>>(a, B, ts);
   return 1;
@@ -1763,15 +1831,15 @@ __global__ void __launch_bounds__(kThreads) k_batch_depth(BatchArgs ba) {
           const uint64_t key = todo ? mix64(sc.hash[lid]) : 0ull;
           const int32_t* row = sc.staging + (size_t)(lid < Q ? lid : 0) * m;
           if ((m & 3) == 0)
-            resolve_warp<true, 1>(a, row, key, lid, todo);
+            resolve_warp<RowI32V, 1>(a, row, key, lid, todo);
           else
-            resolve_warp<false, 1>(a, row, key, lid, todo);
+            resolve_warp<RowI32, 1>(a, row, key, lid, todo);
         }
       } else {
         if ((m & 3) == 0)
-          expand_warp<true, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+          expand_warp<RowI32V, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
         else
-          expand_warp<false, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
+          expand_warp<RowI32, 1>(a, ba.B, ba.ts, w, warp, nwarps, lane);
       }
       __threadfence();
       __syncthreads();

@@ -141,6 +141,7 @@ struct snp_system {
   int32_t m = 0, R = 0, K = 1;
   int32_t max_abs_m = 0;
   std::vector<int32_t> c0, M, rule_neuron, rule_i, rule_j, first_rule, gain;
+  std::vector<uint8_t> c0_packed;  // C0 in a packed store's width (staging of its upload)
   std::vector<int4> rule;
   std::vector<int2> csr;
   // device copies of the system
@@ -169,6 +170,7 @@ struct snp_system {
       d_rec_parent, d_rec_index, d_tmp,
       d_psi, d_prec, d_ctr, d_perm, d_sidx;
   int64_t pool_rows = 0;  // capacity in rows (of the store: every row claimed during an exploration)
+  int32_t row_w = 4;      // bytes per spike count of the store's rows (4: int32; 2, 1: packed)
   int64_t perm_rows = 0;  // capacity of perm (discovery index -> store row)
   int64_t n_store = 0;    // store rows in use
   uint64_t nbuckets = 0;
@@ -189,6 +191,7 @@ struct snp_system {
   std::shared_ptr<snp::BatchArena> batch;
   const int32_t* result_pool = nullptr;  // rows snp_reachable reads (d_pool or the arena)
   const uint32_t* result_perm = nullptr;  // row k of the result is result_pool row result_perm[k] (or k)
+  int32_t result_w = 4;                   // bytes per spike count of result_pool's rows
 
   snp::DevSys dev() const {
     snp::DevSys s;

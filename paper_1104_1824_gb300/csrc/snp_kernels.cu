@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(256) k_psi(DevSys s, const int32_t* rows, cons
 // neurons l, l + 32, ... (coalesced), the lanes' products combined with the
 // saturating product, so that a row of many neurons is not one thread's
 // serial walk.
+template <class RF>
 __global__ void __launch_bounds__(256) k_psi_warp(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
                                                   int32_t max_expand, uint64_t* psi, ChunkState* st) {
   const int m = s.m;
@@ -133,9 +134,9 @@ __global__ void __launch_bounds__(256) k_psi_warp(DevSys s, const int32_t* rows,
   }
   bool over = false;
   for (int64_t p = w0; p < P; p += nw) {
-    const int32_t* row = rows + (size_t)(perm ? __ldg(perm + p) : (uint64_t)p) * m;
+    const typename RF::T* row = row_at<RF>(rows, perm ? __ldg(perm + p) : (uint64_t)p, m);
     PsiAcc acc;
-    for (int n = lane; n < m; n += 32) acc.visit<false>(s, n, __ldg(row + n), max_expand, nullptr);
+    for (int n = lane; n < m; n += 32) acc.visit<false>(s, n, (int32_t)__ldg(row + n), max_expand, nullptr);
     acc.flush();
     uint64_t v = acc.prod;
 #pragma unroll
@@ -148,13 +149,14 @@ __global__ void __launch_bounds__(256) k_psi_warp(DevSys s, const int32_t* rows,
   if (over && lane == 0) set_error(st, kErrOverflow);
 }
 
-// k_psi for m % 4 == 0 with coalesced loads: a block takes 256 rows at a
-// time and moves them through shared memory 32 columns at a time (each row's
-// slab is 128 contiguous bytes, read by 8 consecutive threads); thread t then
-// reads row t's slab at a stride of 33 words, so the 32 lanes of a warp hit 32
-// different banks.
+// k_psi for rows that move in 16-byte pieces (RF::VEC) with coalesced loads:
+// a block takes 256 rows at a time and moves them through shared memory 32
+// columns at a time (each row's slab is 128 contiguous bytes in int32 rows,
+// read by 8 consecutive threads; 64 or 32 bytes in packed rows), unpacked to
+// int32; thread t then reads row t's slab at a stride of 33 words, so the 32
+// lanes of a warp hit 32 different banks.
 constexpr int kPsiRows = 256, kPsiSlab = 32;
-template <bool REC>
+template <class RF, bool REC>
 __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P,
                                                         int32_t max_expand, uint64_t* psi, ParentRec* rec,
                                                         ChunkState* st) {
@@ -171,20 +173,20 @@ __global__ void __launch_bounds__(kPsiRows) k_psi_tiled(DevSys s, const int32_t*
     const int64_t p = p0 + t;
     PsiAcc acc;
     for (int n0 = 0; n0 < m; n0 += kPsiSlab) {
-      const int w = min(kPsiSlab, m - n0);  // columns in this slab (a multiple of 4)
-      const int q4 = w >> 2;                // 16-byte pieces per row
+      const int w = min(kPsiSlab, m - n0);  // columns in this slab (a multiple of RF::PER16)
+      const int q4 = w / RF::PER16;         // 16-byte pieces per row
       __syncthreads();
       // rows stream through L2 only, so that they do not evict the
       // applicability table every visit reads from L1
       for (int i = t; i < nrows * q4; i += kPsiRows) {
         const int r = i / q4, q = i - r * q4;
         const uint64_t pr = perm ? __ldcg(perm + p0 + r) : (uint64_t)(p0 + r);
-        const int4 v = __ldcg(reinterpret_cast<const int4*>(rows + (size_t)pr * m + n0) + q);
-        int32_t* d = &slab[r][4 * q];
-        d[0] = v.x;
-        d[1] = v.y;
-        d[2] = v.z;
-        d[3] = v.w;
+        const uint4 v = __ldcg(reinterpret_cast<const uint4*>(row_at<RF>(rows, pr, m) + n0) + q);
+        int32_t x[RF::PER16];
+        unpack_piece<RF>(v, x);
+        int32_t* d = &slab[r][RF::PER16 * q];
+#pragma unroll
+        for (int k = 0; k < RF::PER16; ++k) d[k] = x[k];
       }
       __syncthreads();
       if (t < nrows)
@@ -224,20 +226,23 @@ int launch_psi_head_check(const uint64_t* psi, int64_t n, ChunkState* st, cudaSt
   return 1;
 }
 
-int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, int32_t max_expand, uint64_t* psi,
-               ParentRec* rec, ChunkState* st, cudaStream_t stream, int nsm) {
+int launch_psi(DevSys s, const int32_t* rows, int w, const uint32_t* perm, int64_t P, int32_t max_expand,
+               uint64_t* psi, ParentRec* rec, ChunkState* st, cudaStream_t stream, int nsm) {
   const int threads = 256;
   const int64_t want = (P + threads - 1) / threads;
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
   if (!rec && P <= (int64_t)nsm * 256) {  // a warp per row
     const int wb = (int)std::max<int64_t>(1, (P + 7) / 8);
-    k_psi_warp<<<wb, 256, 0, stream>>>(s, rows, perm, P, max_expand, psi, st);
+    auto fn = w == 1 ? k_psi_warp<RowU8> : w == 2 ? k_psi_warp<RowU16> : k_psi_warp<RowI32>;
+    fn<<<wb, 256, 0, stream>>>(s, rows, perm, P, max_expand, psi, st);
     return 1;
   }
-  if ((s.m % 4) == 0) {
+  if (w == 1 || w == 2 || (s.m % 4) == 0) {
     const int64_t tiles = (P + kPsiRows - 1) / kPsiRows;
     const int tb = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)nsm * 6));
-    auto fn = rec ? k_psi_tiled<true> : k_psi_tiled<false>;
+    auto fn = w == 1   ? (rec ? k_psi_tiled<RowU8, true> : k_psi_tiled<RowU8, false>)
+              : w == 2 ? (rec ? k_psi_tiled<RowU16, true> : k_psi_tiled<RowU16, false>)
+                       : (rec ? k_psi_tiled<RowI32V, true> : k_psi_tiled<RowI32V, false>);
     fn<<<tb, kPsiRows, 0, stream>>>(s, rows, perm, P, max_expand, psi, rec, st);
     return 1;
   }
@@ -383,27 +388,38 @@ void launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t st) {
   k_iota_u32<<<blocks, 256, 0, st>>>(out, n);
 }
 
-// out[k] = pool[perm[k]] for k < n, one warp per row (16-byte pieces when
-// m % 4 == 0).
+// out[k] = pool[perm[k]] (pool[k] without perm) for k < n as int32 rows, one
+// warp per row (16-byte pieces of the output when m % 4 == 0; packed rows are
+// widened four counts at a time).
+template <class RF>
 __global__ void k_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out) {
   const int lane = threadIdx.x & 31;
   const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   for (int64_t k = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); k < n; k += nw) {
-    const int32_t* src = pool + (size_t)__ldg(perm + k) * m;
+    const typename RF::T* src = row_at<RF>(pool, perm ? __ldg(perm + k) : (uint64_t)k, m);
     int32_t* dst = out + (size_t)k * m;
-    if ((m & 3) == 0) {
-      const int4* s4 = reinterpret_cast<const int4*>(src);
+    if constexpr (RF::VEC) {
       int4* d4 = reinterpret_cast<int4*>(dst);
-      for (int j = lane; j < (m >> 2); j += 32) d4[j] = __ldg(s4 + j);
+      for (int j = lane; j < (m >> 2); j += 32) {
+        if constexpr (RF::W == 1)
+          d4[j] = unpack4_u8(__ldg(reinterpret_cast<const uint32_t*>(src) + j));
+        else if constexpr (RF::W == 2)
+          d4[j] = unpack4_u16(__ldg(reinterpret_cast<const uint2*>(src) + j));
+        else
+          d4[j] = __ldg(reinterpret_cast<const int4*>(src) + j);
+      }
     } else {
       for (int j = lane; j < m; j += 32) dst[j] = __ldg(src + j);
     }
   }
 }
 
-void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out, cudaStream_t st) {
+void launch_gather_rows(const int32_t* pool, int w, const uint32_t* perm, int64_t n, int m, int32_t* out,
+                        cudaStream_t st) {
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152 * 64));
-  k_gather_rows<<<blocks, 256, 0, st>>>(pool, perm, n, m, out);
+  auto fn = w == 1 ? k_gather_rows<RowU8> : w == 2 ? k_gather_rows<RowU16>
+            : (m & 3) == 0 ? k_gather_rows<RowI32V> : k_gather_rows<RowI32>;
+  fn<<<blocks, 256, 0, st>>>(pool, perm, n, m, out);
 }
 
 // Clears the first-occurrence bitmap; with ctr, one thread then moves the
@@ -427,6 +443,7 @@ __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long
 
 // Inserts committed rows [r0, r1) (all distinct) into an empty or partly
 // filled table: used for C0 and to rebuild the table when it grows.
+template <class RF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_insert_rows(DevSys s, const int32_t* pool,
                                                                      const uint32_t* perm, int64_t r0, int64_t r1,
                                                                      DevTable t, ChunkState* st) {
@@ -434,7 +451,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_insert_rows(DevSys s, c
   const int64_t nw = (int64_t)gridDim.x * kWarpsPerBlock;
   for (int64_t r = r0 + (int64_t)blockIdx.x * kWarpsPerBlock + wib; r < r1; r += nw) {
     const uint32_t sr = perm ? __ldg(perm + r) : (uint32_t)r;  // the row's place in the pool (the store)
-    const int32_t* row = pool + (size_t)sr * s.m;
+    const typename RF::T* row = row_at<RF>(pool, sr, s.m);
     const uint64_t h = fingerprint(s, row, lane);
     if (lane == 0) {
       const unsigned long long val = ((unsigned long long)fp32_of(h) << 32) | sr;
@@ -450,6 +467,49 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_insert_rows(DevSys s, c
       if (!done) set_error(st, kErrTableFull);
     }
   }
+}
+
+// *out = max(*out, x[0 .. n)) (*out starts at 0; the counts are >= 0).
+__global__ void k_count_max(const int32_t* x, int64_t n, int32_t* out) {
+  int32_t v = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    v = max(v, __ldg(x + i));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+void launch_count_max(const int32_t* x, int64_t n, int32_t* out, cudaStream_t st) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+  k_count_max<<<blocks, 256, 0, st>>>(x, n, out);
+}
+
+// n int32 rows into rows of format RF (counts within its range), four counts
+// per thread.
+template <class RF>
+__global__ void k_pack_rows(const int32_t* src, int64_t n4, int32_t* dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(src) + i);
+    if constexpr (RF::W == 1)
+      reinterpret_cast<uint32_t*>(dst)[i] = pack4_u8(v);
+    else
+      reinterpret_cast<uint2*>(dst)[i] = pack4_u16(v);
+  }
+}
+
+void launch_pack_rows(const int32_t* src, int64_t n, int m, int w, int32_t* dst, cudaStream_t st) {
+  const int64_t n4 = n * (m / 4);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n4 + 255) / 256, 152 * 32));
+  if (w == 1)
+    k_pack_rows<RowU8><<<blocks, 256, 0, st>>>(src, n4, dst);
+  else
+    k_pack_rows<RowU16><<<blocks, 256, 0, st>>>(src, n4, dst);
+}
+
+void launch_insert_rows(DevSys s, const int32_t* pool, int w, const uint32_t* perm, int64_t r0, int64_t r1,
+                        DevTable t, ChunkState* st, int blocks, cudaStream_t stream) {
+  auto fn = w == 1 ? k_insert_rows<RowU8> : w == 2 ? k_insert_rows<RowU16> : k_insert_rows<RowI32>;
+  fn<<<blocks, kWarpsPerBlock * 32, 0, stream>>>(s, pool, perm, r0, r1, t, st);
 }
 
 // All children of one configuration C in canonical order (no deduplication).

@@ -36,6 +36,10 @@ struct ClaimArgs {
   int32_t inplace = 0;
   uint64_t inplace_base = 0;
   uint64_t wait_ns = 0;       // > 0: time limit of a wait for a slot being claimed
+  // Bytes per spike count of the rows of parents, pool and staging: 4
+  // (int32), or 2 / 1 in a packed store (uint16 / uint8; m a multiple of 8 /
+  // 16).  The pointers keep their int32_t type in every case.
+  int32_t w = 4;
 };
 
 struct CommitArgs {
@@ -125,9 +129,9 @@ size_t batch_tc_smem_bytes_host();
 __global__ void k_batch_init(BatchSys* sys, const int32_t* c0, const int64_t* c0_off, int32_t n);
 
 // Step (a) and Psi for P frontier rows; returns the launches made.
-int launch_psi(DevSys s, const int32_t* rows, const uint32_t* perm, int64_t P, int32_t max_expand, uint64_t* psi,
-               ParentRec* rec, ChunkState* st,
-               cudaStream_t stream, int nsm);
+// rows: w bytes per spike count (4: int32; 2, 1: a packed store).
+int launch_psi(DevSys s, const int32_t* rows, int w, const uint32_t* perm, int64_t P, int32_t max_expand,
+               uint64_t* psi, ParentRec* rec, ChunkState* st, cudaStream_t stream, int nsm);
 // Sets st->psi_saturated when Psi summed (saturating) over psi[0 .. n) is
 // 2^64 - 1: later frontier rows then hold no candidate, and launch_psi with
 // that st writes Psi = 0 for them without reading them.
@@ -183,12 +187,21 @@ __global__ void k_mark(uint32_t* ownbits, const uint32_t* gmin, uint32_t* bits, 
                        ChunkState* st);
 __global__ void k_commit(CommitArgs a);
 void launch_iota_u32(uint32_t* out, int64_t n, cudaStream_t st);
-void launch_gather_rows(const int32_t* pool, const uint32_t* perm, int64_t n, int m, int32_t* out, cudaStream_t st);
+// out[k] = row perm[k] (row k without perm) of a pool of w bytes per count, as int32.
+void launch_gather_rows(const int32_t* pool, int w, const uint32_t* perm, int64_t n, int m, int32_t* out,
+                        cudaStream_t st);
 // Testing hook: marks the slot holding store row `row` as being claimed.
 __global__ void k_hold_slot_of_row(unsigned long long* slots, uint64_t n, uint32_t row);
 __global__ void k_clear_bits(uint32_t* bits, uint32_t nwords, unsigned long long* ctr, const ChunkState* st);
-__global__ void k_insert_rows(DevSys s, const int32_t* pool, const uint32_t* perm, int64_t r0, int64_t r1, DevTable t,
-                              ChunkState* st);
+// *out = max(*out, x[0 .. n)) for counts x >= 0.
+void launch_count_max(const int32_t* x, int64_t n, int32_t* out, cudaStream_t st);
+// n int32 rows of m counts (m % 8 == 0, each count within the range of w
+// bytes) into rows of w = 1 or 2 bytes per count at dst.
+void launch_pack_rows(const int32_t* src, int64_t n, int m, int w, int32_t* dst, cudaStream_t st);
+// Inserts rows [r0, r1) of a pool of w bytes per count into the table
+// (blocks CTAs of kWarpsPerBlock warps).
+void launch_insert_rows(DevSys s, const int32_t* pool, int w, const uint32_t* perm, int64_t r0, int64_t r1,
+                        DevTable t, ChunkState* st, int blocks, cudaStream_t stream);
 __global__ void k_step_children(DevSys s, const int32_t* C, uint64_t n, int32_t* out);
 __global__ void k_fill_u64(unsigned long long* p, uint64_t n, unsigned long long v);
 

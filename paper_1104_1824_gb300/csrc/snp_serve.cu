@@ -206,6 +206,8 @@ int retire(snp_server* S, Request* r) {
   h->batch.reset();
   h->result_pool = h->d_pool.as<int32_t>();
   h->result_perm = nullptr;
+  h->result_w = 4;
+  h->row_w = 4;
   r->status = (b.error & kErrOverflow) ? SNP_E_OVERFLOW
               : (b.error & kErrTimeout) ? SNP_E_TIMEOUT
               : b.error ? SNP_E_INTERNAL : SNP_OK;

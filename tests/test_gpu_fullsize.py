@@ -5,7 +5,8 @@
   per-depth records (tests/golden/oracle_digests.json), the sparse form with
   its automatic pass size (several tasks per warp, the Psi shortcut).
 * The 1024-neuron system at full size (cap 2^22, budget 2^26, depth 4: 16.8 M
-  configurations of 4 KB), sparse and fp8 tensor-core forms: both give the
+  configurations of 4 KB), sparse and fp8 tensor-core forms and the sparse
+  form with a packed (uint16) store: all give the
   same configurations in the same order and the same parent records; every
   configuration is distinct; 1000 sampled configurations are each the
   recorded child of their recorded parent (the oracle recomputes it); the
@@ -67,9 +68,11 @@ def test_dense1024_full_size(gpu):
     gen = torch.Generator(device="cpu").manual_seed(5)
     keys = (torch.randint(1, 2 ** 62, (system.m,), generator=gen, dtype=torch.int64) * 2 + 1).cuda()
     runs = {}
-    for form in (gpu.SNP_T_SPARSE_I32, gpu.SNP_T_TC_F8):
+    for name, form, packed in (("sparse", gpu.SNP_T_SPARSE_I32, False), ("f8", gpu.SNP_T_TC_F8, False),
+                               ("packed", gpu.SNP_T_SPARSE_I32, True)):
         s = gpu.System(system)
-        s.explore(depth, cap=cap, budget=budget, transition=form, record_parents=True)
+        s.explore(depth, cap=cap, budget=budget, transition=form, record_parents=True, packed=packed)
+        assert s.row_width() == (2 if packed else 4)
         n = s.count()
         assert n == 1 + depth * cap
         rows = torch.empty((n, system.m), dtype=torch.int32, device="cuda")
@@ -77,7 +80,7 @@ def test_dense1024_full_size(gpu):
         fp = _row_keys(torch, rows, keys)
         assert torch.unique(fp).numel() == n  # every configuration is new once
         par, idx = s.parents()
-        rng = np.random.default_rng(form)
+        rng = np.random.default_rng(form + 7 * packed)
         ks = np.sort(rng.choice(n - 1, size=1000, replace=False) + 1)
         sample = rows[torch.from_numpy(ks).cuda()].cpu().numpy()
         parents = rows[torch.from_numpy(par[ks]).cuda()].cpu().numpy()
@@ -85,12 +88,13 @@ def test_dense1024_full_size(gpu):
             assert par[k] < k
             ch = o.child(parent, int(idx[k]))
             assert ch is not None and (ch == child).all(), k
-        runs[form] = (fp.cpu().numpy(), par, idx, records(s))
+        runs[name] = (fp.cpu().numpy(), par, idx, records(s))
         del rows, fp
         s.close()
         torch.cuda.empty_cache()
-    a, b = runs[gpu.SNP_T_SPARSE_I32], runs[gpu.SNP_T_TC_F8]
-    assert (a[0] == b[0]).all() and (a[1] == b[1]).all() and (a[2] == b[2]).all() and a[3] == b[3]
+    a = runs["sparse"]
+    for b in (runs["f8"], runs["packed"]):
+        assert (a[0] == b[0]).all() and (a[1] == b[1]).all() and (a[2] == b[2]).all() and a[3] == b[3]
     # the cap and budget rule: every depth accepts cap new configurations
     # before its budget runs out, out of more than 2^64 - 1 candidates
     for d, (new, examined, candidates, truncated) in enumerate(a[3]):

@@ -1,0 +1,186 @@
+"""Packed configurations: the store keeps each spike count in 1 or 2 bytes
+where a bound on every reachable count allows it (snp_explore_opts.packed).
+
+The result must not depend on the store's width: every packed exploration is
+compared with the oracle (or with the oracle's stored digests) exactly as the
+int32 path is, and the width chosen is checked against the bound (counts
+start at C0 and grow by at most gain[j] per step in column j).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import snp_synth
+from test_gpu_parity import assert_same, digest, explore_both, few_choice_system, golden_digests
+
+pytestmark = pytest.mark.gpu
+
+
+def column_gain(system) -> np.ndarray:
+    """gain[j]: the most one step can add to column j -- per neuron the
+    largest entry of column j among its rules (at most one fires), summed."""
+    M = np.asarray(system.M, dtype=np.int64).reshape(system.R, system.m)
+    rn = np.asarray(system.rule_neuron)
+    g = np.zeros(system.m, dtype=np.int64)
+    for n in range(system.m):
+        rows = M[rn == n]
+        if len(rows):
+            g += np.maximum(rows.max(axis=0), 0)
+    return g
+
+
+def expected_width(system, depth: int) -> int:
+    b = int((np.asarray(system.c0, dtype=np.int64) + depth * column_gain(system)).max())
+    if b <= 255 and system.m % 16 == 0:
+        return 1
+    if b <= 65535 and system.m % 8 == 0:
+        return 2
+    return 4
+
+
+@pytest.mark.parametrize("m", [16, 32, 48, 64, 128, 144, 256, 1024])
+def test_packed_uint8_against_the_oracle(gpu, m):
+    """uint8 rows through the narrow (m <= 128) and wide expand kernels."""
+    system = snp_synth.random_system(500 + m, m, (1, 4), (1, min(8, m - 1)), (0, 6), "sparse")
+    s, e = explore_both(gpu, system, 3, cap=300, budget=3000, packed=True)
+    assert s.row_width() == expected_width(system, 3) == 1
+    assert_same(s, e)
+
+
+@pytest.mark.parametrize("m,lo,hi", [(24, 0, 6), (64, 200, 250), (136, 300, 900)])
+def test_packed_uint16_against_the_oracle(gpu, m, lo, hi):
+    """uint16 rows: m a multiple of 8 but not of 16, or counts past 255."""
+    system = snp_synth.random_system(700 + m, m, (1, 4), (1, 6), (lo, hi), "sparse")
+    s, e = explore_both(gpu, system, 3, cap=400, budget=4000, packed=True)
+    assert s.row_width() == expected_width(system, 3) == 2
+    assert_same(s, e)
+
+
+def test_packed_falls_back_to_int32(gpu):
+    """Rows that are no whole number of 16-byte pieces, counts that could pass
+    65535, and the tensor-core forms keep int32 rows."""
+    cases = [snp_synth.random_system(41, 20, (1, 3), (1, 4), (0, 6), "sparse"),
+             snp_synth.random_system(42, 64, (1, 3), (1, 4), (65000, 65530), "sparse")]
+    for system in cases:
+        s, e = explore_both(gpu, system, 3, cap=200, budget=2000, packed=True)
+        assert s.row_width() == 4
+        assert_same(s, e)
+    system = snp_synth.random_64(1)
+    for t in (gpu.SNP_T_TC_F8, gpu.SNP_T_TC_I8):
+        s, e = explore_both(gpu, system, 3, cap=500, budget=5000, packed=True, transition=t)
+        assert s.row_width() == 4
+        assert_same(s, e)
+    s, e = explore_both(gpu, system, 3, cap=500, budget=5000)
+    assert s.row_width() == 4
+    assert_same(s, e)
+
+
+@pytest.mark.parametrize("chunk", [0, 1000, 4097])
+def test_packed_random64_small_digest(gpu, chunk):
+    """The 64-neuron system at depth 4 (uint8 rows) against the oracle's
+    stored digest and per-depth records, several pass sizes."""
+    g = golden_digests()["random64_seed1_small"]
+    p = g["params"]
+    s = gpu.System(snp_synth.random_64(1))
+    s.explore(p["depth"], cap=p["cap"], budget=p["budget"], chunk=chunk, packed=True)
+    assert s.row_width() == 1
+    assert digest(s.reachable()) == g["sha256"]
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in s.depth_stats()] == g["per_depth"]
+
+
+def test_packed_dense1024_cap_2_16(gpu):
+    """The 1024-neuron system with cap 2^16, budget 2^19, depth 3 (uint16
+    rows: the bound reaches 1975) against the oracle's digest."""
+    g = golden_digests()["dense1024_seed3_mid"]
+    p = g["params"]
+    system = snp_synth.dense_1024(3)
+    s = gpu.System(system)
+    s.explore(p["depth"], cap=p["cap"], budget=p["budget"], packed=True)
+    assert s.row_width() == expected_width(system, p["depth"]) == 2
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in s.depth_stats()] == g["per_depth"]
+    got = s.reachable()
+    assert got.shape[0] == g["count"]
+    assert digest(got) == g["sha256"]
+
+
+@pytest.mark.parametrize("m,k,chunk,depth", [(160, 2, 0, 6), (1024, 4, 0, 5), (64, 3, 7, 6)])
+def test_packed_crossing_batches(gpu, m, k, chunk, depth):
+    """Few spiking vectors per parent: every candidate goes through a crossing
+    batch (parent rows unpacked per lane, parent records from the Psi scan)."""
+    system = few_choice_system(m + k, m, k)
+    s, e = explore_both(gpu, system, depth, cap=3000, budget=30000, chunk=chunk, packed=True)
+    assert s.row_width() == 1
+    assert_same(s, e)
+
+
+def test_packed_parent_records(gpu):
+    system = snp_synth.random_64(2)
+    s = gpu.System(system)
+    s.explore(3, cap=5000, budget=80000, record_parents=True, packed=True)
+    assert s.row_width() == 1
+    rows = s.reachable()
+    par, idx = s.parents()
+    o = oracle.Oracle(system)
+    for k in range(1, rows.shape[0], 97):
+        assert (o.child(rows[par[k]], int(idx[k])) == rows[k]).all()
+    e = o.explore(3, cap=5000, budget=80000)
+    assert (rows == e.configs).all()
+
+
+def test_packed_uncapped_growth_rebuilds_the_table(gpu):
+    """No cap: the store and the table grow, and the table is rebuilt from
+    the packed rows found so far (183734 configurations)."""
+    system = snp_synth.random_system(8, 16, (2, 3), (2, 4), (0, 6), "sparse")
+    s, e = explore_both(gpu, system, 4, packed=True)
+    assert s.row_width() == 1
+    assert s.count() == 183734
+    assert_same(s, e)
+
+
+@pytest.mark.parametrize("device_rows", [False, True])
+def test_packed_resume(gpu, device_rows):
+    """A checkpoint (int32 rows) resumed into a packed store gives the result
+    of one exploration; the width then comes from the checkpoint's largest
+    count and the depths still to run."""
+    import torch
+    system = snp_synth.random_64(1)
+    one = gpu.System(system)
+    one.explore(5, cap=20000, budget=300000)
+    a = gpu.System(system)
+    a.explore(2, cap=20000, budget=300000)
+    rows, raw = a.checkpoint()
+    if device_rows:
+        rows = torch.from_numpy(rows).cuda()
+    b = gpu.System(system)
+    b.resume((rows, raw), 5, cap=20000, budget=300000, packed=True)
+    assert b.row_width() == 1
+    assert (b.reachable() == one.reachable()).all()
+    assert [(x.new, x.examined, x.candidates) for x in b.depth_stats()] == \
+        [(x.new, x.examined, x.candidates) for x in one.depth_stats()]
+
+
+def test_packed_store_after_int32_and_back(gpu):
+    """One handle alternating widths: the store's capacity is re-read in rows
+    of each exploration's width."""
+    system = snp_synth.dense_1024(3)
+    s = gpu.System(system)
+    e = oracle.Oracle(system).explore(3, cap=1024, budget=8192)
+    for packed in (True, False, True):
+        s.explore(3, cap=1024, budget=8192, packed=packed)
+        assert s.row_width() == (2 if packed else 4)
+        assert (s.reachable() == e.configs).all()
+
+
+@pytest.mark.slow
+def test_packed_random64_full_size(gpu):
+    """Depth 8, cap 2^20, budget 2^24 (the benchmark's launch configuration)
+    with uint8 rows: the oracle's digest and per-depth records."""
+    g = golden_digests()["random64_seed1_full"]
+    p = g["params"]
+    s = gpu.System(snp_synth.random_64(1))
+    s.explore(p["depth"], cap=p["cap"], budget=p["budget"], packed=True)
+    assert s.row_width() == 1
+    got = s.reachable()
+    assert got.shape[0] == g["count"]
+    assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in s.depth_stats()] == g["per_depth"]
+    assert digest(got) == g["sha256"]
