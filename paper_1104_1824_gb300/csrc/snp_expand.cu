@@ -45,10 +45,10 @@ struct ExpandSmem {
   long long* dpc;             // [B] parent of a queued row still to be built, else -1
   unsigned long long* dt;     // [B] its index among the parent's candidates
   uint32_t* lids;             // [B] chunk-local indices of the queued rows
-  int32_t* par;               // [m4] parent
+  int32_t* par;               // [m4] parent (not kept in the wide mode: its row is read from the store)
   int32_t* buf;               // [m4] block base child
   uint32_t* msk;              // [m4] applicable-rule masks
-  int32_t* ntl;               // [m4] neurons with two or more applicable rules, least significant first
+  uint16_t* ntl;              // [m4] neurons with two or more applicable rules, least significant first
   int2* chg;                  // [m4] (old rule, new rule) pairs of the last block step
   int* hdr;                   // [8] kNnt, kNlow, kRL, kNchg, kNred; hbase at hdr + 6
   uint8_t* dig;               // [m4] digits of the block base
@@ -66,20 +66,21 @@ __host__ __device__ inline size_t expand_keys_bytes(int B) { return ((size_t)B *
 
 __host__ __device__ inline size_t expand_warp_bytes(int m, int B, int ts) {
   const int m4 = round4(m);
-  size_t b = (size_t)B * ts * 4 + expand_keys_bytes(B) + (size_t)m4 * 16 + (size_t)m4 * 8 + 32 + (size_t)m4;
+  size_t b = (size_t)B * ts * 4 + expand_keys_bytes(B) + (size_t)m4 * 14 + (size_t)m4 * 8 + 32 + (size_t)m4;
   return (b + 15) & ~size_t(15);
 }
 
 // Wide rows (more than kWideM neurons): a warp keeps one scratch row instead
 // of one row per lane, and queues up to 32 crossing-batch candidates.
 constexpr int kWideB = 32;
-constexpr int kWide = 2;  // KIND of the wide mode
+constexpr int kWide = 2;        // KIND of the wide mode
+constexpr int kWideWarps = 11;  // warps per CTA (one CTA per SM: 11 x 20.6 KB of shared memory at m = 1024)
 // words of the low neurons' header: (start, length) per low neuron, then the
 // packed low digits of the block's candidates (5 bits per neuron); then the table
-constexpr int kLowDig = 16, kLowHdr = 48, kLowTab = 1536;
+constexpr int kLowDig = 16, kLowHdr = 48, kLowTab = 1024;
 __host__ __device__ inline size_t expand_wide_bytes(int m) {
   const int m4 = round4(m);
-  size_t b = (size_t)m4 * 4 + expand_keys_bytes(kWideB) + (size_t)m4 * 16 + 32 + (size_t)(kLowHdr + kLowTab) * 4 +
+  size_t b = (size_t)m4 * 4 + expand_keys_bytes(kWideB) + (size_t)m4 * 10 + 32 + (size_t)(kLowHdr + kLowTab) * 4 +
              (size_t)m4;
   return (b + 15) & ~size_t(15);
 }
@@ -155,12 +156,13 @@ template <typename T>
 __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const T* __restrict__ row, ExpandSmem& w, int B,
                                                  int lane) {
   __syncwarp();
-  for (int n = lane; n < s.m; n += 32) w.par[n] = row[n];
+  if (w.par)
+    for (int n = lane; n < s.m; n += 32) w.par[n] = row[n];
   __syncwarp();
   uint64_t prod = 1;
   const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
   for (int n = n0; n < n1; ++n) {
-    const uint32_t mask = (uint32_t)appl(s, n, w.par[n]);
+    const uint32_t mask = (uint32_t)appl(s, n, w.par ? w.par[n] : (int32_t)row[n]);
     w.msk[n] = mask;
     prod = sat_mul(prod, mask ? (uint64_t)__popc(mask) : 1ull);
   }
@@ -177,7 +179,7 @@ __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const T* __res
     const int n = top - lane;
     const bool nt = n >= 0 && __popc(w.msk[n]) > 1;
     const uint32_t b = __ballot_sync(0xffffffffu, nt);
-    if (nt) w.ntl[count + __popc(b & ((1u << lane) - 1u))] = n;
+    if (nt) w.ntl[count + __popc(b & ((1u << lane) - 1u))] = (uint16_t)n;
     count += __popc(b);
   }
   __syncwarp();
@@ -195,11 +197,17 @@ __device__ __forceinline__ uint64_t parent_state(const DevSys& s, const T* __res
 // The block base becomes candidate t of the loaded parent: digits, child in
 // buf, hash, and the count of neurons whose digit picks a rule that repeats an
 // earlier applicable rule's row.
-template <bool WIDE = false>
-__device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint64_t t, uint64_t after, int lane) {
-  for (int n = lane; n < s.m; n += 32) w.buf[n] = w.par[n];
+// (The wide mode passes the parent's row in the store as prow, there being
+// no copy of it in shared memory.)
+template <bool WIDE = false, typename T = int32_t>
+__device__ __forceinline__ void decode_full(const DevSys& s, ExpandSmem& w, uint64_t t, uint64_t after, int lane,
+                                            const T* prow = nullptr) {
   uint64_t hp = 0;
-  for (int n = lane; n < s.m; n += 32) hp += col_hash(s, n, w.par[n]);
+  for (int n = lane; n < s.m; n += 32) {
+    const int32_t x = WIDE ? (int32_t)prow[n] : w.par[n];
+    w.buf[n] = x;
+    hp += col_hash(s, n, x);
+  }
   __syncwarp();
   const int n0 = lane * s.K, n1 = min(n0 + s.K, s.m);
   uint64_t q = (after > t) ? 0ull : t / after;
@@ -646,7 +654,7 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
   w.par = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(w.keys) + expand_keys_bytes(B));
   w.buf = w.par + m4;
   w.msk = reinterpret_cast<uint32_t*>(w.buf + m4);
-  w.ntl = reinterpret_cast<int32_t*>(w.msk + m4);
+  w.ntl = reinterpret_cast<uint16_t*>(w.msk + m4);
   w.chg = reinterpret_cast<int2*>(w.ntl + m4);
   w.hdr = reinterpret_cast<int*>(w.chg + m4);
   w.dig = reinterpret_cast<uint8_t*>(w.hdr + 8);
@@ -655,8 +663,9 @@ __device__ __forceinline__ ExpandSmem expand_smem(unsigned char* base, int m, in
 }
 
 // Per-warp shared memory of the wide mode: the scratch row, the queue of
-// crossing-batch candidates, then the parent state as in expand_smem (no
-// change list: the odometer's swaps go straight into the block base).
+// crossing-batch candidates, then the parent state as in expand_smem without
+// the parent's row (read from the store when a task starts) and without a
+// change list (the odometer's swaps go straight into the block base).
 __device__ __forceinline__ ExpandSmem expand_smem_wide(unsigned char* base, int m) {
   const int m4 = round4(m);
   ExpandSmem w;
@@ -665,10 +674,10 @@ __device__ __forceinline__ ExpandSmem expand_smem_wide(unsigned char* base, int 
   w.dpc = reinterpret_cast<long long*>(w.keys + kWideB);
   w.dt = reinterpret_cast<unsigned long long*>(w.dpc + kWideB);
   w.lids = reinterpret_cast<uint32_t*>(w.dt + kWideB);
-  w.par = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(w.keys) + expand_keys_bytes(kWideB));
-  w.buf = w.par + m4;
+  w.par = nullptr;
+  w.buf = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(w.keys) + expand_keys_bytes(kWideB));
   w.msk = reinterpret_cast<uint32_t*>(w.buf + m4);
-  w.ntl = reinterpret_cast<int32_t*>(w.msk + m4);
+  w.ntl = reinterpret_cast<uint16_t*>(w.msk + m4);
   w.chg = nullptr;
   w.hdr = reinterpret_cast<int*>(w.ntl + m4);
   w.low = w.hdr + 8;
@@ -1063,7 +1072,7 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
   const uint64_t b = (g - p_lo) / (uint64_t)RL;
-  decode_full<true>(s, w, b * (uint64_t)RL, after, lane);
+  decode_full<true>(s, w, b * (uint64_t)RL, after, lane, parent_row<RF>(a, p));
   uint64_t hk = 0;
   bool redk = true;
   if (lane < RL) {
@@ -1310,7 +1319,7 @@ __global__ void __launch_bounds__(256, 2) k_expand(ClaimArgs a, int B, int ts) {
 
 // The wide mode of k_expand (rows of more than kWideM neurons).
 template <class RF>
-__global__ void __launch_bounds__(256, 1) k_expand_wide(ClaimArgs a) {
+__global__ void __launch_bounds__(kWideWarps * 32, 1) k_expand_wide(ClaimArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   if (a.ctr && __ldcg(a.ctr + 1) == 0) return;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -1368,7 +1377,7 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const int m = a.sys.m;
   if (m > kWideM) {
     const size_t per_warp = expand_wide_bytes(m);
-    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, (226u << 10) / per_warp));
+    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(kWideWarps, (226u << 10) / per_warp));
     const size_t smem = per_warp * wpb;
     // one task per warp: a task's first block costs a full decode (C + S . M
     // over every neuron), which wide rows make expensive
