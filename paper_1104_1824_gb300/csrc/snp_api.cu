@@ -969,8 +969,11 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
                                 h->d_red.as<uint8_t>(), st, nsm);
             sd.launches += 3;
           } else {
-            launch_expand(a, st, nsm);
-            sd.launches += 1;
+            if (m > kWideM) {
+              TRY(h->d_bcache.reserve(wide_base_bytes(m)));
+              a.bcache = h->d_bcache.as<int32_t>();
+            }
+            sd.launches += launch_expand(a, st, nsm);
           }
           CK(cudaGetLastError());
           if (o->kernel_timing) CK(cudaEventRecord(h->evk[slot][1], st));

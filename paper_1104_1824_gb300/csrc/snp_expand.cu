@@ -1055,6 +1055,110 @@ __device__ __forceinline__ void flush_queue_wide(const ClaimArgs& a, ExpandSmem&
                         [&](int L) { build_flat_row<RF>(a, w.tile, w.dpc[L], w.dt[L], lane); });
 }
 
+// Base children (every firing neuron on its first applicable rule) of the
+// first kBaseSlots parents of a pass that hold at least kBaseMin of its
+// candidates, one CTA each: the wide mode then decodes a block base as the
+// cached base child plus the rows of the neurons whose digit is not 0, rather
+// than C plus a chosen row of M_Pi for every firing neuron.
+struct BaseSlot {
+  int64_t parent;  // frontier row, or -1: slot unused in this pass
+  uint64_t hash;   // linear hash of the base child (unmixed)
+};
+constexpr uint64_t kBaseMin = 4096;
+
+__host__ __device__ inline size_t base_rows_offset() { return sizeof(BaseSlot) * kBaseSlots; }
+
+template <class RF>
+__global__ void __launch_bounds__(256) k_wide_base(ClaimArgs a) {
+  extern __shared__ __align__(16) int32_t brow[];  // [m]
+  __shared__ int64_t s_p0;
+  __shared__ unsigned long long s_h;
+  const DevSys& s = a.sys;
+  const int m = s.m;
+  BaseSlot* hdr = reinterpret_cast<BaseSlot*>(a.bcache);
+  int32_t* out = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(a.bcache) + base_rows_offset()) +
+                 (size_t)blockIdx.x * round4(m);
+  if (threadIdx.x == 0) {
+    int64_t lo = 0, hi = a.P;  // largest p with off[p] <= g0 (off is sorted, off[0] = 0)
+    while (hi - lo > 1) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (__ldg(a.off + mid) <= a.g0) lo = mid; else hi = mid;
+    }
+    s_p0 = lo;
+    s_h = 0;
+  }
+  __syncthreads();
+  const int64_t p = s_p0 + blockIdx.x;
+  bool use = !(a.ctr && __ldcg(a.ctr + 1) == 0) && p < a.P;
+  if (use) {
+    const uint64_t lo = max(__ldg(a.off + p), a.g0), hi = min(__ldg(a.off + p + 1), a.g0 + a.Q);
+    use = hi > lo && hi - lo >= kBaseMin;
+  }
+  if (!use) {
+    if (threadIdx.x == 0) hdr[blockIdx.x].parent = -1;
+    return;
+  }
+  const typename RF::T* prow = parent_row<RF>(a, p);
+  for (int n = threadIdx.x; n < m; n += blockDim.x) brow[n] = (int32_t)prow[n];
+  __syncthreads();
+  uint64_t h = 0;
+  for (int n = threadIdx.x; n < m; n += blockDim.x) {
+    const int32_t x = (int32_t)prow[n];
+    h += col_hash(s, n, x);
+    const uint32_t mask = (uint32_t)appl(s, n, x);
+    if (!mask) continue;
+    const int r = __ldg(s.first_rule + n) + __ffs(mask) - 1;
+    h += __ldg(s.rowkey + r);
+    const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
+    for (int e = e0; e < e1; ++e) {
+      const int2 cv = __ldg(s.csr + e);
+      atomicAdd(&brow[cv.x], cv.y);
+    }
+  }
+  h = warp_sum_u64(h);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_h, (unsigned long long)h);
+  __syncthreads();
+  for (int n = threadIdx.x; n < m; n += blockDim.x) out[n] = brow[n];
+  if (threadIdx.x == 0) {
+    hdr[blockIdx.x].hash = s_h;
+    hdr[blockIdx.x].parent = p;
+  }
+}
+
+// The block base for candidate t of the loaded parent from its cached base
+// child: the neurons whose digit of t is not 0 (least significant first)
+// swap their first applicable rule's row for the chosen one.  Same digits,
+// base row and hash as decode_full.
+__device__ __forceinline__ void decode_from_base(const DevSys& s, ExpandSmem& w, const int32_t* base, uint64_t hbase,
+                                                 uint64_t t, int lane) {
+  const int m4 = round4(s.m);
+  const int4* b4 = reinterpret_cast<const int4*>(base);
+  int4* d4 = reinterpret_cast<int4*>(w.buf);
+  for (int j = lane; j < (m4 >> 2); j += 32) d4[j] = __ldcg(b4 + j);
+  for (int n = lane; n < s.m; n += 32) w.dig[n] = 0;
+  __syncwarp();
+  uint64_t h = hbase, q = t;
+  int red = 0;
+  const int nnt = w.hdr[kNnt];
+  for (int i = 0; i < nnt && q != 0; ++i) {
+    const int n = w.ntl[i];
+    const uint32_t mask = w.msk[n];
+    const uint32_t d = next_digit(q, __popc(mask));
+    if (d == 0) continue;
+    const int r0 = rule_of(s, w, n, 0), rd = rule_of(s, w, n, (int)d);
+    warp_swap_rule(s, w.buf, r0, rd, lane);
+    h += __ldg(s.rowkey + rd) - __ldg(s.rowkey + r0);
+    red += redundant_choice(s, mask, rd) ? 1 : 0;
+    if (lane == 0) w.dig[n] = (uint8_t)d;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    hbase_of(w) = h;
+    w.hdr[kNred] = red;
+  }
+  __syncwarp();
+}
+
 // Block mode in the wide mode: lane k < RL owns candidate k of each block as
 // in block_run, but keeps only its hash; rows are built on demand from the
 // block base, to which the odometer applies its swaps directly.
@@ -1072,7 +1176,19 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   }
   const int RL = w.hdr[kRL], nlow = w.hdr[kNlow], nnt = w.hdr[kNnt];
   const uint64_t b = (g - p_lo) / (uint64_t)RL;
-  decode_full<true>(s, w, b * (uint64_t)RL, after, lane, parent_row<RF>(a, p));
+  int slot = -1;  // the parent's cached base child, if the pass has one
+  if (a.bcache) {
+    const BaseSlot* hs = reinterpret_cast<const BaseSlot*>(a.bcache);
+    const uint32_t hit = __ballot_sync(0xffffffffu, lane < kBaseSlots && __ldcg(&hs[lane].parent) == p);
+    slot = hit ? __ffs(hit) - 1 : -1;
+  }
+  if (slot >= 0)
+    decode_from_base(s, w,
+                     reinterpret_cast<const int32_t*>(reinterpret_cast<const unsigned char*>(a.bcache) +
+                                                      base_rows_offset()) + (size_t)slot * round4(s.m),
+                     __ldcg(&reinterpret_cast<const BaseSlot*>(a.bcache)[slot].hash), b * (uint64_t)RL, lane);
+  else
+    decode_full<true>(s, w, b * (uint64_t)RL, after, lane, parent_row<RF>(a, p));
   uint64_t hk = 0;
   bool redk = true;
   if (lane < RL) {
@@ -1373,6 +1489,8 @@ void launch_resolve_rows(ClaimArgs a, const int32_t* rows, const unsigned long l
     k_resolve_rows<RowI32><<<blocks, 256, 0, st>>>(a, rows, hash, redundant);
 }
 
+size_t wide_base_bytes(int m) { return base_rows_offset() + (size_t)kBaseSlots * round4(m) * 4; }
+
 int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
   const int m = a.sys.m;
   if (m > kWideM) {
@@ -1385,11 +1503,17 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
     a.run = (uint32_t)std::max<uint64_t>(8ull * kWideB, ((uint64_t)a.Q + warps - 1) / warps);
     const uint64_t ntasks = ((uint64_t)a.Q + a.run - 1) / a.run;
     const int blocks = (int)std::min<uint64_t>((ntasks + wpb - 1) / wpb, (uint64_t)nsm);
+    if (a.bcache) {  // base children of the pass's largest parents
+      const size_t bs = (size_t)round4(m) * 4;
+      auto fb = a.w == 2 ? k_wide_base<RowU16> : a.w == 1 ? k_wide_base<RowU8>
+                : (m % 4) == 0 ? k_wide_base<RowI32V> : k_wide_base<RowI32>;
+      fb<<<kBaseSlots, 256, bs, st>>>(a);
+    }
     auto fn = a.w == 2 ? k_expand_wide<RowU16> : a.w == 1 ? k_expand_wide<RowU8>
               : (m % 4) == 0 ? k_expand_wide<RowI32V> : k_expand_wide<RowI32>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     fn<<<blocks > 0 ? blocks : 1, wpb * 32, smem, st>>>(a);
-    return 1;
+    return a.bcache ? 2 : 1;
   }
   const int ts = round4(m) + 4;  // tile row stride (words): 16-byte aligned, rotates banks
   const int B = (int)std::min<size_t>(32, std::max<size_t>(1, (32u << 10) / (4u * ts)));

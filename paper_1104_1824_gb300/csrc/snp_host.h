@@ -168,7 +168,8 @@ struct snp_system {
   // exploration state
   DevBuf d_pool, d_slots, d_gmin, d_slot_of, d_bits, d_wbase, d_srow, d_own, d_off, d_scan_tmp, d_st,
       d_rec_parent, d_rec_index, d_tmp,
-      d_psi, d_prec, d_ctr, d_perm, d_sidx;
+      d_psi, d_prec, d_ctr, d_perm, d_sidx,
+      d_bcache;  // wide mode: base children of each pass's largest parents
   int64_t pool_rows = 0;  // capacity in rows (of the store: every row claimed during an exploration)
   int32_t row_w = 4;      // bytes per spike count of the store's rows (4: int32; 2, 1: packed)
   int64_t perm_rows = 0;  // capacity of perm (discovery index -> store row)

@@ -40,7 +40,14 @@ struct ClaimArgs {
   // (int32), or 2 / 1 in a packed store (uint16 / uint8; m a multiple of 8 /
   // 16).  The pointers keep their int32_t type in every case.
   int32_t w = 4;
+  // Wide mode: base children of the pass's largest parents (wide_base_bytes;
+  // filled by the launch before each pass), or nullptr.
+  int32_t* bcache = nullptr;
 };
+
+// Wide mode: base children cached per pass (headers, then rows of round4(m)).
+constexpr int kBaseSlots = 8;
+size_t wide_base_bytes(int m);
 
 struct CommitArgs {
   DevSys sys;
