@@ -111,6 +111,10 @@ def load_library(path: str = LIB_PATH):
     lib.snp_parents.argtypes = [vp, vp, vp, i64, ctypes.POINTER(i64)]
     lib.snp_depth_stats.argtypes = [vp, i32, ctypes.POINTER(snp_depth_info)]
     lib.snp_row_width.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.snp_explore_resume.argtypes = [vp, vp, i64, ctypes.POINTER(snp_depth_info), i32,
+                                       ctypes.POINTER(snp_explore_opts), ctypes.POINTER(i32), vp]
+    lib.snp_debug_fail_allocation.argtypes = [i64]
+    lib.snp_abi_version.argtypes = []
     lib.snp_explore_static.argtypes = [vp, ctypes.POINTER(snp_explore_opts), vp, i64, ctypes.POINTER(i64),
                                        ctypes.POINTER(i32), vp]
     lib.snp_tc_peak_tops.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -220,7 +224,8 @@ def snp_explore_resume(h, rows: np.ndarray, stats, opts: snp_explore_opts,
     else:
         rows = np.ascontiguousarray(rows, dtype=np.int32)
         ptr, n = rows.ctypes.data, int(rows.shape[0])
-    _check(load_library().snp_explore_resume(h, ctypes.c_void_p(ptr), ctypes.c_int64(n), stats,
+    _check(load_library().snp_explore_resume(h, ctypes.c_void_p(ptr), ctypes.c_int64(n),
+                                             ctypes.cast(stats, ctypes.POINTER(snp_depth_info)),
                                              ctypes.c_int32(len(stats)), ctypes.byref(opts), ctypes.byref(dr),
                                              _ptr(truncated_flags)))
     return dr.value

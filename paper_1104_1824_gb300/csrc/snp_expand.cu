@@ -726,29 +726,40 @@ __device__ __forceinline__ void warp_swap_rule(const DevSys& s, int32_t* row, in
 }
 
 // Row of candidate L of the current block in the scratch row: the block base
-// with the low digits of L (all lanes decode the same digits).
+// with the low digits of L (all lanes decode the same digits).  cur holds the
+// packed low digits of the row the scratch row already holds (kNoRow: none
+// of this block): only the digits that differ are swapped, so that the
+// owners of a block, taken in lane order, mostly cost one swap each.
+constexpr uint32_t kNoRow = 0xFFFFFFFFu;
 template <bool VEC>
-__device__ __forceinline__ void build_block_row(const DevSys& s, ExpandSmem& w, int L, int nlow, int lane) {
-  __syncwarp();
-  warp_copy_row<VEC>(w.buf, w.tile, s.m, lane);
-  __syncwarp();
-  const bool tab = w.hdr[kLowOk] != 0;
+__device__ __forceinline__ void build_block_row(const DevSys& s, ExpandSmem& w, int L, int nlow, int lane,
+                                                uint32_t& cur) {
+  uint32_t from = cur;
   const uint32_t pk = (uint32_t)w.low[kLowDig + L];
+  if (from == kNoRow) {
+    __syncwarp();
+    warp_copy_row<VEC>(w.buf, w.tile, s.m, lane);
+    __syncwarp();
+    from = 0;
+  }
+  cur = pk;
+  const bool tab = w.hdr[kLowOk] != 0;
   for (int i = 0; i < nlow; ++i) {
-    const uint32_t d = (pk >> (5 * i)) & 31u;
-    if (d == 0) continue;
+    const uint32_t d0 = (from >> (5 * i)) & 31u, d = (pk >> (5 * i)) & 31u;
+    if (d == d0) continue;
     const int n = w.ntl[i];
     if (tab) {  // the support's columns are distinct: a lane reads its three before it writes them
       const int len = w.low[2 * i + 1];
       const int32_t* col = w.low + kLowHdr + w.low[2 * i];
-      const int32_t* dv = col + (int)d * len;
+      const int32_t* dv = col + (int)d * len;   // M[rule d] - M[rule 0] (d >= 1)
+      const int32_t* dv0 = col + (int)d0 * len;
       for (int k0 = 0; k0 < len; k0 += 96) {
         int c[3], v[3], x[3];
 #pragma unroll
         for (int u = 0; u < 3; ++u) {
           const int k = k0 + lane + 32 * u;
           c[u] = k < len ? col[k] : -1;
-          v[u] = k < len ? dv[k] : 0;
+          v[u] = k < len ? (d ? dv[k] : 0) - (d0 ? dv0[k] : 0) : 0;
         }
 #pragma unroll
         for (int u = 0; u < 3; ++u) x[u] = c[u] >= 0 ? w.tile[c[u]] : 0;
@@ -758,7 +769,7 @@ __device__ __forceinline__ void build_block_row(const DevSys& s, ExpandSmem& w, 
       }
       __syncwarp();
     } else {
-      warp_swap_rule(s, w.tile, rule_of(s, w, n, 0), rule_of(s, w, n, (int)d), lane);
+      warp_swap_rule(s, w.tile, rule_of(s, w, n, (int)d0), rule_of(s, w, n, (int)d), lane);
     }
   }
 }
@@ -1210,8 +1221,9 @@ __device__ __forceinline__ uint64_t block_run_wide(const ClaimArgs& a, ExpandSme
   for (;;) {
     const uint64_t c = gb + lane;
     const bool todo = lane < RL && c >= g && c < gend && !redk && w.hdr[kNred] == 0;
+    uint32_t cur = kNoRow;  // the scratch row holds no candidate of this block yet
     resolve_warp_wide<RF>(a, w.tile, mix64(hbase_of(w) + hk), (uint32_t)(c - a.g0), todo, lane,
-                          [&](int L) { build_block_row<RF::VEC>(s, w, L, nlow, lane); });
+                          [&](int L) { build_block_row<RF::VEC>(s, w, L, nlow, lane, cur); });
     gb += (uint64_t)RL;
     if (gb >= gend) break;
     // next block: the odometer, every lane following the same digits

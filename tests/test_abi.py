@@ -33,6 +33,15 @@ def test_binding_covers_the_header(built_library):
         assert callable(getattr(snp, name)), name
 
 
+def test_binding_declares_every_argument_list(built_library):
+    """Every entry point has its argument types declared: without them ctypes
+    passes a Python int as a 32-bit C int, which truncates a pointer."""
+    import paper_1104_1824_gb300 as snp
+    lib = snp.load_library(built_library)
+    for name in snp.EXPORTS:
+        assert getattr(lib, name).argtypes is not None, name
+
+
 def test_abi_version_and_defaults(built_library):
     import paper_1104_1824_gb300 as snp
     assert snp.snp_abi_version() == 1
