@@ -903,6 +903,34 @@ __device__ __forceinline__ void warp_store_row(const int32_t* row, typename RF::
   }
 }
 
+// Rows of int32 counts leave the scratch row by a bulk copy (cp.async.bulk,
+// issued by lane 0) rather than by 16-byte stores of every lane: the lanes'
+// writes to the scratch row are made visible to the async proxy before the
+// copy is issued; the scratch row is written again only after the copy has
+// read it; the owners publish only after every copy has completed and been
+// made visible to generic loads (then the usual fence and release).
+__device__ __forceinline__ void bulk_store_row(void* dst, const int32_t* scratch, uint32_t bytes, int lane) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+                 "r"((uint32_t)__cvta_generic_to_shared(scratch)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+}
+__device__ __forceinline__ void bulk_wait_read(int lane) {
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncwarp();
+}
+__device__ __forceinline__ void bulk_wait_all(int lane) {
+  if (lane == 0) {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+  }
+  __syncwarp();
+}
+
 constexpr int kProbe = 3, kCompare = 4;
 
 // Step (d) in the wide mode, for one key per lane (lanes with todo set).
@@ -1007,7 +1035,8 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
         }
       }
       // owners: consecutive store rows with one atomic, rows written by the
-      // whole warp, then each owner publishes its slot
+      // whole warp (int32 rows: by bulk copies), then each owner publishes
+      // its slot
       const uint32_t ob = __ballot_sync(0xffffffffu, st == kOwner);
       if (ob) {
         uint64_t sidx = 0;
@@ -1022,10 +1051,17 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
           const uint64_t sl = __shfl_sync(0xffffffffu, sidx, L);
           const uint32_t ll = __shfl_sync(0xffffffffu, lid, L);
           if (a.store_ctr && sl >= a.store_cap) continue;  // reported by lane L below
-          build(L);
-          warp_store_row<RF>(scratch, a.store_ctr ? row_at<RF>(a.pool, sl, m) : row_at<RF>(a.staging, ll, m), m,
-                             lane);
+          typename RF::T* dst = a.store_ctr ? row_at<RF>(a.pool, sl, m) : row_at<RF>(a.staging, ll, m);
+          if constexpr (RF::W == 4 && RF::VEC) {
+            bulk_wait_read(lane);  // the previous owner's copy has read the scratch row
+            build(L);
+            bulk_store_row(dst, scratch, (uint32_t)m * 4u, lane);
+          } else {
+            build(L);
+            warp_store_row<RF>(scratch, dst, m, lane);
+          }
         }
+        if constexpr (RF::W == 4 && RF::VEC) bulk_wait_all(lane);
         __threadfence();
         __syncwarp();
         if (st == kOwner) {
