@@ -1116,7 +1116,7 @@ constexpr uint64_t kBaseMin = 4096;
 __host__ __device__ inline size_t base_rows_offset() { return sizeof(BaseSlot) * kBaseSlots; }
 
 template <class RF>
-__global__ void __launch_bounds__(256) k_wide_base(ClaimArgs a) {
+__global__ void __launch_bounds__(1024) k_wide_base(ClaimArgs a) {
   extern __shared__ __align__(16) int32_t brow[];  // [m]
   __shared__ int64_t s_p0;
   __shared__ unsigned long long s_h;
@@ -1157,9 +1157,13 @@ __global__ void __launch_bounds__(256) k_wide_base(ClaimArgs a) {
     const int r = __ldg(s.first_rule + n) + __ffs(mask) - 1;
     h += __ldg(s.rowkey + r);
     const int e0 = __ldg(&s.rule[r].w), e1 = __ldg(&s.rule[r + 1].w);
-    for (int e = e0; e < e1; ++e) {
-      const int2 cv = __ldg(s.csr + e);
-      atomicAdd(&brow[cv.x], cv.y);
+    for (int e = e0; e < e1; e += 8) {  // eight loads in flight before their adds
+      int2 cv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) cv[u] = e + u < e1 ? __ldg(s.csr + e + u) : make_int2(-1, 0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (cv[u].x >= 0) atomicAdd(&brow[cv[u].x], cv[u].y);
     }
   }
   h = warp_sum_u64(h);
@@ -1555,7 +1559,7 @@ int launch_expand(ClaimArgs a, cudaStream_t st, int nsm) {
       const size_t bs = (size_t)round4(m) * 4;
       auto fb = a.w == 2 ? k_wide_base<RowU16> : a.w == 1 ? k_wide_base<RowU8>
                 : (m % 4) == 0 ? k_wide_base<RowI32V> : k_wide_base<RowI32>;
-      fb<<<kBaseSlots, 256, bs, st>>>(a);
+      fb<<<kBaseSlots, std::min(1024, (m + 31) / 32 * 32), bs, st>>>(a);
     }
     auto fn = a.w == 2 ? k_expand_wide<RowU16> : a.w == 1 ? k_expand_wide<RowU8>
               : (m % 4) == 0 ? k_expand_wide<RowI32V> : k_expand_wide<RowI32>;
