@@ -121,9 +121,10 @@ typedef struct {
  *                    index and the spiking vector's index (snp_parents).
  *  chunk             candidates per device pass; <= 0 chooses automatically:
  *                    up to 2^22 while the rows a pass may claim stay within
- *                    512 MiB, at least 2^20; 2^21 for systems of more than
- *                    128 neurons while the store's reserve for claims past
- *                    the cap (one pass per depth) stays within 64 GiB; the
+ *                    512 MiB, at least 2^20; 2^22 or else 2^21 for systems
+ *                    of more than 128 neurons while the store's reserve for
+ *                    claims past the cap (one pass per depth) stays within
+ *                    64 GiB; the
  *                    last passes of a capped depth are shortened to what the
  *                    cap is expected to take; 65536 at most in the
  *                    int8 tensor-core form, 2^20 at most in the fp8 form.

@@ -572,12 +572,14 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
   // at most 65536 spiking vectors.
   uint64_t qmax = o->chunk > 0 ? (uint64_t)o->chunk
                                : std::min<uint64_t>(1ull << 22, std::max<uint64_t>(1ull << 20, (1ull << 29) / (4ull * m)));
-  // Wide rows: passes of 2^21 (fewer first-block decodes per candidate) while
-  // the store's reserve for claims past the cap, one pass per depth, stays
-  // within 64 GiB.
-  if (o->chunk <= 0 && m > kWideM &&
-      (long double)(1ull << 21) * std::max(o->depth, 1) * 4.0L * m <= (long double)(64ull << 30))
-    qmax = 1ull << 21;
+  // Wide rows: passes of 2^22, else 2^21 (fewer passes, so fewer task starts
+  // and pass tails per candidate), the largest for which the store's reserve
+  // for claims past the cap, one pass per depth, stays within 64 GiB.
+  for (int lg = 22; lg >= 21 && o->chunk <= 0 && m > kWideM; --lg)
+    if ((long double)(1ull << lg) * std::max(o->depth, 1) * 4.0L * m <= (long double)(64ull << 30)) {
+      qmax = 1ull << lg;
+      break;
+    }
   qmax = std::min<uint64_t>(qmax, 1ull << 30);
   if (tc) {
     qmax = std::min<uint64_t>(qmax, 1ull << 16);
