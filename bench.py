@@ -65,7 +65,7 @@ WORKLOADS = {
     "dense1024": dict(seed=3, depth=4, cap=1 << 22, budget=1 << 26,
                       desc="random SNP system seed 3: m=1024, 4 rules/neuron (R=4096), out-degree 64, c U[1,8], "
                            "i U[c,8], j U{0,1,2}, p U[1,8], C0 U[0,16]; BFS depth 4, frontier cap 2^22, candidate "
-                           "budget 2^26, passes of up to 2^22 spiking vectors (2^20 in the fp8 tensor-core form, 65536 in the "
+                           "budget 2^26, passes of up to 2^22 spiking vectors (2^21 in the fp8 tensor-core form, 65536 in the "
                            "int8 one)",
                       cpu_sample=dict(depth=1, cap=1 << 12, budget=1 << 14),
                       ref_sample=dict(depth=1, cap=1 << 11, budget=1 << 13)),

@@ -127,7 +127,9 @@ typedef struct {
  *                    64 GiB; the
  *                    last passes of a capped depth are shortened to what the
  *                    cap is expected to take; 65536 at most in the
- *                    int8 tensor-core form, 2^20 at most in the fp8 form.
+ *                    int8 tensor-core form, 2^21 at most in the fp8 form
+ *                    (2^20 when its store's reserve, two passes per depth,
+ *                    would exceed 64 GiB).
  *  stream            cudaStream_t to run on, or NULL for the default stream.
  *  kernel_timing     1: time the expand kernel of every pass with CUDA events
  *                    on `stream` (snp_depth_info.expand_ms).

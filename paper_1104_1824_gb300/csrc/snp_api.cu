@@ -585,8 +585,9 @@ int explore_impl(snp_handle h, const snp_explore_opts* o, int32_t* depth_reached
     qmax = std::min<uint64_t>(qmax, 1ull << 16);
     TRY(tc_prepare(h, qmax, st));
   }
-  if (tc5) {
-    qmax = std::min<uint64_t>(qmax, 1ull << 20);
+  if (tc5) {  // 2^21 while the in-place store's reserve (two passes per depth) stays within 64 GiB, else 2^20
+    const bool big = (long double)(1ull << 21) * 2.0L * std::max(o->depth, 1) * 4.0L * m <= (long double)(64ull << 30);
+    qmax = std::min<uint64_t>(qmax, big ? 1ull << 21 : 1ull << 20);
     TRY(tc5_prepare(h, qmax));
   }
   // Packed store: uint8 or uint16 counts where asked for, in the sparse form,
