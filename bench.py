@@ -312,8 +312,10 @@ def time_form(args, system, w, snp, torch, dist, dev, world, local, transition: 
 
 
 def roofline_of(args, system, snp, transition: str, r, packed: bool = False):
-    """Roofline object of the form's dominant kernel (the
-    algorithmic bytes per candidate and per configuration)."""
+    """Roofline object of the form's dominant kernel: its algorithmic bytes
+    (per candidate examined and per configuration kept, as snp_depth_info's
+    expand_bytes counts them) or, for the int8 form, its dense operations,
+    over the kernel's event time."""
     ms = r["ms"]
     nlaunch = max(1, r["chunks"])
     if transition == "tc":
