@@ -86,7 +86,7 @@ WORKLOADS = {
 
 
 # timed steps by default: a timed region of at least 2 s
-DEFAULT_STEPS = {"dense1024": 80, "random64": 300, "batch4096": 5, "serving": 1, "paper": 2000}
+DEFAULT_STEPS = {"dense1024": 120, "random64": 300, "batch4096": 5, "serving": 1, "paper": 2000}
 
 
 def rank_info():
