@@ -184,3 +184,14 @@ def test_packed_random64_full_size(gpu):
     assert got.shape[0] == g["count"]
     assert [[a.new, a.examined, str(a.candidates), a.truncated] for a in s.depth_stats()] == g["per_depth"]
     assert digest(got) == g["sha256"]
+
+
+@pytest.mark.parametrize("chunk,packed", [(0, False), (20000, False), (9000, True)])
+def test_wide_passes_over_several_large_parents(gpu, chunk, packed):
+    """Rows of 160 neurons whose parents hold 8192 spiking vectors each, with a
+    cap of 30000: a pass spans several parents with at least 4096 of its
+    candidates, so the block bases of the wide mode come from several cached
+    base children (and from a full decode where a parent has fewer)."""
+    system = few_choice_system(173, 160, 13)
+    s, e = explore_both(gpu, system, 3, cap=30000, chunk=chunk, packed=packed)
+    assert_same(s, e)
