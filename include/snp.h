@@ -151,14 +151,14 @@ typedef struct {
  *                    configurations; exactness unchanged).  The bound: counts
  *                    never go below 0 and one step adds at most gain[j] =
  *                    sum over neurons of their largest entry in column j of
- *                    M_Pi, so no count exceeds max(C0[j]) + depth * gain[j]
+ *                    M_Pi, so no count of column j exceeds C0[j] + depth * gain[j]
  *                    (for a resumed exploration: the checkpoint's largest
  *                    count + the depths still to run times the largest
  *                    gain).  uint8 needs m % 16 == 0 and uint16 m % 8 == 0
  *                    (rows of whole 16-byte pieces); the tensor-core forms
  *                    keep int32, and so do snp_explore_batch, the server and
- *                    snp_explore_static, which read no other value of this
- *                    field.  snp_row_width reports the width used;
+ *                    snp_explore_static, which ignore this field.
+ *                    snp_row_width reports the width used;
  *                    snp_reachable returns int32 rows whatever it is.
  *                    0: int32 (the default).
  *  reserved          must be 0.
