@@ -38,6 +38,29 @@ def test_profiled_traffic_follows_the_code(tmp_path, monkeypatch):
     assert bench.profiled_traffic("other") is None
 
 
+def test_roofline_of_the_packed_store(tmp_path, monkeypatch):
+    """The packed form's roofline: its own ncu summary for traffic, the row
+    width in the kernel's name, achieved = algorithmic bytes / kernel time,
+    against the measured copy bandwidth."""
+    import types
+    _fake_tree(tmp_path, monkeypatch, "__global__ void k() {}\n")
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 5000.0}')
+    h = bench.kernel_source_hash()
+    (tmp_path / "profiles" / "expand_packed_kernel_w.txt").write_text(
+        f"kernel_source_hash: {h}\ndram_bytes_per_candidate: 64.0\n")
+    (tmp_path / "profiles" / "expand_kernel_w.txt").write_text(
+        f"kernel_source_hash: {h}\ndram_bytes_per_candidate: 256.0\n")
+    args = types.SimpleNamespace(workload="w")
+    system = types.SimpleNamespace(m=64, R=160)
+    r = dict(ms=10.0, expand_ms=5.0, chunks=4, expand_bytes=10 ** 10, candidates=4000, row_width=1)
+    packed = bench.roofline_of(args, system, None, "sparse", r, packed=True)
+    plain = bench.roofline_of(args, system, None, "sparse", dict(r, row_width=4))
+    assert "1 byte(s) per count" in packed["kernel"] and "byte(s)" not in plain["kernel"]
+    assert packed["traffic"] == 64 * 1000 and plain["traffic"] == 256 * 1000
+    assert packed["achieved"] == 2000.0 and packed["peak"] == 5000.0 and packed["frac"] == 0.4
+    assert packed["algorithmic_bytes_per_launch"] == 10 ** 10 // 4 and packed["expand_share_of_step"] == 0.5
+
+
 def test_e2e_steps_load_explore_and_read_back_every_time():
     """Every timed e2e step goes through the C ABI from host arrays to a full
     read-back; only the pinned result buffer is sized in an untimed step."""
