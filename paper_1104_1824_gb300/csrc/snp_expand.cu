@@ -1052,7 +1052,7 @@ __device__ __forceinline__ void resolve_warp_wide(const ClaimArgs& a, int32_t* s
           const uint32_t ll = __shfl_sync(0xffffffffu, lid, L);
           if (a.store_ctr && sl >= a.store_cap) continue;  // reported by lane L below
           typename RF::T* dst = a.store_ctr ? row_at<RF>(a.pool, sl, m) : row_at<RF>(a.staging, ll, m);
-          if constexpr (RF::W == 4 && RF::VEC) {
+          if constexpr (RF::W == 4 && RF::VEC) {  // m % 4 == 0: a row is whole, aligned 16-byte units
             bulk_wait_read(lane);  // the previous owner's copy has read the scratch row
             build(L);
             bulk_store_row(dst, scratch, (uint32_t)m * 4u, lane);
