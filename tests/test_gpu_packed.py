@@ -195,3 +195,44 @@ def test_wide_passes_over_several_large_parents(gpu, chunk, packed):
     system = few_choice_system(173, 160, 13)
     s, e = explore_both(gpu, system, 3, cap=30000, chunk=chunk, packed=packed)
     assert_same(s, e)
+
+
+def pairs(m):
+    """m neurons in pairs passing one spike to each other: C0's only child is C0."""
+    return snp_synth.make_system(m, list(range(m)), [1] * m, [1] * m, [1] * m, [1] * m,
+                                 [[n ^ 1] for n in range(m)], [1] * m, name="pairs")
+
+
+@pytest.mark.parametrize("m", [32, 144])
+def test_packed_wait_runs_out(gpu, m):
+    """A held hash slot makes the wait run out with a packed store too (narrow
+    and wide kernels); the handle explores normally afterwards."""
+    s = gpu.System(pairs(m))
+    gpu.snp_debug_hold_root_slot(True)
+    with pytest.raises(gpu.SnpError) as ei:
+        s.explore(2, timeout_ms=50, packed=True)
+    assert ei.value.code == gpu.SNP_E_TIMEOUT
+    s.explore(2, packed=True)
+    assert s.row_width() == 1 and s.count() == 1
+
+
+def test_packed_max_expand(gpu):
+    """Rows holding more than max_expand spikes somewhere are kept but not
+    expanded, read from uint8 rows."""
+    s, e = explore_both(gpu, snp_synth.random_64(1), 4, cap=4000, budget=40000, max_expand=3, packed=True)
+    assert s.row_width() == 1
+    assert_same(s, e)
+
+
+def test_packed_wide_parent_records(gpu):
+    """Parent records with uint8 rows in the wide mode (256 neurons)."""
+    system = snp_synth.random_system(88, 256, (1, 3), (2, 4), (0, 5), "sparse")
+    s = gpu.System(system)
+    s.explore(3, cap=800, budget=8000, record_parents=True, packed=True)
+    assert s.row_width() == expected_width(system, 3) == 1
+    rows = s.reachable()
+    par, idx = s.parents()
+    o = oracle.Oracle(system)
+    for k in range(1, rows.shape[0], 13):
+        assert (o.child(rows[par[k]], int(idx[k])) == rows[k]).all()
+    assert (rows == o.explore(3, cap=800, budget=8000).configs).all()
