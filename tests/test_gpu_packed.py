@@ -236,3 +236,37 @@ def test_packed_wide_parent_records(gpu):
     for k in range(1, rows.shape[0], 13):
         assert (o.child(rows[par[k]], int(idx[k])) == rows[k]).all()
     assert (rows == o.explore(3, cap=800, budget=8000).configs).all()
+
+
+@pytest.mark.parametrize("m,packed_width", [(64, 1), (1024, 2)])
+def test_packed_rows_into_device_memory(gpu, m, packed_width):
+    """snp_reachable widens packed rows straight into a device buffer, after an
+    exploration on a side stream."""
+    import torch
+    system = snp_synth.random_64(1) if m == 64 else snp_synth.dense_1024(3)
+    kw = dict(cap=1 << 12, budget=1 << 16) if m == 64 else dict(cap=1024, budget=8192)
+    s = gpu.System(system)
+    stream = torch.cuda.Stream()
+    s.explore(3, stream=stream, packed=True, **kw)
+    assert s.row_width() == packed_width
+    n = s.count()
+    out = torch.empty((n, system.m), dtype=torch.int32, device="cuda")
+    gpu.snp_reachable(s.h, out, n)
+    e = oracle.Oracle(system).explore(3, **kw)
+    assert (out.cpu().numpy() == e.configs).all()
+
+
+def test_packed_passes_of_one_candidate(gpu):
+    """uint8 rows with passes of a single candidate (every pass a ragged tail)."""
+    system = snp_synth.random_system(901, 16, (1, 3), (1, 4), (0, 4), "sparse")
+    s, e = explore_both(gpu, system, 3, cap=50, budget=400, chunk=1, packed=True)
+    assert s.row_width() == 1
+    assert_same(s, e)
+
+
+def test_packed_uint16_crossing_batches(gpu):
+    """uint16 rows (24 neurons) in the narrow kernel's crossing batches."""
+    system = few_choice_system(27, 24, 3)
+    s, e = explore_both(gpu, system, 6, cap=2000, budget=20000, packed=True)
+    assert s.row_width() == 2
+    assert_same(s, e)
